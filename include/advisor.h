@@ -1,0 +1,239 @@
+/*
+ * advisor.h -- C ABI of the GB300 (sm_103a) cost-model hot path of the
+ * OpenMP Advisor method (arXiv 2301.03636).
+ *
+ * The method (Sec. 3, Fig. 2): every kernel of a program has a set of
+ * generated offload variants (Sec. 4.1.3); a trained cost model predicts the
+ * runtime of every variant from its features (Sec. 4.2), and the variants of
+ * each kernel are sorted by predicted cost so that the best can be selected.
+ * This library computes, on one GPU:
+ *
+ *   descriptor -> validation -> integer features -> z-score standardisation
+ *   -> MLP regression (predicted ln runtime) -> per-kernel argmin,
+ *
+ * and trains the MLP from measured (here: synthetic) runtimes (training mode).
+ *
+ * Conventions for every entry point:
+ *  - Memory: every device buffer belongs to the caller.  The library never
+ *    allocates or frees device memory; sizes of the model's parameter block
+ *    and of the scratch workspace are reported by advisor_model_param_bytes
+ *    and advisor_workspace_bytes.  The model object holds host metadata only.
+ *  - Pointers prefixed d_ are device pointers, h_ host pointers.  Device
+ *    buffers must be 256-byte aligned (cudaMalloc and torch allocations are).
+ *  - Asynchrony: calls enqueue kernels on `stream` and return without
+ *    synchronising, except advisor_get_device_status.
+ *  - Errors: argument errors are returned immediately and nothing is
+ *    enqueued.  Per-row descriptor errors are reported in d_row_status.
+ *    Errors found on the device (malformed segment offsets, a wait that ran
+ *    out of time) set a sticky status word read by advisor_get_device_status.
+ *    A failed CUDA launch returns ADVISOR_ERR_CUDA.
+ *  - Threading: a model object may be used from one host thread at a time.
+ */
+#ifndef ADVISOR_H
+#define ADVISOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ADVISOR_OK = 0,
+    ADVISOR_ERR_INVALID_ARGUMENT = 1,
+    ADVISOR_ERR_BAD_DESCRIPTOR = 2,   /* device status: a descriptor failed validation */
+    ADVISOR_ERR_OUT_OF_MEMORY = 3,    /* workspace or parameter block too small */
+    ADVISOR_ERR_CUDA = 4,
+    ADVISOR_ERR_TIMEOUT = 5,          /* device status: a bounded wait gave up */
+    ADVISOR_ERR_UNSUPPORTED = 6,      /* shape or precision this build does not run */
+    ADVISOR_ERR_BAD_SEGMENTS = 7      /* device status: segment offsets not monotone / out of range */
+} advisor_status;
+
+/* Arithmetic of the MLP scorer.  FP32: SIMT FP32 FMA ("plain" path).
+ * BF16 / FP16: tcgen05 tensor cores, 16-bit operands, FP32 accumulation in
+ * tensor memory, FP32 bias/ReLU epilogue, output layer in FP32.
+ * FP64: SIMT FP64 with the oracle's summation order (slow; used for the
+ * near-tie re-score and for error calibration). */
+typedef enum {
+    ADVISOR_FP32 = 0,
+    ADVISOR_BF16 = 1,
+    ADVISOR_FP16 = 2,
+    ADVISOR_FP64 = 3
+} advisor_precision;
+
+/* One generated variant of one kernel: 16 x int64 = 128 bytes, array of
+ * structures, row-major.  Fields follow the per-kernel information of
+ * Sec. 4.1.1 (loop nest), the data classes of Sec. 4.1.2 (mapped bytes) and
+ * the five variant parameters of Sec. 4.1.3.  Valid ranges (a row outside
+ * them gets a nonzero status bit and is never selected):
+ *   depth 1..4; trip[i] in 1..2^24 for i < depth, trip[i] == 1 otherwise;
+ *   flops_per_iter, bytes_per_iter in 1..2^32; h2d_bytes, d2h_bytes in 0..2^48;
+ *   teams, threads in 1..2^24; pf_pos in 0..depth-1; dist_collapse == 0 if
+ *   pf_pos == 0 else 1..pf_pos; pf_collapse in 1..depth-pf_pos; schedule 0..2;
+ *   data_mode 0..1; trip product <= 2^48, trip product * flops_per_iter and
+ *   trip product * bytes_per_iter <= 2^62. */
+typedef struct {
+    int64_t depth;          /* number of nested for loops (NUM, Sec. 4.1.3) */
+    int64_t trip[4];        /* trip count of loop levels 0..3 */
+    int64_t flops_per_iter; /* operations in the loop body */
+    int64_t bytes_per_iter; /* bytes touched by the loop body */
+    int64_t h2d_bytes;      /* mapped to the device (alloc/to/tofrom, Sec. 4.1.2) */
+    int64_t d2h_bytes;      /* mapped back to the host (from/tofrom) */
+    int64_t teams;
+    int64_t threads;
+    int64_t pf_pos;         /* loop x carrying 'parallel for' (0: combined with distribute) */
+    int64_t dist_collapse;  /* collapse of 'teams distribute' */
+    int64_t pf_collapse;    /* collapse of 'parallel for' */
+    int64_t schedule;       /* 0 static, 1 dynamic, 2 guided */
+    int64_t data_mode;      /* the two-valued data-transfer parameter */
+} advisor_variant_desc;
+
+/* Row status bits written by the extraction kernels (0 = valid). */
+#define ADVISOR_ROW_BAD_DEPTH       0x01u
+#define ADVISOR_ROW_BAD_TRIP        0x02u
+#define ADVISOR_ROW_BAD_WORK        0x04u
+#define ADVISOR_ROW_BAD_MAPPED      0x08u
+#define ADVISOR_ROW_BAD_PARALLELISM 0x10u
+#define ADVISOR_ROW_BAD_VARIANT     0x20u
+#define ADVISOR_ROW_BAD_RANGE       0x40u
+
+typedef struct advisor_model* advisor_model_t;
+
+/* Text of a status code (static storage). */
+const char* advisor_status_string(advisor_status s);
+
+/* ---- model object -------------------------------------------------------- */
+
+/* Create the host object of an MLP with layer widths widths[0..n_widths-1]
+ * (Sec. 5, Exp. 3: fully connected, ReLU hidden layers, one output neuron).
+ * widths[0] = number of features F (32, 64 or 128), widths[n_widths-1] must be
+ * 1, 3 <= n_widths <= 8, hidden widths 1..1024.  The tensor-core precisions
+ * additionally need every hidden width <= 256 (checked when scoring). */
+advisor_status advisor_model_create(const int32_t* h_widths, int32_t n_widths, advisor_model_t* out);
+advisor_status advisor_model_destroy(advisor_model_t m);
+
+/* Bytes of the caller-allocated device parameter block: FP32 master weights,
+ * their packed 16-bit tensor-core copies, standardisation constants and the
+ * Adam moments. */
+size_t advisor_model_param_bytes(advisor_model_t m);
+
+/* Bytes of the caller-allocated scratch workspace for calls of up to max_rows
+ * rows and max_kernels kernels (16-bit activations of the tensor-core path,
+ * candidate lists of the near-tie re-score, training activations). */
+size_t advisor_workspace_bytes(advisor_model_t m, int64_t max_rows, int64_t max_kernels);
+
+/* Attach the device parameter block and workspace (sizes as reported above,
+ * 256-byte aligned).  Must precede set_params.  May be called again to move
+ * the workspace (e.g. a larger one). */
+advisor_status advisor_model_bind(advisor_model_t m, void* d_params, size_t param_bytes,
+                                  void* d_workspace, size_t workspace_bytes,
+                                  int64_t max_rows, int64_t max_kernels);
+
+/* Load parameters.  d_params_fp32: the FP32 master parameters, per layer
+ * W[out][in] row-major followed by b[out].  d_mu, d_sigma: the z-score
+ * standardisation of the features (Sec. 5, Exp. 3): z = (feature/65536 - mu)
+ * / sigma, FP64, F entries each, sigma > 0.  Packs the 16-bit copies and
+ * resets the Adam state. */
+advisor_status advisor_model_set_params(advisor_model_t m, const float* d_params_fp32,
+                                        const double* d_mu, const double* d_sigma,
+                                        cudaStream_t stream);
+
+/* Copy the FP32 master parameters out (d_params_fp32, same layout). */
+advisor_status advisor_model_get_params(advisor_model_t m, float* d_params_fp32, cudaStream_t stream);
+
+/* Number of FP32 master parameters. */
+int64_t advisor_model_param_count(advisor_model_t m);
+
+/* Fit the standardisation on a calibration sample: mean and population
+ * standard deviation of feature/65536 over the valid rows (sigma 0 -> 1).
+ * d_feat_q16 [n_rows][F], d_row_status nullable.  Writes F doubles each. */
+advisor_status advisor_fit_standardizer(const int32_t* d_feat_q16, const uint8_t* d_row_status,
+                                        int64_t n_rows, int32_t n_features, double* d_mu,
+                                        double* d_sigma, cudaStream_t stream);
+
+/* ---- hot path ----------------------------------------------------------- */
+
+/* a1-a2: validate descriptors and extract the F integer features of each
+ * (Fig. 2 "Feature Extraction"), bit-exact.  Features are Q16.16 fixed point:
+ * binary logarithms of counts, bytes and their products (digit-by-digit
+ * base-2 logarithm by repeated squaring), signed differences of those,
+ * one-hot and small-integer variant parameters.  d_feat_q16 [n_rows][F]
+ * row-major int32; invalid rows get all-zero features.  d_row_status [n_rows]
+ * (nullable) receives the ADVISOR_ROW_* bits.  F in {32, 64, 128}. */
+advisor_status advisor_extract_features(const advisor_variant_desc* d_desc, int64_t n_rows,
+                                        int32_t n_features, int32_t* d_feat_q16,
+                                        uint8_t* d_row_status, cudaStream_t stream);
+
+/* a3-a5: predicted ln runtime of every row (Fig. 2 "Predicted Runtime").
+ * d_feat_q16 [n_rows][F]; d_row_status nullable (rows with nonzero status
+ * score +inf); d_scores [n_rows] FP32.  precision as advisor_precision; the
+ * 16-bit precisions use the workspace. */
+advisor_status advisor_score_variants(advisor_model_t m, const int32_t* d_feat_q16,
+                                      const uint8_t* d_row_status, int64_t n_rows,
+                                      advisor_precision precision, float* d_scores,
+                                      cudaStream_t stream);
+
+/* a6-a7: per-kernel selection (Fig. 2 "sort codes based on cost and select").
+ * Kernel k owns rows d_seg_off[k] .. d_seg_off[k+1]-1 (int64, non-decreasing,
+ * d_seg_off[0] >= 0, last <= n_rows).  d_best_local[k] = index of the selected
+ * row within kernel k (0-based), -1 if the kernel has no finite score;
+ * d_best_score[k] its predicted ln runtime.  Ties go to the lowest index.
+ * With d_feat_q16 == NULL the selection is the argmin of d_scores.  With
+ * features, rows whose score is within 2*eps_scores of their kernel's minimum
+ * are re-scored in FP32, and rows still within 2*eps_fp32 of the FP32 minimum
+ * are re-scored in FP64 with the oracle's summation order, so that the
+ * selection equals the FP64 argmin whenever |score - fp64| <= eps_scores and
+ * |fp32 - fp64| <= eps_fp32 hold.  d_best_score then holds the value of the
+ * last tier that decided the kernel. */
+advisor_status advisor_select_best(advisor_model_t m, const float* d_scores, int64_t n_rows,
+                                   const int64_t* d_seg_off, int64_t n_kernels,
+                                   const int32_t* d_feat_q16, float eps_scores, float eps_fp32,
+                                   int32_t* d_best_local, double* d_best_score,
+                                   cudaStream_t stream);
+
+/* a1-a7 in one call: descriptors -> features -> scores -> selection, the
+ * features of the tensor-core path going straight to 16-bit standardised
+ * activations.  d_scores and d_row_status are optional outputs (nullable).
+ * Near-tie re-score as in advisor_select_best (recomputes the features of the
+ * candidate rows from their descriptors); eps_scores < 0 disables it. */
+advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                            const int64_t* d_seg_off, int64_t n_kernels,
+                            advisor_precision precision, float eps_scores, float eps_fp32,
+                            int32_t* d_best_local, double* d_best_score, float* d_scores,
+                            uint8_t* d_row_status, cudaStream_t stream);
+
+/* a8: one training step (Sec. 3 training mode; Sec. 5 Exp. 3): forward,
+ * loss = 0.5 * mean (y - label)^2 over the n_rows rows (labels: ln runtime),
+ * hand-written backward, Adam update of the FP32 master weights followed by
+ * a repack of the 16-bit copies.  precision ADVISOR_FP32 (SIMT) or
+ * ADVISOR_BF16 / ADVISOR_FP16 (16-bit operands for the forward/backward
+ * GEMMs, FP32 accumulation and master weights).  h_adam = {lr, beta1, beta2,
+ * eps, weight_decay} (host floats, copied at call time).  d_loss (nullable)
+ * receives the loss (FP32) of the forward pass before the update.  Needs
+ * n_rows <= the max_rows the workspace was bound with. */
+advisor_status advisor_train_step(advisor_model_t m, const int32_t* d_feat_q16, const float* d_labels,
+                                  int64_t n_rows, advisor_precision precision, const float* h_adam,
+                                  float* d_loss, cudaStream_t stream);
+
+/* Gradient only (no update): d_grad [param_count] FP32 of the same loss,
+ * same layout as the master parameters.  For gradient checks. */
+advisor_status advisor_loss_grad(advisor_model_t m, const int32_t* d_feat_q16, const float* d_labels,
+                                 int64_t n_rows, advisor_precision precision, float* d_grad,
+                                 float* d_loss, cudaStream_t stream);
+
+/* Read and clear the model's sticky device status word (synchronises
+ * `stream`).  Returns ADVISOR_OK, ADVISOR_ERR_TIMEOUT, ADVISOR_ERR_BAD_SEGMENTS
+ * or ADVISOR_ERR_CUDA. */
+advisor_status advisor_get_device_status(advisor_model_t m, cudaStream_t stream);
+
+/* Number of kernels this library launched since load (host-side counter of
+ * successful launches; for launch accounting in benchmarks). */
+int64_t advisor_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADVISOR_H */
