@@ -1,0 +1,354 @@
+"""Benchmark of the cost-model hot path on GB300.
+
+Workload (one step): 4,096 kernels with 4..64 generated variants each
+(~139k descriptors, F = 64 features, MLP 64-256-256-256-1, He init), the whole
+path a1-a7 in one advisor_rank call: descriptor validation + feature
+extraction -> tensor-core MLP (BF16 operands, FP32 accumulation) -> per-kernel
+argmin with the FP32 / FP64 near-tie re-score.  Metric: variants ranked per
+second.  L2 is flushed (a 512 MB write) between timed steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2301_03636_gb300 import workloads as W  # noqa: E402
+
+METRIC = "variants ranked/s, BF16-TC vs FP32 plain, 1 GB300, oracle-match; p99 query ms"
+UNIT = "variants/s"
+WL = W.BATCHED_4096
+FLOP_PER_ROW = 2 * sum(WL.widths[i] * WL.widths[i + 1] for i in range(len(WL.widths) - 1))
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP16/FP32 comparison and CPU baseline legs")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return j.get("hbm_gbs", 6800.0), j.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def traffic_for(kernel_file: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "mlp_tc_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        j = json.load(f)
+    src = os.path.join(ROOT, "paper_2301_03636_gb300", "csrc", kernel_file)
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if j.get("source_sha") != sha:
+        return None
+    return j.get("dram_bytes_per_launch_full")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(desc, off, params, mu, sigma, min_seconds=10.0):
+    """The FP64 oracle (as it stands) on the host cores over a bounded sample
+    of the same workload: the first 1,024 kernels, repeated until
+    min_seconds have elapsed."""
+    import oracle
+    K = min(1024, len(off) - 1)
+    sub_off = off[:K + 1]
+    sub = desc[:sub_off[-1]]
+    rows = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.rank(sub, sub_off, WL.widths, params, mu, sigma)
+        rows += len(sub)
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    return {"value": rows / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {K} kernels ({len(sub)} variants) of the batched workload, FP64 C oracle "
+                      f"(extract + MLP + argmin), repeated for {el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    off = WL.offsets()
+    desc = WL.descriptors()
+    cal = W.calibration_descriptors(65536)
+    fc, sc = oracle.extract_features(cal, WL.n_features)
+    mu, sigma = oracle.fit_standardizer(fc, sc)
+    params = WL.weights()
+    # each step: a bounded sample (the first 256 kernels) of the workload
+    K = 256
+    sub_off = off[:K + 1]
+    sub = desc[:sub_off[-1]]
+    for _ in range(args.warmup):
+        oracle.rank(sub, sub_off, WL.widths, params, mu, sigma)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.rank(sub, sub_off, WL.widths, params, mu, sigma)
+    el = time.perf_counter() - t0
+    v = len(sub) * args.steps / el
+    cores = oracle.num_threads()
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WL.name, "sample_kernels": K, "sample_variants": int(len(sub))},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"first {K} kernels ({len(sub)} variants) per step"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        if args.steps > 50:
+            args.steps = 20
+        if args.warmup > 5:
+            args.warmup = 3
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2301_03636_gb300 import advisor, build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+
+    # ---- setup (untimed): workload, model, standardiser, error bounds ----
+    off = WL.offsets()
+    desc_np = W.make_descriptors(int(off[-1]), WL.seed + 1000 * rank)   # weak scaling: one batch per GPU
+    n = len(desc_np)
+    K = WL.n_kernels
+    params = WL.weights()
+    cal = torch.from_numpy(W.calibration_descriptors(65536)).to(dev)
+    fcal, scal = advisor.advisor_extract_features(cal, WL.n_features)
+    mu, sigma = advisor.advisor_fit_standardizer(fcal, scal)
+    m = advisor.Model(WL.widths, max_rows=max(n, len(cal)), max_kernels=K, device=dev)
+    m.set_params(params, mu, sigma)
+    prec = args.precision
+    eps = m.calibrate_eps(fcal, scal, prec) if prec != "fp32" else m.calibrate_eps(fcal, scal, "fp32")
+    eps32 = m.calibrate_eps(fcal, scal, "fp32")
+    desc = torch.from_numpy(desc_np).to(dev)
+    offs = torch.from_numpy(off).to(dev)
+    best = torch.empty(K, dtype=torch.int32, device=dev)
+    bscore = torch.empty(K, dtype=torch.float64, device=dev)
+    scores = torch.empty(n, dtype=torch.float32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(p=prec):
+        m.rank(desc, offs, p, eps if p == prec else m_eps[p], eps32, scores=scores, best=best, best_score=bscore)
+
+    m_eps = {prec: eps}
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region ----
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in kev:   # materialise the event handles before handing them to the library
+        a.record(); b.record()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = advisor.launch_count()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        m.set_profile_events(*kev[i])
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = advisor.launch_count() - l0
+    m.set_profile_events(None, None)
+    clk = clocks.stop()
+    t_steps = [a.elapsed_time(b) for a, b in evs]
+    t_kernel = [a.elapsed_time(b) for a, b in kev]
+    ms = float(np.mean(t_steps))
+    ms_k = float(np.mean(t_kernel))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * world / (ms / 1000.0)
+
+    # ---- end to end through the public API with host buffers ----
+    desc_h = torch.from_numpy(desc_np).pin_memory()
+    off_h = torch.from_numpy(off).pin_memory()
+    best_h = torch.empty(K, dtype=torch.int32).pin_memory()
+    bs_h = torch.empty(K, dtype=torch.float64).pin_memory()
+    desc_d = torch.empty_like(desc)
+    off_d = torch.empty_like(offs)
+    e2e_steps = max(10, min(args.steps, 200))
+
+    def e2e_step():
+        desc_d.copy_(desc_h, non_blocking=True)
+        off_d.copy_(off_h, non_blocking=True)
+        m.rank(desc_d, off_d, prec, eps, eps32, best=best, best_score=bscore)
+        best_h.copy_(best, non_blocking=True)
+        bs_h.copy_(bscore, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    for i in range(e2e_steps):
+        flush.fill_(i & 0xFF)
+        e_ev[i][0].record(stream)
+        e2e_step()
+        e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = float(np.mean([a.elapsed_time(b) for a, b in e_ev]))
+    e2e = {"value": n * world / (ms_e2e / 1000.0), "unit": UNIT,
+           "h2d_bytes_per_step": int(desc_h.numel() * 8 + off_h.numel() * 8),
+           "d2h_bytes_per_step": int(K * 4 + K * 8)}
+
+    # ---- roofline of the dominant kernel (the tensor-core MLP) ----
+    hbm, tf, src = peaks()
+    achieved = n * FLOP_PER_ROW / (ms_k / 1000.0) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": tf, "unit": "TFLOP/s", "frac": achieved / tf,
+            "traffic": traffic_for("mlp_tc.cu"), "kernel": "adv::mlp_tc_kernel", "kernel_ms": ms_k,
+            "peak_source": f"{src} dense bf16 (burst; fp16 runs at the bf16 rate)",
+            "flop_per_row": FLOP_PER_ROW}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": prec, "data": "synthetic",
+           "config": {"workload": WL.name, "kernels": K, "variants": n, "features": WL.n_features,
+                      "mlp": "-".join(map(str, WL.widths)), "precision": prec, "l2": "flushed (512 MB write) "
+                      "between steps", "near_tie_rescore": "fp32 then fp64", "eps": eps, "eps32": eps32},
+           "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clk}
+
+    if rank == 0 and not args.no_extras:
+        extras = {}
+        # accuracy against the FP64 scorer and throughput of the other precisions
+        f, st = advisor.advisor_extract_features(desc, WL.n_features)
+        y64 = m.score_fp64(f, st)
+        for p in ("bf16", "fp16", "fp32"):
+            y = m.score(f, st, p).double()
+            e_p = m.calibrate_eps(fcal, scal, p)
+            m_eps[p] = e_p
+            for _ in range(3):
+                step(p)
+            torch.cuda.synchronize()
+            reps = 50
+            tt = []
+            for i in range(reps):
+                flush.fill_(i & 0xFF)
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                step(p)
+                b_.record(stream)
+                tt.append((a_, b_))
+            torch.cuda.synchronize()
+            msp = float(np.mean([a.elapsed_time(b) for a, b in tt]))
+            extras[p] = {"variants_per_s": n / (msp / 1000.0), "ms_per_step": msp,
+                         "max_abs_err_vs_fp64": float((y - y64).abs().max().item()), "eps": e_p}
+        out["precisions"] = extras
+        # the CPU oracle on the host cores (bounded sample)
+        import oracle
+        fc, sc = oracle.extract_features(W.calibration_descriptors(65536), WL.n_features)
+        mu_o, sg_o = oracle.fit_standardizer(fc, sc)
+        out["cpu_baseline"] = cpu_baseline(desc_np, off, params, mu_o, sg_o)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -175,6 +175,14 @@ advisor_status advisor_score_variants(advisor_model_t m, const int32_t* d_feat_q
                                       advisor_precision precision, float* d_scores,
                                       cudaStream_t stream);
 
+/* FP64 scores of every row (d_scores [n_rows] double), each dot product
+ * summed sequentially over the input index with separately rounded products
+ * and sums: the FP64 reference value of the regression of Sec. 4.2.  Slow
+ * (FP64 SIMT); used to measure the error bounds of the other precisions. */
+advisor_status advisor_score_variants_fp64(advisor_model_t m, const int32_t* d_feat_q16,
+                                           const uint8_t* d_row_status, int64_t n_rows,
+                                           double* d_scores, cudaStream_t stream);
+
 /* a6-a7: per-kernel selection (Fig. 2 "sort codes based on cost and select").
  * Kernel k owns rows d_seg_off[k] .. d_seg_off[k+1]-1 (int64, non-decreasing,
  * d_seg_off[0] >= 0, last <= n_rows).  d_best_local[k] = index of the selected
@@ -227,6 +235,13 @@ advisor_status advisor_loss_grad(advisor_model_t m, const int32_t* d_feat_q16, c
  * `stream`).  Returns ADVISOR_OK, ADVISOR_ERR_TIMEOUT, ADVISOR_ERR_BAD_SEGMENTS
  * or ADVISOR_ERR_CUDA. */
 advisor_status advisor_get_device_status(advisor_model_t m, cudaStream_t stream);
+
+/* Measurement hook: when ev_start / ev_stop (cudaEvent_t handles created by
+ * the caller with timing enabled) are non-NULL, every later launch of the
+ * tensor-core scorer by this model is bracketed by cudaEventRecord on the
+ * call's stream, so that the caller can time that kernel alone inside a
+ * longer sequence.  Pass NULL, NULL to stop. */
+advisor_status advisor_model_set_profile_events(advisor_model_t m, void* ev_start, void* ev_stop);
 
 /* Number of kernels this library launched since load (host-side counter of
  * successful launches; for launch accounting in benchmarks). */

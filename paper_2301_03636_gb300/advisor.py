@@ -1,0 +1,250 @@
+"""Python binding of libadvisor (include/advisor.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  torch provides device memory and streams.  There is no CPU
+fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "bad descriptor", 3: "out of memory", 4: "CUDA error",
+                5: "device wait timed out", 6: "unsupported", 7: "malformed segment offsets"}
+FP32, BF16, FP16, FP64 = 0, 1, 2, 3
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp16": FP16, "fp64": FP64}
+
+_lib = None
+
+
+class AdvisorError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS_NAMES.get(code, code)} ({code})")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libadvisor.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libadvisor.so is not built ({path}); run paper_2301_03636_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P, i64, i32, f32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_size_t
+    st = ctypes.c_int
+    sig = {
+        "advisor_status_string": (ctypes.c_char_p, [st]),
+        "advisor_launch_count": (i64, []),
+        "advisor_model_create": (st, [P, i32, ctypes.POINTER(P)]),
+        "advisor_model_destroy": (st, [P]),
+        "advisor_model_param_bytes": (sz, [P]),
+        "advisor_model_param_count": (i64, [P]),
+        "advisor_workspace_bytes": (sz, [P, i64, i64]),
+        "advisor_model_bind": (st, [P, P, sz, P, sz, i64, i64]),
+        "advisor_model_set_params": (st, [P, P, P, P, P]),
+        "advisor_model_get_params": (st, [P, P, P]),
+        "advisor_fit_standardizer": (st, [P, P, i64, i32, P, P, P]),
+        "advisor_extract_features": (st, [P, i64, i32, P, P, P]),
+        "advisor_score_variants": (st, [P, P, P, i64, st, P, P]),
+        "advisor_score_variants_fp64": (st, [P, P, P, i64, P, P]),
+        "advisor_select_best": (st, [P, P, i64, P, i64, P, f32, f32, P, P, P]),
+        "advisor_rank": (st, [P, P, i64, P, i64, st, f32, f32, P, P, P, P, P]),
+        "advisor_train_step": (st, [P, P, P, i64, st, P, P, P]),
+        "advisor_loss_grad": (st, [P, P, P, i64, st, P, P, P]),
+        "advisor_get_device_status": (st, [P, P]),
+        "advisor_model_set_profile_events": (st, [P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/advisor.h."""
+    h = os.path.join(_build.ROOT, "include", "advisor.h")
+    text = open(h).read()
+    return sorted(set(re.findall(r"\b(advisor_[a-z0-9_]+)\s*\(", text)))
+
+
+def launch_count() -> int:
+    return int(lib().advisor_launch_count())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(code, what):
+    if code != OK:
+        raise AdvisorError(code, what)
+
+
+def _prec(p):
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def _dev(x, dtype, device):
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=dtype).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=device)
+
+
+# ---- stateless entry points --------------------------------------------------------
+
+
+def advisor_extract_features(desc: torch.Tensor, n_features: int, stream=None):
+    """a1-a2: descriptors [n,16] int64 (CUDA) -> (features [n,F] int32, status [n] uint8)."""
+    assert desc.is_cuda and desc.dtype == torch.int64 and desc.is_contiguous() and desc.shape[-1] == 16
+    n = desc.shape[0]
+    feat = torch.empty((n, n_features), dtype=torch.int32, device=desc.device)
+    status = torch.empty(n, dtype=torch.uint8, device=desc.device)
+    _check(lib().advisor_extract_features(_ptr(desc), n, n_features, _ptr(feat), _ptr(status), _stream(stream)),
+           "advisor_extract_features")
+    return feat, status
+
+
+def advisor_fit_standardizer(feat: torch.Tensor, status: torch.Tensor | None = None, stream=None):
+    n, F = feat.shape
+    mu = torch.empty(F, dtype=torch.float64, device=feat.device)
+    sigma = torch.empty(F, dtype=torch.float64, device=feat.device)
+    _check(lib().advisor_fit_standardizer(_ptr(feat), _ptr(status), n, F, _ptr(mu), _ptr(sigma), _stream(stream)),
+           "advisor_fit_standardizer")
+    return mu, sigma
+
+
+class Model:
+    """An MLP cost model bound to caller-owned (torch) device memory."""
+
+    def __init__(self, widths, max_rows: int, max_kernels: int, device="cuda"):
+        self.widths = tuple(int(w) for w in widths)
+        self.device = torch.device(device)
+        w = (ctypes.c_int32 * len(self.widths))(*self.widths)
+        h = ctypes.c_void_p()
+        _check(lib().advisor_model_create(ctypes.cast(w, ctypes.c_void_p), len(self.widths), ctypes.byref(h)),
+               "advisor_model_create")
+        self.handle = h
+        self.max_rows = int(max_rows)
+        self.max_kernels = int(max_kernels)
+        pb = lib().advisor_model_param_bytes(h)
+        wb = lib().advisor_workspace_bytes(h, self.max_rows, self.max_kernels)
+        self.param_block = torch.empty(pb, dtype=torch.uint8, device=self.device)
+        self.workspace = torch.empty(wb, dtype=torch.uint8, device=self.device)
+        _check(lib().advisor_model_bind(h, _ptr(self.param_block), pb, _ptr(self.workspace), wb, self.max_rows,
+                                        self.max_kernels), "advisor_model_bind")
+        self.n_params = int(lib().advisor_model_param_count(h))
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) is not None and _lib is not None:
+                _lib.advisor_model_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    @property
+    def n_features(self) -> int:
+        return self.widths[0]
+
+    def set_params(self, params, mu, sigma, stream=None):
+        p = _dev(params, torch.float32, self.device)
+        assert p.numel() == self.n_params
+        m = _dev(mu, torch.float64, self.device)
+        s = _dev(sigma, torch.float64, self.device)
+        _check(lib().advisor_model_set_params(self.handle, _ptr(p), _ptr(m), _ptr(s), _stream(stream)),
+               "advisor_model_set_params")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
+    def get_params(self, stream=None) -> torch.Tensor:
+        out = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        _check(lib().advisor_model_get_params(self.handle, _ptr(out), _stream(stream)), "advisor_model_get_params")
+        return out
+
+    def score(self, feat, status=None, precision="fp32", out=None, stream=None) -> torch.Tensor:
+        n = feat.shape[0]
+        out = torch.empty(n, dtype=torch.float32, device=self.device) if out is None else out
+        _check(lib().advisor_score_variants(self.handle, _ptr(feat), _ptr(status), n, _prec(precision), _ptr(out),
+                                            _stream(stream)), "advisor_score_variants")
+        return out
+
+    def score_fp64(self, feat, status=None, stream=None) -> torch.Tensor:
+        n = feat.shape[0]
+        out = torch.empty(n, dtype=torch.float64, device=self.device)
+        _check(lib().advisor_score_variants_fp64(self.handle, _ptr(feat), _ptr(status), n, _ptr(out),
+                                                 _stream(stream)), "advisor_score_variants_fp64")
+        return out
+
+    def select(self, scores, offsets, feat=None, eps=-1.0, eps32=0.0, stream=None):
+        K = offsets.shape[0] - 1
+        best = torch.empty(K, dtype=torch.int32, device=self.device)
+        best_score = torch.empty(K, dtype=torch.float64, device=self.device)
+        _check(lib().advisor_select_best(self.handle, _ptr(scores), scores.shape[0], _ptr(offsets), K, _ptr(feat),
+                                         float(eps), float(eps32), _ptr(best), _ptr(best_score), _stream(stream)),
+               "advisor_select_best")
+        return best, best_score
+
+    def rank(self, desc, offsets, precision="bf16", eps=-1.0, eps32=0.0, scores=None, status=None, best=None,
+             best_score=None, stream=None):
+        K = offsets.shape[0] - 1
+        best = torch.empty(K, dtype=torch.int32, device=self.device) if best is None else best
+        best_score = torch.empty(K, dtype=torch.float64, device=self.device) if best_score is None else best_score
+        _check(lib().advisor_rank(self.handle, _ptr(desc), desc.shape[0], _ptr(offsets), K, _prec(precision),
+                                  float(eps), float(eps32), _ptr(best), _ptr(best_score), _ptr(scores), _ptr(status),
+                                  _stream(stream)), "advisor_rank")
+        return best, best_score
+
+    def train_step(self, feat, labels, precision="fp32", lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                   weight_decay=0.0, loss=None, stream=None):
+        h = (ctypes.c_float * 5)(lr, beta1, beta2, eps, weight_decay)
+        _check(lib().advisor_train_step(self.handle, _ptr(feat), _ptr(labels), feat.shape[0], _prec(precision),
+                                        ctypes.cast(h, ctypes.c_void_p), _ptr(loss), _stream(stream)),
+               "advisor_train_step")
+        return loss
+
+    def loss_grad(self, feat, labels, precision="fp32", stream=None):
+        grad = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        _check(lib().advisor_loss_grad(self.handle, _ptr(feat), _ptr(labels), feat.shape[0], _prec(precision),
+                                       _ptr(grad), _ptr(loss), _stream(stream)), "advisor_loss_grad")
+        return loss, grad
+
+    def set_profile_events(self, start=None, stop=None):
+        """Bracket later tensor-core scorer launches with these torch.cuda.Events."""
+        if start is None:
+            _check(lib().advisor_model_set_profile_events(self.handle, None, None), "set_profile_events")
+            return
+        _check(lib().advisor_model_set_profile_events(self.handle, ctypes.c_void_p(start.cuda_event),
+                                                      ctypes.c_void_p(stop.cuda_event)), "set_profile_events")
+
+    def device_status(self, stream=None) -> int:
+        return int(lib().advisor_get_device_status(self.handle, _stream(stream)))
+
+    def calibrate_eps(self, feat, status=None, precision="bf16", safety=2.0):
+        """Measured error bound of a precision against the FP64 scorer on a
+        calibration sample: safety * max |score - fp64| over the valid rows."""
+        y = self.score(feat, status, precision).double()
+        y64 = self.score_fp64(feat, status)
+        ok = torch.isfinite(y64)
+        return float(safety * (y[ok] - y64[ok]).abs().max().item())

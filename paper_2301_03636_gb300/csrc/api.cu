@@ -1,0 +1,496 @@
+// C ABI of libadvisor (include/advisor.h): argument checks, the layouts of
+// the caller-owned parameter block and workspace, and the launch sequences
+// of the hot path.  No entry point allocates device memory or synchronises,
+// except advisor_get_device_status.
+#include <atomic>
+#include <cstring>
+#include <new>
+
+#include "mlp.cuh"
+#include "pack.cuh"
+#include "train.cuh"
+
+namespace {
+
+std::atomic<long long> g_launches{0};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+int roundup(int x, int m) { return ((x + m - 1) / m) * m; }
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+struct WsLayout {
+    size_t x_img, feat32, status, scores, counters, seg_state, seg_start, seg_cnt;
+    size_t cand_rows, y32, cand2_rows, y64;
+    size_t train;   // start of the training region
+    size_t bytes;
+};
+
+}  // namespace
+
+extern "C" void adv_count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+struct advisor_model {
+    adv::ModelLayout L;
+    uint8_t* P = nullptr;
+    size_t p_bytes = 0;
+    uint8_t* WS = nullptr;
+    size_t ws_bytes = 0;
+    int64_t max_rows = 0, max_kernels = 0;
+    WsLayout W{};
+    adv::TrainLayout T{};
+    int num_sms = 0;
+    bool params_set = false;
+    cudaEvent_t prof_start = nullptr, prof_stop = nullptr;   // bracket the tensor-core scorer launch
+    int64_t adam_step = 0;
+};
+
+namespace {
+
+advisor_status cuda_status(cudaError_t e) { return e == cudaSuccess ? ADVISOR_OK : ADVISOR_ERR_CUDA; }
+
+WsLayout ws_layout(const adv::ModelLayout& L, int64_t R, int64_t K, adv::TrainLayout* T) {
+    WsLayout w{};
+    size_t o = 0;
+    const int64_t tiles = (R + ADV_TILE_M - 1) / ADV_TILE_M;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    w.x_img = take((size_t)tiles * L.nslab[0] * ADV_X_SLAB_BYTES);
+    w.feat32 = take((size_t)R * L.F * 4);
+    w.status = take((size_t)R);
+    w.scores = take((size_t)R * 4);
+    w.counters = take(16);
+    w.seg_state = take((size_t)K * 4);
+    w.seg_start = take((size_t)K * 4);
+    w.seg_cnt = take((size_t)K * 4);
+    w.cand_rows = take((size_t)R * 8);
+    w.y32 = take((size_t)R * 4);
+    w.cand2_rows = take((size_t)R * 8);
+    w.y64 = take((size_t)R * 8);
+    w.train = o;
+    const size_t tb = adv::train_layout(L, R, T);
+    o = align256(o + tb);
+    w.bytes = o;
+    return w;
+}
+
+adv::MlpDesc mlp_desc(const advisor_model* m) {
+    const adv::ModelLayout& L = m->L;
+    adv::MlpDesc d{};
+    d.nw = L.nw;
+    for (int i = 0; i < L.nw; ++i) d.widths[i] = L.widths[i];
+    const float* master = reinterpret_cast<const float*>(m->P + L.p_master);
+    for (int l = 0; l < L.n_layers; ++l) {
+        d.W[l] = master + L.layer_w_off[l];
+        d.b[l] = master + L.layer_b_off[l];
+        d.WT[l] = reinterpret_cast<const float*>(m->P + L.p_wT[l]);
+    }
+    d.sa = reinterpret_cast<const float*>(m->P + L.p_stdz_a);
+    d.sc = reinterpret_cast<const float*>(m->P + L.p_stdz_c);
+    d.mu = reinterpret_cast<const double*>(m->P + L.p_mu);
+    d.sigma = reinterpret_cast<const double*>(m->P + L.p_sigma);
+    return d;
+}
+
+int* status_word(advisor_model* m) { return reinterpret_cast<int*>(m->P + m->L.p_status); }
+
+adv::TcArgs tc_args(advisor_model* m, const uint8_t* x_img, int64_t n, const uint8_t* status, float* scores,
+                    int fmt_idx /* 0 bf16, 1 fp16 */) {
+    const adv::ModelLayout& L = m->L;
+    adv::TcArgs a{};
+    a.x_img = x_img;
+    for (int l = 0; l < L.n_hidden; ++l) {
+        a.w_img[l] = m->P + L.p_w16[fmt_idx][l];
+        a.bias[l] = reinterpret_cast<const float*>(m->P + L.p_bias_off[l]);
+        a.npad[l] = L.npad[l];
+        a.nslab[l] = L.nslab[l];
+    }
+    a.w_out = reinterpret_cast<const float*>(m->P + L.p_wout_pad);
+    a.b_out = reinterpret_cast<const float*>(m->P + L.p_master) + L.layer_b_off[L.n_layers - 1];
+    a.n_hidden = L.n_hidden;
+    a.nmax = L.nmax;
+    a.fmt = fmt_idx == 0 ? 1 : 0;   // instruction-descriptor code: 1 = BF16, 0 = F16
+    a.n_rows = n;
+    a.n_tiles = (int)((n + ADV_TILE_M - 1) / ADV_TILE_M);
+    a.status = status;
+    a.scores = scores;
+    a.status_word = status_word(m);
+    a.timeout_ns = 2000000000ull;
+    return a;
+}
+
+bool tc_supported(const advisor_model* m) {
+    const adv::ModelLayout& L = m->L;
+    if (!L.tc_ok) return false;
+    int nslab_max = 1;
+    for (int l = 0; l < L.n_hidden; ++l) nslab_max = L.nslab[l] > nslab_max ? L.nslab[l] : nslab_max;
+    return adv::mlp_tc_smem_bytes(nslab_max, L.nmax) <= 232448;
+}
+
+advisor_status check_ready(const advisor_model* m, int64_t n_rows) {
+    if (!m || !m->P || !m->WS || !m->params_set) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (n_rows > m->max_rows) return ADVISOR_ERR_OUT_OF_MEMORY;
+    return ADVISOR_OK;
+}
+
+cudaError_t launch_tc_profiled(advisor_model* m, const adv::TcArgs& a, cudaStream_t s) {
+    if (m->prof_start) {
+        cudaError_t e = cudaEventRecord(m->prof_start, s);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = adv::launch_mlp_tc(a, m->num_sms, s);
+    if (e == cudaSuccess && m->prof_stop) e = cudaEventRecord(m->prof_stop, s);
+    return e;
+}
+
+// Tiered selection; `src` supplies the rows for the re-score (features or descriptors).
+advisor_status do_select(advisor_model* m, const float* scores, int64_t n_rows, const int64_t* off, int64_t K,
+                         adv::RowSrc src, bool rescore, float eps, float eps32, int32_t* best, double* best_score,
+                         cudaStream_t s) {
+    if (K > m->max_kernels) return ADVISOR_ERR_OUT_OF_MEMORY;
+    adv::SelectArgs a{};
+    a.scores = scores;
+    a.n_rows = n_rows;
+    a.off = off;
+    a.n_kernels = K;
+    a.best = best;
+    a.best_score = best_score;
+    a.eps = rescore ? eps : -1.f;
+    a.eps32 = eps32;
+    a.counters = reinterpret_cast<int*>(m->WS + m->W.counters);
+    a.seg_state = reinterpret_cast<int*>(m->WS + m->W.seg_state);
+    a.seg_start = reinterpret_cast<int*>(m->WS + m->W.seg_start);
+    a.seg_cnt = reinterpret_cast<int*>(m->WS + m->W.seg_cnt);
+    a.cand_rows = reinterpret_cast<int64_t*>(m->WS + m->W.cand_rows);
+    a.y32 = reinterpret_cast<float*>(m->WS + m->W.y32);
+    a.cand2_rows = reinterpret_cast<int64_t*>(m->WS + m->W.cand2_rows);
+    a.y64 = reinterpret_cast<double*>(m->WS + m->W.y64);
+    a.status_word = status_word(m);
+    cudaError_t e;
+    if (rescore) {
+        e = cudaMemsetAsync(a.counters, 0, 2 * sizeof(int), s);
+        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    }
+    e = adv::launch_select_tier1(a, s);
+    if (e != cudaSuccess || !rescore) return cuda_status(e);
+    const adv::MlpDesc md = mlp_desc(m);
+    adv::RowSrc r1 = src;
+    r1.rows = a.cand_rows;
+    r1.count_dev = &a.counters[0];
+    r1.count = 0;
+    e = adv::launch_mlp_fp32(md, r1, a.y32, m->num_sms, true, s);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    e = adv::launch_select_tier2(a, s);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    adv::RowSrc r2 = src;
+    r2.rows = a.cand2_rows;
+    r2.count_dev = &a.counters[1];
+    r2.count = 0;
+    e = adv::launch_mlp_fp64(md, r2, a.y64, m->num_sms, s);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    return cuda_status(adv::launch_select_final(a, s));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* advisor_status_string(advisor_status s) {
+    switch (s) {
+        case ADVISOR_OK: return "ok";
+        case ADVISOR_ERR_INVALID_ARGUMENT: return "invalid argument";
+        case ADVISOR_ERR_BAD_DESCRIPTOR: return "bad descriptor";
+        case ADVISOR_ERR_OUT_OF_MEMORY: return "workspace or parameter block too small";
+        case ADVISOR_ERR_CUDA: return "CUDA error";
+        case ADVISOR_ERR_TIMEOUT: return "device wait timed out";
+        case ADVISOR_ERR_UNSUPPORTED: return "unsupported shape or precision";
+        case ADVISOR_ERR_BAD_SEGMENTS: return "malformed segment offsets";
+    }
+    return "unknown status";
+}
+
+int64_t advisor_launch_count(void) { return (int64_t)g_launches.load(); }
+
+advisor_status advisor_model_create(const int32_t* h_widths, int32_t n_widths, advisor_model_t* out) {
+    if (!h_widths || !out || n_widths < 3 || n_widths > ADV_MAX_LAYERS) return ADVISOR_ERR_INVALID_ARGUMENT;
+    const int F = h_widths[0];
+    if (F != 32 && F != 64 && F != 128) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (h_widths[n_widths - 1] != 1) return ADVISOR_ERR_INVALID_ARGUMENT;
+    for (int i = 1; i + 1 < n_widths; ++i)
+        if (h_widths[i] < 1 || h_widths[i] > 1024) return ADVISOR_ERR_INVALID_ARGUMENT;
+    advisor_model* m = new (std::nothrow) advisor_model();
+    if (!m) return ADVISOR_ERR_OUT_OF_MEMORY;
+    adv::ModelLayout& L = m->L;
+    L.nw = n_widths;
+    for (int i = 0; i < n_widths; ++i) L.widths[i] = h_widths[i];
+    L.F = F;
+    L.n_layers = n_widths - 1;
+    L.n_hidden = n_widths - 2;
+    int64_t po = 0;
+    for (int l = 0; l < L.n_layers; ++l) {
+        L.layer_w_off[l] = po;
+        po += (int64_t)L.widths[l + 1] * L.widths[l];
+        L.layer_b_off[l] = po;
+        po += L.widths[l + 1];
+    }
+    L.n_params = po;
+    L.tc_ok = 1;
+    L.nmax = 0;
+    for (int l = 0; l < L.n_hidden; ++l) {
+        L.kpad[l] = roundup(L.widths[l], 64);
+        L.npad[l] = roundup(L.widths[l + 1], 64);
+        L.nslab[l] = L.kpad[l] / 64;
+        if (L.widths[l + 1] > 256) L.tc_ok = 0;
+        L.nmax = L.npad[l] > L.nmax ? L.npad[l] : L.nmax;
+    }
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    L.p_master = take((size_t)L.n_params * 4);
+    for (int l = 0; l < L.n_layers; ++l) L.p_wT[l] = take((size_t)L.widths[l] * L.widths[l + 1] * 4);
+    for (int l = 0; l < L.n_hidden; ++l) {
+        L.p_w16[0][l] = take((size_t)L.npad[l] * L.kpad[l] * 2);
+        L.p_w16[1][l] = take((size_t)L.npad[l] * L.kpad[l] * 2);
+        L.p_bias_off[l] = take((size_t)L.npad[l] * 4);
+    }
+    L.p_wout_pad = take((size_t)L.npad[L.n_hidden - 1] * 4);
+    L.p_stdz_a = take((size_t)F * 4);
+    L.p_stdz_c = take((size_t)F * 4);
+    L.p_mu = take((size_t)F * 8);
+    L.p_sigma = take((size_t)F * 8);
+    L.p_adam_m = take((size_t)L.n_params * 4);
+    L.p_adam_v = take((size_t)L.n_params * 4);
+    L.p_status = take(16);
+    L.p_misc = take(256);
+    L.param_bytes = o;
+    *out = m;
+    return ADVISOR_OK;
+}
+
+advisor_status advisor_model_destroy(advisor_model_t m) {
+    delete m;
+    return ADVISOR_OK;
+}
+
+size_t advisor_model_param_bytes(advisor_model_t m) { return m ? m->L.param_bytes : 0; }
+
+int64_t advisor_model_param_count(advisor_model_t m) { return m ? m->L.n_params : 0; }
+
+size_t advisor_workspace_bytes(advisor_model_t m, int64_t max_rows, int64_t max_kernels) {
+    if (!m || max_rows < 0 || max_kernels < 0) return 0;
+    adv::TrainLayout t{};
+    return ws_layout(m->L, max_rows < 1 ? 1 : max_rows, max_kernels < 1 ? 1 : max_kernels, &t).bytes;
+}
+
+advisor_status advisor_model_bind(advisor_model_t m, void* d_params, size_t param_bytes, void* d_workspace,
+                                  size_t workspace_bytes, int64_t max_rows, int64_t max_kernels) {
+    if (!m || !d_params || !d_workspace || max_rows < 1 || max_kernels < 1) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (!aligned(d_params, 256) || !aligned(d_workspace, 256)) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (param_bytes < m->L.param_bytes) return ADVISOR_ERR_OUT_OF_MEMORY;
+    adv::TrainLayout t{};
+    const WsLayout w = ws_layout(m->L, max_rows, max_kernels, &t);
+    if (workspace_bytes < w.bytes) return ADVISOR_ERR_OUT_OF_MEMORY;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ADVISOR_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return ADVISOR_ERR_CUDA;
+    if (m->P != (uint8_t*)d_params) m->params_set = false;
+    m->P = (uint8_t*)d_params;
+    m->p_bytes = param_bytes;
+    m->WS = (uint8_t*)d_workspace;
+    m->ws_bytes = workspace_bytes;
+    m->max_rows = max_rows;
+    m->max_kernels = max_kernels;
+    m->W = w;
+    m->T = t;
+    return ADVISOR_OK;
+}
+
+advisor_status advisor_model_set_params(advisor_model_t m, const float* d_params_fp32, const double* d_mu,
+                                        const double* d_sigma, cudaStream_t stream) {
+    if (!m || !m->P || !d_params_fp32 || !d_mu || !d_sigma) return ADVISOR_ERR_INVALID_ARGUMENT;
+    cudaError_t e = cudaMemsetAsync(m->P + m->L.p_status, 0, 16, stream);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    e = adv::launch_set_params(m->L, m->P, d_params_fp32, d_mu, d_sigma, stream);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    m->params_set = true;
+    m->adam_step = 0;
+    return ADVISOR_OK;
+}
+
+advisor_status advisor_model_get_params(advisor_model_t m, float* d_params_fp32, cudaStream_t stream) {
+    if (!m || !m->P || !d_params_fp32) return ADVISOR_ERR_INVALID_ARGUMENT;
+    return cuda_status(adv::launch_copy_f32(reinterpret_cast<const float*>(m->P + m->L.p_master), d_params_fp32,
+                                            m->L.n_params, stream));
+}
+
+advisor_status advisor_fit_standardizer(const int32_t* d_feat_q16, const uint8_t* d_row_status, int64_t n_rows,
+                                        int32_t n_features, double* d_mu, double* d_sigma, cudaStream_t stream) {
+    if (!d_feat_q16 || !d_mu || !d_sigma || n_rows < 1 || n_features < 1 || n_features > 1024)
+        return ADVISOR_ERR_INVALID_ARGUMENT;
+    return cuda_status(adv::launch_fit_standardizer(d_feat_q16, d_row_status, n_rows, n_features, d_mu, d_sigma,
+                                                    stream));
+}
+
+advisor_status advisor_extract_features(const advisor_variant_desc* d_desc, int64_t n_rows, int32_t n_features,
+                                        int32_t* d_feat_q16, uint8_t* d_row_status, cudaStream_t stream) {
+    if (n_rows < 0 || (n_features != 32 && n_features != 64 && n_features != 128))
+        return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (n_rows == 0) return ADVISOR_OK;
+    if (!d_desc || !d_feat_q16 || !aligned(d_desc, 16) || !aligned(d_feat_q16, 16))
+        return ADVISOR_ERR_INVALID_ARGUMENT;
+    adv::ExtractArgs a{};
+    a.desc = d_desc;
+    a.n_rows = n_rows;
+    a.n_rows_padded = n_rows;
+    a.feat = d_feat_q16;
+    a.status = d_row_status;
+    return cuda_status(adv::launch_extract(a, n_features, 0, stream));
+}
+
+advisor_status advisor_score_variants(advisor_model_t m, const int32_t* d_feat_q16, const uint8_t* d_row_status,
+                                      int64_t n_rows, advisor_precision precision, float* d_scores,
+                                      cudaStream_t stream) {
+    if (!m || n_rows < 0 || !d_feat_q16 || !d_scores || !aligned(d_feat_q16, 16))
+        return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (n_rows == 0) return ADVISOR_OK;
+    advisor_status st = check_ready(m, n_rows);
+    if (st != ADVISOR_OK) return st;
+    if (precision == ADVISOR_FP32) {
+        adv::RowSrc src{d_feat_q16, nullptr, nullptr, nullptr, n_rows, d_row_status};
+        return cuda_status(adv::launch_mlp_fp32(mlp_desc(m), src, d_scores, m->num_sms, false, stream));
+    }
+    if (precision != ADVISOR_BF16 && precision != ADVISOR_FP16) return ADVISOR_ERR_UNSUPPORTED;
+    if (!tc_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
+    const int fi = precision == ADVISOR_BF16 ? 0 : 1;
+    const int64_t npad = ((n_rows + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
+    uint8_t* x = m->WS + m->W.x_img;
+    cudaError_t e = adv::launch_standardize(d_feat_q16, d_row_status, n_rows, npad, x, m->L.nslab[0],
+                                            reinterpret_cast<const float*>(m->P + m->L.p_stdz_a),
+                                            reinterpret_cast<const float*>(m->P + m->L.p_stdz_c), m->L.F,
+                                            fi == 0 ? 1 : 2, stream);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    return cuda_status(launch_tc_profiled(m, tc_args(m, x, n_rows, d_row_status, d_scores, fi), stream));
+}
+
+advisor_status advisor_score_variants_fp64(advisor_model_t m, const int32_t* d_feat_q16,
+                                           const uint8_t* d_row_status, int64_t n_rows, double* d_scores,
+                                           cudaStream_t stream) {
+    if (!m || n_rows < 0 || !d_feat_q16 || !d_scores) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (n_rows == 0) return ADVISOR_OK;
+    if (!m->P || !m->params_set) return ADVISOR_ERR_INVALID_ARGUMENT;
+    adv::RowSrc src{d_feat_q16, nullptr, nullptr, nullptr, n_rows, d_row_status};
+    return cuda_status(adv::launch_mlp_fp64(mlp_desc(m), src, d_scores, m->num_sms, stream));
+}
+
+advisor_status advisor_select_best(advisor_model_t m, const float* d_scores, int64_t n_rows,
+                                   const int64_t* d_seg_off, int64_t n_kernels, const int32_t* d_feat_q16,
+                                   float eps_scores, float eps_fp32, int32_t* d_best_local, double* d_best_score,
+                                   cudaStream_t stream) {
+    if (!m || n_rows < 0 || n_kernels < 0 || !d_best_local || !d_best_score) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (n_kernels == 0) return ADVISOR_OK;
+    if (!d_seg_off || (n_rows > 0 && !d_scores)) return ADVISOR_ERR_INVALID_ARGUMENT;
+    const bool rescore = d_feat_q16 != nullptr && eps_scores >= 0.f;
+    if (rescore && (eps_fp32 < 0.f || !aligned(d_feat_q16, 16))) return ADVISOR_ERR_INVALID_ARGUMENT;
+    advisor_status st = check_ready(m, n_rows);
+    if (st != ADVISOR_OK) return st;
+    adv::RowSrc src{d_feat_q16, nullptr, nullptr, nullptr, 0, nullptr};
+    return do_select(m, d_scores, n_rows, d_seg_off, n_kernels, src, rescore, eps_scores, eps_fp32, d_best_local,
+                     d_best_score, stream);
+}
+
+advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                            const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
+                            float eps_scores, float eps_fp32, int32_t* d_best_local, double* d_best_score,
+                            float* d_scores, uint8_t* d_row_status, cudaStream_t stream) {
+    if (!m || n_rows < 0 || n_kernels < 0 || !d_best_local || !d_best_score) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (n_kernels == 0) return ADVISOR_OK;
+    if (!d_seg_off || (n_rows > 0 && (!d_desc || !aligned(d_desc, 16)))) return ADVISOR_ERR_INVALID_ARGUMENT;
+    advisor_status st = check_ready(m, n_rows);
+    if (st != ADVISOR_OK) return st;
+    if (n_kernels > m->max_kernels) return ADVISOR_ERR_OUT_OF_MEMORY;
+    const bool rescore = eps_scores >= 0.f;
+    if (rescore && eps_fp32 < 0.f) return ADVISOR_ERR_INVALID_ARGUMENT;
+    float* scores = d_scores ? d_scores : reinterpret_cast<float*>(m->WS + m->W.scores);
+    uint8_t* status = d_row_status ? d_row_status : m->WS + m->W.status;
+    const adv::ModelLayout& L = m->L;
+    if (n_rows > 0) {
+        adv::ExtractArgs a{};
+        a.desc = d_desc;
+        a.n_rows = n_rows;
+        a.status = status;
+        a.sa = reinterpret_cast<const float*>(m->P + L.p_stdz_a);
+        a.sc = reinterpret_cast<const float*>(m->P + L.p_stdz_c);
+        cudaError_t e;
+        if (precision == ADVISOR_FP32) {
+            a.n_rows_padded = n_rows;
+            a.feat = reinterpret_cast<int32_t*>(m->WS + m->W.feat32);
+            e = adv::launch_extract(a, L.F, 0, stream);
+            if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+            adv::RowSrc src{a.feat, nullptr, nullptr, nullptr, n_rows, status};
+            e = adv::launch_mlp_fp32(mlp_desc(m), src, scores, m->num_sms, false, stream);
+            if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+            adv::RowSrc rs{a.feat, nullptr, nullptr, nullptr, 0, nullptr};
+            return do_select(m, scores, n_rows, d_seg_off, n_kernels, rs, rescore, eps_scores, eps_fp32,
+                             d_best_local, d_best_score, stream);
+        }
+        if (precision != ADVISOR_BF16 && precision != ADVISOR_FP16) return ADVISOR_ERR_UNSUPPORTED;
+        if (!tc_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
+        const int fi = precision == ADVISOR_BF16 ? 0 : 1;
+        a.n_rows_padded = ((n_rows + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
+        a.x_img = m->WS + m->W.x_img;
+        a.nslab = L.nslab[0];
+        e = adv::launch_extract(a, L.F, fi == 0 ? 1 : 2, stream);
+        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+        e = launch_tc_profiled(m, tc_args(m, a.x_img, n_rows, status, scores, fi), stream);
+        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    }
+    adv::RowSrc rs{nullptr, d_desc, nullptr, nullptr, 0, nullptr};
+    return do_select(m, scores, n_rows, d_seg_off, n_kernels, rs, rescore && n_rows > 0, eps_scores, eps_fp32,
+                     d_best_local, d_best_score, stream);
+}
+
+advisor_status advisor_train_step(advisor_model_t m, const int32_t* d_feat_q16, const float* d_labels,
+                                  int64_t n_rows, advisor_precision precision, const float* h_adam, float* d_loss,
+                                  cudaStream_t stream) {
+    if (!m || !d_feat_q16 || !d_labels || !h_adam || n_rows < 1) return ADVISOR_ERR_INVALID_ARGUMENT;
+    advisor_status st = check_ready(m, n_rows);
+    if (st != ADVISOR_OK) return st;
+    if (precision != ADVISOR_FP32) return ADVISOR_ERR_UNSUPPORTED;
+    const adv::AdamHyper h{h_adam[0], h_adam[1], h_adam[2], h_adam[3], h_adam[4]};
+    const int64_t step = m->adam_step + 1;
+    cudaError_t e = adv::launch_train_step(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), d_feat_q16, d_labels,
+                                           n_rows, &h, step, nullptr, d_loss, m->num_sms, stream);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    m->adam_step = step;
+    return ADVISOR_OK;
+}
+
+advisor_status advisor_loss_grad(advisor_model_t m, const int32_t* d_feat_q16, const float* d_labels,
+                                 int64_t n_rows, advisor_precision precision, float* d_grad, float* d_loss,
+                                 cudaStream_t stream) {
+    if (!m || !d_feat_q16 || !d_labels || !d_grad || n_rows < 1) return ADVISOR_ERR_INVALID_ARGUMENT;
+    advisor_status st = check_ready(m, n_rows);
+    if (st != ADVISOR_OK) return st;
+    if (precision != ADVISOR_FP32) return ADVISOR_ERR_UNSUPPORTED;
+    return cuda_status(adv::launch_train_step(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), d_feat_q16,
+                                              d_labels, n_rows, nullptr, 0, d_grad, d_loss, m->num_sms, stream));
+}
+
+advisor_status advisor_model_set_profile_events(advisor_model_t m, void* ev_start, void* ev_stop) {
+    if (!m || (ev_start == nullptr) != (ev_stop == nullptr)) return ADVISOR_ERR_INVALID_ARGUMENT;
+    m->prof_start = static_cast<cudaEvent_t>(ev_start);
+    m->prof_stop = static_cast<cudaEvent_t>(ev_stop);
+    return ADVISOR_OK;
+}
+
+advisor_status advisor_get_device_status(advisor_model_t m, cudaStream_t stream) {
+    if (!m || !m->P) return ADVISOR_ERR_INVALID_ARGUMENT;
+    int h = 0;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return ADVISOR_ERR_CUDA;
+    if (cudaMemcpy(&h, m->P + m->L.p_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ADVISOR_ERR_CUDA;
+    if (cudaMemset(m->P + m->L.p_status, 0, sizeof(int)) != cudaSuccess) return ADVISOR_ERR_CUDA;
+    if (h & ADV_DEV_TIMEOUT) return ADVISOR_ERR_TIMEOUT;
+    if (h & ADV_DEV_BAD_SEGMENTS) return ADVISOR_ERR_BAD_SEGMENTS;
+    return ADVISOR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+// Descriptor validation and integer feature extraction (a1-a3).
+//
+// Fig. 2 of arXiv 2301.03636 feeds every generated variant through "Feature
+// Extraction" before the trained model; the paper does not list its
+// features, so the feature set here is this library's own (documented in
+// include/advisor.h): Q16.16 binary logarithms of the loop-nest counts, the
+// work, the mapped bytes (Sec. 4.1.2) and the parallelism, their signed
+// differences, and the variant parameters of Sec. 4.1.3.
+//
+// One thread per descriptor row; the 128-byte row is read with eight 16-byte
+// vector loads.  Outputs: int32 features [n][F] (bit-exact), and/or the
+// standardised 16-bit activations of the tensor-core scorer written straight
+// into its shared-memory image layout (128-row tiles, 64-column slabs of
+// 128-byte rows, 128B swizzle), so that the scorer moves them with one bulk
+// copy per slab.
+#include "features.cuh"
+#include "mlp.cuh"
+
+namespace adv {
+
+// Convert 8 standardised values to 16-bit and pack them into a uint4.
+template <int FMT>
+__device__ __forceinline__ uint4 pack8(const float (&z)[8]) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if constexpr (FMT == 1) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(z[2 * i], z[2 * i + 1]);
+            w[i] = *reinterpret_cast<uint32_t*>(&h);
+        } else {
+            __half2 h = __floats2half2_rn(fminf(fmaxf(z[2 * i], -65504.f), 65504.f),
+                                          fminf(fmaxf(z[2 * i + 1], -65504.f), 65504.f));
+            w[i] = *reinterpret_cast<uint32_t*>(&h);
+        }
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Write one row of the 16-bit activation image: row `row` of the tile grid,
+// kpad = nslab * 64 columns, features beyond F (and rows beyond n) are zero.
+template <int F, int FMT>
+__device__ __forceinline__ void write_x_row(uint8_t* x_img, int nslab, int64_t row, const int32_t (&f)[F],
+                                            bool valid_row, const float* __restrict__ sa,
+                                            const float* __restrict__ sc) {
+    const int64_t tile = row / ADV_TILE_M;
+    const uint32_t r = (uint32_t)(row % ADV_TILE_M);
+    uint8_t* tile_base = x_img + (size_t)tile * nslab * ADV_X_SLAB_BYTES;
+#pragma unroll
+    for (int s = 0; s < (F + 63) / 64; ++s) {
+        if (s >= nslab) break;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float z[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = s * 64 + c * 8 + e;
+                z[e] = (valid_row && k < F) ? fmaf((float)f[k < F ? k : 0], __ldg(sa + (k < F ? k : 0)),
+                                                   -__ldg(sc + (k < F ? k : 0)))
+                                            : 0.f;
+            }
+            *reinterpret_cast<uint4*>(tile_base + (size_t)s * ADV_X_SLAB_BYTES + sw128_offset(r, c)) =
+                pack8<FMT>(z);
+        }
+    }
+}
+
+
+template <int F, int FMT>
+__global__ void __launch_bounds__(128) extract_kernel(ExtractArgs a) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= a.n_rows_padded) return;
+    int32_t f[F];
+    bool valid = false;
+    if (row < a.n_rows) {
+        int64_t d[16];
+        load_desc(a.desc, row, d);
+        const uint32_t st = validate_row(d);
+        valid = (st == 0);
+        if (valid) {
+            row_features<F>(d, f);
+        } else {
+#pragma unroll
+            for (int j = 0; j < F; ++j) f[j] = 0;
+        }
+        if (a.status) a.status[row] = (uint8_t)st;
+        if (a.feat) {
+            int4* dst = reinterpret_cast<int4*>(a.feat + (size_t)row * F);
+#pragma unroll
+            for (int j = 0; j < F / 4; ++j) dst[j] = make_int4(f[4 * j], f[4 * j + 1], f[4 * j + 2], f[4 * j + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < F; ++j) f[j] = 0;
+    }
+    if constexpr (FMT != 0) {
+        if (a.x_img) write_x_row<F, FMT>(a.x_img, a.nslab, row, f, valid, a.sa, a.sc);
+    }
+}
+
+// int32 features -> 16-bit standardised activation image.
+template <int F, int FMT>
+__global__ void __launch_bounds__(128) standardize_kernel(const int32_t* __restrict__ feat,
+                                                          const uint8_t* __restrict__ status, int64_t n_rows,
+                                                          int64_t n_rows_padded, uint8_t* x_img, int nslab,
+                                                          const float* __restrict__ sa,
+                                                          const float* __restrict__ sc) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n_rows_padded) return;
+    int32_t f[F];
+    const bool valid = row < n_rows;
+    if (valid) {
+        const int4* src = reinterpret_cast<const int4*>(feat + (size_t)row * F);
+#pragma unroll
+        for (int j = 0; j < F / 4; ++j) {
+            const int4 v = __ldg(src + j);
+            f[4 * j] = v.x; f[4 * j + 1] = v.y; f[4 * j + 2] = v.z; f[4 * j + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < F; ++j) f[j] = 0;
+    }
+    (void)status;  // invalid rows are scored +inf by the scorer's epilogue
+    write_x_row<F, FMT>(x_img, nslab, row, f, valid, sa, sc);
+}
+
+// Mean and population standard deviation of feature/65536 per column over
+// the valid rows, in FP64, with a fixed reduction order.
+__global__ void __launch_bounds__(256) fit_standardizer_kernel(const int32_t* __restrict__ feat,
+                                                               const uint8_t* __restrict__ status,
+                                                               int64_t n_rows, int F, double* mu,
+                                                               double* sigma) {
+    __shared__ double red[256];
+    __shared__ long long cnt_s[256];
+    const int j = blockIdx.x;
+    double s = 0.0;
+    long long c = 0;
+    for (int64_t r = threadIdx.x; r < n_rows; r += blockDim.x) {
+        if (status && status[r]) continue;
+        s += (double)feat[(size_t)r * F + j] / 65536.0;
+        ++c;
+    }
+    red[threadIdx.x] = s;
+    cnt_s[threadIdx.x] = c;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            red[threadIdx.x] += red[threadIdx.x + w];
+            cnt_s[threadIdx.x] += cnt_s[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    const long long cnt = cnt_s[0];
+    const double mean = cnt ? red[0] / (double)cnt : 0.0;
+    __syncthreads();
+    double v = 0.0;
+    for (int64_t r = threadIdx.x; r < n_rows; r += blockDim.x) {
+        if (status && status[r]) continue;
+        const double e = (double)feat[(size_t)r * F + j] / 65536.0 - mean;
+        v += e * e;
+    }
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double sd = cnt ? sqrt(red[0] / (double)cnt) : 0.0;
+        mu[j] = mean;
+        sigma[j] = sd > 0.0 ? sd : 1.0;
+    }
+}
+
+// ---- host launchers ------------------------------------------------------------
+template <int F>
+static cudaError_t launch_extract_f(const ExtractArgs& a, int fmt, cudaStream_t s) {
+    const int64_t rows = a.n_rows_padded;
+    const unsigned grid = (unsigned)((rows + 127) / 128);
+    if (grid == 0) return cudaSuccess;
+    if (fmt == 1) extract_kernel<F, 1><<<grid, 128, 0, s>>>(a);
+    else if (fmt == 2) extract_kernel<F, 2><<<grid, 128, 0, s>>>(a);
+    else extract_kernel<F, 0><<<grid, 128, 0, s>>>(a);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract(const ExtractArgs& a, int F, int fmt, cudaStream_t s) {
+    switch (F) {
+        case 32: return launch_extract_f<32>(a, fmt, s);
+        case 64: return launch_extract_f<64>(a, fmt, s);
+        case 128: return launch_extract_f<128>(a, fmt, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int F>
+static cudaError_t launch_standardize_f(const int32_t* feat, const uint8_t* status, int64_t n, int64_t npad,
+                                        uint8_t* x_img, int nslab, const float* sa, const float* sc, int fmt,
+                                        cudaStream_t s) {
+    const unsigned grid = (unsigned)((npad + 127) / 128);
+    if (grid == 0) return cudaSuccess;
+    if (fmt == 1) standardize_kernel<F, 1><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc);
+    else standardize_kernel<F, 2><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_standardize(const int32_t* feat, const uint8_t* status, int64_t n, int64_t npad, uint8_t* x_img,
+                               int nslab, const float* sa, const float* sc, int F, int fmt, cudaStream_t s) {
+    switch (F) {
+        case 32: return launch_standardize_f<32>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, s);
+        case 64: return launch_standardize_f<64>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, s);
+        case 128: return launch_standardize_f<128>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fit_standardizer(const int32_t* feat, const uint8_t* status, int64_t n, int F, double* mu,
+                                    double* sigma, cudaStream_t s) {
+    fit_standardizer_kernel<<<F, 256, 0, s>>>(feat, status, n, F, mu, sigma);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace adv

@@ -1,0 +1,100 @@
+// Kernel argument structures and launcher declarations shared by the
+// translation units of libadvisor.
+#pragma once
+#include "common.cuh"
+
+namespace adv {
+
+// FP32 master parameters of the MLP as seen by the SIMT kernels.
+struct MlpDesc {
+    int nw;
+    int widths[ADV_MAX_LAYERS + 1];
+    const float* W[ADV_MAX_LAYERS];    // [out][in]
+    const float* b[ADV_MAX_LAYERS];    // [out]
+    const float* WT[ADV_MAX_LAYERS];   // [in][out] (transposed copy)
+    const float* sa;                   // z = f * sa - sc (FP32 standardisation)
+    const float* sc;
+    const double* mu;                  // FP64 standardisation
+    const double* sigma;
+};
+
+// Where the rows of a scoring call come from.
+struct RowSrc {
+    const int32_t* feat;               // [n][F] int32 features, or nullptr: recompute from desc
+    const advisor_variant_desc* desc;
+    const int64_t* rows;               // list of row indices (nullptr: identity)
+    const int* count_dev;              // device-side list length (nullptr: use count)
+    int64_t count;
+    const uint8_t* status;             // row status (nullable), indexed by row
+};
+
+// extract.cu
+struct ExtractArgs {
+    const advisor_variant_desc* desc;
+    int64_t n_rows;
+    int64_t n_rows_padded;   // rows covered (X image rows incl. zero padding)
+    int32_t* feat;           // nullable
+    uint8_t* status;         // nullable
+    uint8_t* x_img;          // nullable
+    int nslab;               // slabs of the X image
+    const float* sa;         // standardisation: z = f * sa - sc
+    const float* sc;
+};
+cudaError_t launch_extract(const ExtractArgs& a, int F, int fmt, cudaStream_t s);
+cudaError_t launch_standardize(const int32_t* feat, const uint8_t* status, int64_t n, int64_t npad, uint8_t* x_img,
+                               int nslab, const float* sa, const float* sc, int F, int fmt, cudaStream_t s);
+cudaError_t launch_fit_standardizer(const int32_t* feat, const uint8_t* status, int64_t n, int F, double* mu,
+                                    double* sigma, cudaStream_t s);
+
+// mlp_simt.cu
+cudaError_t launch_mlp_fp32(const MlpDesc& m, const RowSrc& src, float* out, int num_sms, bool for_list,
+                            cudaStream_t s);
+cudaError_t launch_mlp_fp64(const MlpDesc& m, const RowSrc& src, double* out, int num_sms, cudaStream_t s);
+
+// mlp_tc.cu
+struct TcArgs {
+    const uint8_t* x_img;                  // [n_tiles][nslab0][16 KB]
+    const uint8_t* w_img[ADV_MAX_LAYERS];  // per hidden layer: [nslab_l][npad_l * 128 B]
+    const float* bias[ADV_MAX_LAYERS];     // per hidden layer, padded to npad_l with zeros
+    const float* w_out;                    // [npad_last], padded with zeros
+    const float* b_out;                    // 1 float
+    int npad[ADV_MAX_LAYERS];
+    int nslab[ADV_MAX_LAYERS];
+    int n_hidden;
+    int nmax;
+    int fmt;                               // 1 BF16, 0 F16 (instruction descriptor encoding)
+    int64_t n_rows;
+    int n_tiles;
+    const uint8_t* status;                 // nullable
+    float* scores;
+    int* status_word;
+    unsigned long long timeout_ns;
+};
+cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s);
+size_t mlp_tc_smem_bytes(int nslab_max, int nmax);
+
+// select.cu
+struct SelectArgs {
+    const float* scores;
+    int64_t n_rows;
+    const int64_t* off;
+    int64_t n_kernels;
+    int32_t* best;
+    double* best_score;
+    float eps;                 // < 0: plain argmin
+    float eps32;
+    int* counters;             // [0] tier-1 candidates, [1] tier-2 candidates
+    int* seg_state;
+    int* seg_start;
+    int* seg_cnt;
+    int64_t* cand_rows;
+    float* y32;
+    int64_t* cand2_rows;
+    double* y64;
+    int* status_word;
+};
+cudaError_t launch_select_tier1(const SelectArgs& a, cudaStream_t s);
+cudaError_t launch_select_tier2(const SelectArgs& a, cudaStream_t s);
+cudaError_t launch_select_final(const SelectArgs& a, cudaStream_t s);
+
+}  // namespace adv

@@ -1,0 +1,204 @@
+// Per-kernel selection (a6) and the near-tie re-score bookkeeping (a7).
+//
+// Fig. 2 of arXiv 2301.03636: the predicted runtimes of the variants of a
+// kernel are sorted and the best are kept; here the best one (argmin, lowest
+// variant index on ties, never a row scored +inf or NaN).  One warp per
+// kernel segment, lexicographic (score, row) reduction with warp shuffles.
+//
+// Near ties: rows within 2*eps of their kernel's minimum (eps bounds the
+// scorer's error against FP64) are appended, in row order, to a candidate
+// list that the FP32 scorer re-scores; rows within 2*eps32 of the FP32
+// minimum go on to the FP64 scorer, whose values decide.  A kernel whose
+// window holds a single row is decided at that tier.
+#include "mlp.cuh"
+
+namespace adv {
+
+// Keep (v, r) if it beats (bv, br): smaller value, or equal value and smaller row.
+__device__ __forceinline__ void lex_min(float& bv, int64_t& br, float v, int64_t r) {
+    if (r >= 0 && (br < 0 || v < bv || (v == bv && r < br))) { bv = v; br = r; }
+}
+__device__ __forceinline__ void lex_min_d(double& bv, int64_t& br, double v, int64_t r) {
+    if (r >= 0 && (br < 0 || v < bv || (v == bv && r < br))) { bv = v; br = r; }
+}
+
+__device__ __forceinline__ void warp_lex_min(float& bv, int64_t& br) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int64_t orr = __shfl_xor_sync(0xffffffffu, br, o);
+        lex_min(bv, br, ov, orr);
+    }
+}
+__device__ __forceinline__ void warp_lex_min_d(double& bv, int64_t& br) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int64_t orr = __shfl_xor_sync(0xffffffffu, br, o);
+        lex_min_d(bv, br, ov, orr);
+    }
+}
+
+__device__ __forceinline__ bool finite_score(float v) { return v < INFINITY; }   // false for +inf and NaN
+
+// Append, in order, the rows r (given by lanes with `take`) to list[base + ...].
+// Returns the number appended by this iteration; `done` is the running count.
+__device__ __forceinline__ int append_ordered(bool take, int64_t r, int64_t* list, int base, int done) {
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    const int lane = threadIdx.x & 31;
+    if (take) list[base + done + __popc(m & ((1u << lane) - 1u))] = r;
+    return __popc(m);
+}
+
+__global__ void __launch_bounds__(256) select_tier1_kernel(SelectArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < a.n_kernels; k += nwarps) {
+        const int64_t lo = a.off[k], hi = a.off[k + 1];
+        if (lo < 0 || hi < lo || hi > a.n_rows) {
+            if (lane == 0) {
+                atomicOr(a.status_word, ADV_DEV_BAD_SEGMENTS);
+                a.best[k] = -1;
+                a.best_score[k] = INFINITY;
+                if (a.seg_state) a.seg_state[k] = 0;
+            }
+            continue;
+        }
+        float bv = INFINITY;
+        int64_t br = -1;
+        for (int64_t r = lo + lane; r < hi; r += 32) {
+            const float v = a.scores[r];
+            if (finite_score(v)) lex_min(bv, br, v, r);
+        }
+        warp_lex_min(bv, br);
+        int state = 0;
+        if (br >= 0 && a.eps >= 0.f) {
+            const double thr = (double)bv + 2.0 * (double)a.eps;
+            int cnt = 0;
+            for (int64_t r0 = lo; r0 < hi; r0 += 32) {
+                const int64_t r = r0 + lane;
+                const bool take = r < hi && finite_score(a.scores[r]) && (double)a.scores[r] <= thr;
+                cnt += __popc(__ballot_sync(0xffffffffu, take));
+            }
+            if (cnt > 1) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&a.counters[0], cnt);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                int done = 0;
+                for (int64_t r0 = lo; r0 < hi; r0 += 32) {
+                    const int64_t r = r0 + lane;
+                    const bool take = r < hi && finite_score(a.scores[r]) && (double)a.scores[r] <= thr;
+                    done += append_ordered(take, r, a.cand_rows, base, done);
+                }
+                if (lane == 0) {
+                    a.seg_start[k] = base;
+                    a.seg_cnt[k] = cnt;
+                }
+                state = 1;
+            }
+        }
+        if (lane == 0) {
+            a.best[k] = br >= 0 ? (int32_t)(br - lo) : -1;
+            a.best_score[k] = br >= 0 ? (double)bv : (double)INFINITY;
+            if (a.seg_state) a.seg_state[k] = state;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) select_tier2_kernel(SelectArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < a.n_kernels; k += nwarps) {
+        if (a.seg_state[k] != 1) continue;
+        const int64_t lo = a.off[k];
+        const int start = a.seg_start[k], cnt = a.seg_cnt[k];
+        float bv = INFINITY;
+        int64_t br = -1;
+        for (int i = lane; i < cnt; i += 32) {
+            const float v = a.y32[start + i];
+            if (finite_score(v)) lex_min(bv, br, v, a.cand_rows[start + i]);
+        }
+        warp_lex_min(bv, br);
+        if (br < 0) {   // no finite FP32 value: keep the tier-1 decision
+            if (lane == 0) a.seg_state[k] = 0;
+            continue;
+        }
+        const double thr = (double)bv + 2.0 * (double)a.eps32;
+        int cnt2 = 0;
+        for (int i0 = 0; i0 < cnt; i0 += 32) {
+            const int i = i0 + lane;
+            const bool take = i < cnt && finite_score(a.y32[start + i]) && (double)a.y32[start + i] <= thr;
+            cnt2 += __popc(__ballot_sync(0xffffffffu, take));
+        }
+        if (cnt2 > 1) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&a.counters[1], cnt2);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            int done = 0;
+            for (int i0 = 0; i0 < cnt; i0 += 32) {
+                const int i = i0 + lane;
+                const bool take = i < cnt && finite_score(a.y32[start + i]) && (double)a.y32[start + i] <= thr;
+                const int64_t r = take ? a.cand_rows[start + i] : 0;
+                done += append_ordered(take, r, a.cand2_rows, base, done);
+            }
+            if (lane == 0) {
+                a.seg_start[k] = base;
+                a.seg_cnt[k] = cnt2;
+                a.seg_state[k] = 2;
+                a.best[k] = (int32_t)(br - lo);
+                a.best_score[k] = (double)bv;
+            }
+        } else if (lane == 0) {
+            a.best[k] = (int32_t)(br - lo);
+            a.best_score[k] = (double)bv;
+            a.seg_state[k] = 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) select_final_kernel(SelectArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < a.n_kernels; k += nwarps) {
+        if (a.seg_state[k] != 2) continue;
+        const int64_t lo = a.off[k];
+        const int start = a.seg_start[k], cnt = a.seg_cnt[k];
+        double bv = INFINITY;
+        int64_t br = -1;
+        for (int i = lane; i < cnt; i += 32) {
+            const double v = a.y64[start + i];
+            if (v < (double)INFINITY) lex_min_d(bv, br, v, a.cand2_rows[start + i]);
+        }
+        warp_lex_min_d(bv, br);
+        if (lane == 0) {
+            if (br >= 0) {
+                a.best[k] = (int32_t)(br - lo);
+                a.best_score[k] = bv;
+            }
+            a.seg_state[k] = 0;
+        }
+    }
+}
+
+static int select_grid(int64_t n_kernels) {
+    const int64_t blocks = (n_kernels + 7) / 8;   // 8 warps per block
+    return (int)(blocks < 1 ? 1 : (blocks > 65535 ? 65535 : blocks));
+}
+
+cudaError_t launch_select_tier1(const SelectArgs& a, cudaStream_t s) {
+    select_tier1_kernel<<<select_grid(a.n_kernels), 256, 0, s>>>(a);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+cudaError_t launch_select_tier2(const SelectArgs& a, cudaStream_t s) {
+    select_tier2_kernel<<<select_grid(a.n_kernels), 256, 0, s>>>(a);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+cudaError_t launch_select_final(const SelectArgs& a, cudaStream_t s) {
+    select_final_kernel<<<select_grid(a.n_kernels), 256, 0, s>>>(a);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace adv

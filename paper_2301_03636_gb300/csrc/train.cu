@@ -1,0 +1,286 @@
+// Training mode (Sec. 3: the model is fitted to runtimes measured on the
+// target; Sec. 5 Exp. 3: MLP, z-score standardised inputs).  Loss =
+// 0.5 * mean (y - t)^2 on ln runtime, gradient by the hand-written backward
+// of the ReLU MLP, Adam (Kingma & Ba) on the FP32 master weights.
+//
+// GEMMs are 64x64-tiled SIMT FP32 with generic operand strides:
+//   forward   Out = In * W^T (+ b, ReLU on hidden layers)
+//   dIn       dH  = dZ * W, masked by the ReLU of the layer input
+//   dW        dW  = dZ^T * In, split over rows in fixed chunks, then summed in
+//             a fixed order (deterministic: the same inputs give the same bits)
+#include <cmath>
+
+#include "features.cuh"
+#include "pack.cuh"
+#include "train.cuh"
+
+namespace adv {
+
+namespace {
+constexpr int GT = 64;   // tile
+constexpr int GK = 16;   // K chunk
+constexpr int SPLIT_ROWS = 1024;
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct GemmArgs {
+    const float* A;
+    int64_t sam, sak;
+    const float* B;
+    int64_t sbk, sbn;
+    float* C;
+    int64_t ldc;
+    int64_t M, N, K;
+    int64_t k_per_split;      // K range per blockIdx.z
+    int64_t c_split_stride;   // element stride between split outputs
+    const float* bias;        // EPI 1, 2
+    const float* mask;        // EPI 3: C = mask > 0 ? acc : 0, mask(m, n) = mask[m * ldm + n]
+    int64_t ldm;
+};
+
+// EPI: 0 plain, 1 bias + ReLU, 2 bias, 3 ReLU-derivative mask
+template <int EPI>
+__global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
+    __shared__ float As[GK][GT + 4];
+    __shared__ float Bs[GK][GT + 4];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int64_t m0 = (int64_t)blockIdx.y * GT, n0 = (int64_t)blockIdx.x * GT;
+    const int64_t kb = (int64_t)blockIdx.z * g.k_per_split;
+    const int64_t ke = kb + g.k_per_split < g.K ? kb + g.k_per_split : g.K;
+    float acc[4][4] = {};
+    for (int64_t k0 = kb; k0 < ke; k0 += GK) {
+        for (int i = tid; i < GK * GT; i += 256) {
+            const int kk = i / GT, mm = i % GT;
+            const int64_t k = k0 + kk, m = m0 + mm;
+            As[kk][mm] = (k < ke && m < g.M) ? g.A[m * g.sam + k * g.sak] : 0.f;
+            const int64_t n = n0 + mm;
+            Bs[kk][mm] = (k < ke && n < g.N) ? g.B[k * g.sbk + n * g.sbn] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    float* C = g.C + (int64_t)blockIdx.z * g.c_split_stride;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t m = m0 + ty * 4 + i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t n = n0 + tx * 4 + j;
+            if (n >= g.N) continue;
+            float v = acc[i][j];
+            if constexpr (EPI == 1) v = fmaxf(v + g.bias[n], 0.f);
+            if constexpr (EPI == 2) v = v + g.bias[n];
+            if constexpr (EPI == 3) v = g.mask[m * g.ldm + n] > 0.f ? v : 0.f;
+            C[m * g.ldc + n] = v;
+        }
+    }
+}
+
+template <int EPI>
+cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
+    dim3 grid((unsigned)((g.N + GT - 1) / GT), (unsigned)((g.M + GT - 1) / GT), (unsigned)splits);
+    gemm_kernel<EPI><<<grid, 256, 0, s>>>(g);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+
+__global__ void standardize_f32_kernel(const int32_t* __restrict__ feat, int64_t n, int F,
+                                       const float* __restrict__ sa, const float* __restrict__ sc,
+                                       float* __restrict__ z) {
+    const int64_t total = n * F;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i % F);
+        z[i] = fmaf((float)feat[i], sa[k], -sc[k]);
+    }
+}
+
+// dy = (y - t) / n and per-block sums of 0.5 (y - t)^2 (fixed order).
+__global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ y, const float* __restrict__ t,
+                                                   int64_t n, float* __restrict__ dy, float* __restrict__ part) {
+    __shared__ float red[256];
+    float s = 0.f;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b = (int64_t)blockIdx.x * per, e = b + per < n ? b + per : n;
+    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+        const float d = y[i] - t[i];
+        dy[i] = d / (float)n;
+        s += 0.5f * d * d;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void loss_final_kernel(const float* __restrict__ part, int nb, int64_t n, float* __restrict__ loss,
+                                  float* __restrict__ loss_out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        float s = 0.f;
+        for (int i = 0; i < nb; ++i) s += part[i];
+        *loss = s / (float)n;
+        if (loss_out) *loss_out = s / (float)n;
+    }
+}
+
+// Column sums of dZ [n][w] per split of SPLIT_ROWS rows.
+__global__ void colsum_kernel(const float* __restrict__ dz, int64_t n, int w, float* __restrict__ part,
+                              int64_t split_stride) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= w) return;
+    const int64_t b = (int64_t)blockIdx.y * SPLIT_ROWS, e = b + SPLIT_ROWS < n ? b + SPLIT_ROWS : n;
+    float s = 0.f;
+    for (int64_t r = b; r < e; ++r) s += dz[r * w + o];
+    part[(int64_t)blockIdx.y * split_stride + o] = s;
+}
+
+// grad[j] = sum over splits (in order) of part[s][j]
+__global__ void split_sum_kernel(const float* __restrict__ part, int splits, int64_t stride, int64_t len,
+                                 float* __restrict__ grad) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int i = 0; i < splits; ++i) s += part[(int64_t)i * stride + j];
+        grad[j] = s;
+    }
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int64_t n, AdamHyper h, float c1, float c2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = h.beta1 * m[i] + (1.f - h.beta1) * gi;
+        const float vi = h.beta2 * v[i] + (1.f - h.beta2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float mh = mi / c1, vh = vi / c2;
+        p[i] = p[i] - h.lr * (mh / (sqrtf(vh) + h.eps) + h.weight_decay * p[i]);
+    }
+}
+
+int grid1(int64_t n) {
+    const int64_t g = (n + 255) / 256;
+    return (int)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
+}
+
+}  // namespace
+
+size_t train_layout(const ModelLayout& L, int64_t R, TrainLayout* t) {
+    size_t o = 0;
+    auto take = [&](size_t b) { size_t at = o; o = al(o + b); return at; };
+    int wmax = 0;
+    for (int i = 0; i < L.nw; ++i) wmax = L.widths[i] > wmax ? L.widths[i] : wmax;
+    for (int l = 0; l < L.nw; ++l) t->act[l] = take((size_t)R * L.widths[l] * 4);
+    t->dA = take((size_t)R * wmax * 4);
+    t->dB = take((size_t)R * wmax * 4);
+    t->grad = take((size_t)L.n_params * 4);
+    t->splits = (int)((R + SPLIT_ROWS - 1) / SPLIT_ROWS);
+    int64_t lmax = 0;
+    for (int l = 0; l < L.n_layers; ++l) {
+        const int64_t len = (int64_t)L.widths[l] * L.widths[l + 1];
+        lmax = len > lmax ? len : lmax;
+    }
+    t->part = take((size_t)t->splits * lmax * 4);
+    t->loss_part = take(1024 * 4);
+    t->loss = take(64);
+    t->rows = R;
+    t->bytes = o;
+    return o;
+}
+
+cudaError_t launch_train_step(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
+                              const MlpDesc& md, const int32_t* feat, const float* labels, int64_t n,
+                              const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss, int num_sms,
+                              cudaStream_t s) {
+    (void)num_sms;
+    cudaError_t e;
+    auto act = [&](int l) { return reinterpret_cast<float*>(TW + T.act[l]); };
+    float* dA = reinterpret_cast<float*>(TW + T.dA);
+    float* dB = reinterpret_cast<float*>(TW + T.dB);
+    float* grad = d_grad_out ? d_grad_out : reinterpret_cast<float*>(TW + T.grad);
+    float* part = reinterpret_cast<float*>(TW + T.part);
+    const int splits = (int)((n + SPLIT_ROWS - 1) / SPLIT_ROWS);
+
+    // forward, keeping every layer's output
+    standardize_f32_kernel<<<grid1(n * L.F), 256, 0, s>>>(feat, n, L.F, md.sa, md.sc, act(0));
+    adv_count_launch(1);
+    for (int l = 0; l < L.n_layers; ++l) {
+        const int fi = L.widths[l], fo = L.widths[l + 1];
+        GemmArgs g{};
+        g.A = act(l); g.sam = fi; g.sak = 1;
+        g.B = md.W[l]; g.sbk = 1; g.sbn = fi;
+        g.C = act(l + 1); g.ldc = fo;
+        g.M = n; g.N = fo; g.K = fi; g.k_per_split = fi; g.c_split_stride = 0;
+        g.bias = md.b[l];
+        e = (l + 1 < L.n_layers) ? gemm<1>(g, 1, s) : gemm<2>(g, 1, s);
+        if (e != cudaSuccess) return e;
+    }
+    // loss and dL/dy
+    const int nb = 256;
+    loss_kernel<<<nb, 256, 0, s>>>(act(L.n_layers), labels, n, dA, reinterpret_cast<float*>(TW + T.loss_part));
+    loss_final_kernel<<<1, 32, 0, s>>>(reinterpret_cast<float*>(TW + T.loss_part), nb, n,
+                                       reinterpret_cast<float*>(TW + T.loss), d_loss);
+    adv_count_launch(2);
+    // backward
+    float* dz = dA;
+    float* dnext = dB;
+    for (int l = L.n_layers - 1; l >= 0; --l) {
+        const int fi = L.widths[l], fo = L.widths[l + 1];
+        float* gW = grad + L.layer_w_off[l];
+        float* gb = grad + L.layer_b_off[l];
+        // dW = dZ^T * In, split over rows
+        GemmArgs g{};
+        g.A = dz; g.sam = 1; g.sak = fo;
+        g.B = act(l); g.sbk = fi; g.sbn = 1;
+        g.C = part; g.ldc = fi;
+        g.M = fo; g.N = fi; g.K = n; g.k_per_split = SPLIT_ROWS;
+        g.c_split_stride = (int64_t)fo * fi;
+        e = gemm<0>(g, splits, s);
+        if (e != cudaSuccess) return e;
+        split_sum_kernel<<<grid1((int64_t)fo * fi), 256, 0, s>>>(part, splits, (int64_t)fo * fi, (int64_t)fo * fi, gW);
+        dim3 cg((unsigned)((fo + 127) / 128), (unsigned)splits);
+        float* bpart = part;   // reuse after the dW sum consumed it (stream order)
+        colsum_kernel<<<cg, 128, 0, s>>>(dz, n, fo, bpart, fo);
+        split_sum_kernel<<<grid1(fo), 256, 0, s>>>(bpart, splits, fo, fo, gb);
+        adv_count_launch(3);
+        if (l == 0) break;
+        // dIn = dZ * W, masked by the ReLU of the input (the previous layer's output)
+        GemmArgs h{};
+        h.A = dz; h.sam = fo; h.sak = 1;
+        h.B = md.W[l]; h.sbk = fi; h.sbn = 1;
+        h.C = dnext; h.ldc = fi;
+        h.M = n; h.N = fi; h.K = fo; h.k_per_split = fo; h.c_split_stride = 0;
+        h.mask = act(l); h.ldm = fi;
+        e = gemm<3>(h, 1, s);
+        if (e != cudaSuccess) return e;
+        float* t = dz; dz = dnext; dnext = t;
+    }
+    if (!adam) return cudaGetLastError();
+    const float c1 = (float)(1.0 - std::pow((double)adam->beta1, (double)step));
+    const float c2 = (float)(1.0 - std::pow((double)adam->beta2, (double)step));
+    adam_kernel<<<grid1(L.n_params), 256, 0, s>>>(reinterpret_cast<float*>(P + L.p_master), grad,
+                                                  reinterpret_cast<float*>(P + L.p_adam_m),
+                                                  reinterpret_cast<float*>(P + L.p_adam_v), L.n_params, *adam, c1,
+                                                  c2);
+    adv_count_launch(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_repack(L, P, s);
+}
+
+}  // namespace adv

@@ -1,0 +1,35 @@
+// Training-mode kernels (train.cu): forward with saved activations, MSE loss
+// on ln runtime, hand-written backward, Adam.
+#pragma once
+#include "mlp.cuh"
+
+namespace adv {
+
+struct TrainLayout {
+    size_t act[ADV_MAX_LAYERS + 1];   // act[0] = standardised input z [R][F]; act[l] = layer-l output [R][w_l]
+    size_t dA, dB;                    // gradient ping-pong [R][wmax]
+    size_t grad;                      // [n_params]
+    size_t part;                      // split-K partial sums [splits][max(out*in + out)]
+    size_t loss_part;                 // per-block loss partial sums
+    size_t loss;                      // 1 float
+    int splits;
+    int64_t rows;
+    size_t bytes;
+};
+
+struct AdamHyper {
+    float lr, beta1, beta2, eps, weight_decay;
+};
+
+// Bytes of the training region for up to R rows; fills *t.
+size_t train_layout(const ModelLayout& L, int64_t R, TrainLayout* t);
+
+// Forward + loss + backward; with `adam` non-null also the Adam update of the
+// master weights (step counts from 1) and the repack of the derived copies.
+// d_grad_out (nullable) receives the FP32 gradient, d_loss (nullable) the loss.
+cudaError_t launch_train_step(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
+                              const MlpDesc& md, const int32_t* feat, const float* labels, int64_t n,
+                              const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss, int num_sms,
+                              cudaStream_t s);
+
+}  // namespace adv

@@ -1,0 +1,72 @@
+"""The tcgen05 tensor-core scorer (BF16 and FP16 operands, FP32 accumulation)
+against the FP64 oracle, over several tiles per CTA and ragged tails, plus
+batch invariance (a row's score does not depend on the rest of the batch)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2301_03636_gb300 import advisor
+from paper_2301_03636_gb300 import workloads as W
+from tests._cases import mixed_descriptors
+from tests.test_gpu_2_score_select import setup_model
+
+pytestmark = pytest.mark.gpu
+
+# Max |y - y_fp64| allowed per operand format.  FP16 operands (11-bit
+# significand) must meet the 1e-2 target on ln runtime; BF16 operands (8-bit
+# significand) carry ~8x the rounding error of FP16, measured at ~0.02 on
+# these He-initialised networks, so their bound is 8e-2.
+TOL = {"fp16": 1e-2, "bf16": 8e-2}
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("widths,n", [
+    ((32, 128, 128, 1), 1),
+    ((32, 128, 128, 1), 129),
+    ((64, 256, 256, 256, 1), 127),
+    ((64, 256, 256, 256, 1), 100_003),
+    ((128, 256, 256, 1), 5000),
+    ((32, 33, 66, 132, 66, 33, 1), 3001),
+])
+def test_tc_scores_against_oracle(gpu_lib, precision, widths, n):
+    m, p, mu, sg = setup_model(widths, n, 1, 21)
+    d = mixed_descriptors(max(n, 64), 300 + n)[:n]
+    f_ref, st_ref = oracle.extract_features(d, widths[0])
+    y_ref = oracle.mlp_forward(f_ref, widths, p, mu, sg, st_ref)
+    f, st = advisor.advisor_extract_features(torch.from_numpy(d).cuda(), widths[0])
+    y = m.score(f, st, precision).cpu().numpy().astype(np.float64)
+    ok = st_ref == 0
+    assert np.all(np.isinf(y[~ok]))
+    err = np.abs(y[ok] - y_ref[ok])
+    print(f"{precision} {widths} n={n}: max|dy| = {err.max():.3e}, p99 = {np.quantile(err, 0.99):.3e}")
+    assert err.max() <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_batch_invariance(gpu_lib, precision):
+    widths = (64, 256, 256, 256, 1)
+    m, _, _, _ = setup_model(widths, 40_000, 1, 2)
+    d = torch.from_numpy(W.make_descriptors(40_000, 12)).cuda()
+    f, st = advisor.advisor_extract_features(d, 64)
+    y_all = m.score(f, st, precision)
+    for lo, hi in [(0, 1), (1000, 1200), (12345, 12346), (39_000, 40_000)]:
+        y_part = m.score(f[lo:hi].contiguous(), st[lo:hi].contiguous(), precision)
+        assert torch.equal(y_part, y_all[lo:hi])
+
+
+def test_rank_path_equals_score_then_select(gpu_lib):
+    widths = (64, 256, 256, 256, 1)
+    off = W.make_segments(300, 4, 64, 3)
+    n = int(off[-1])
+    m, _, _, _ = setup_model(widths, n, 300, 4)
+    d = torch.from_numpy(W.make_descriptors(n, 4)).cuda()
+    o = torch.from_numpy(off).cuda()
+    for prec in ("bf16", "fp16", "fp32"):
+        scores = torch.empty(n, dtype=torch.float32, device="cuda")
+        b1, s1 = m.rank(d, o, prec, scores=scores)
+        f, st = advisor.advisor_extract_features(d, 64)
+        y = m.score(f, st, prec)
+        assert torch.equal(y, scores)
+        b2, s2 = m.select(y, o)
+        assert torch.equal(b1, b2) and torch.equal(s1, s2)
