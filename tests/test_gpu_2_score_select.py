@@ -49,13 +49,13 @@ def _segments(n_kernels, lo, hi, seed):
 
 
 def test_select_plain_argmin_matches_oracle(gpu_lib):
-    m, p, mu, sg = setup_model((32, 128, 128, 1), 4000, 300, 3)
     rng = np.random.Generator(np.random.PCG64(2))
     counts = rng.integers(0, 30, size=300)
     counts[[0, 5, 17]] = 0
     counts[[1, 9]] = 1
     off = W.counts_to_offsets(counts)
     n = int(off[-1])
+    m, p, mu, sg = setup_model((32, 128, 128, 1), n, 300, 3)
     y = rng.integers(-3, 4, size=n).astype(np.float32)  # many exact ties
     y[rng.choice(n, 40, replace=False)] = np.inf
     y[rng.choice(n, 10, replace=False)] = np.nan
