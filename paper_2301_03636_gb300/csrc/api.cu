@@ -82,6 +82,7 @@ adv::MlpDesc mlp_desc(const advisor_model* m) {
         d.W[l] = master + L.layer_w_off[l];
         d.b[l] = master + L.layer_b_off[l];
         d.WT[l] = reinterpret_cast<const float*>(m->P + L.p_wT[l]);
+        d.wt_ld[l] = (L.widths[l + 1] + 3) / 4 * 4;
     }
     d.sa = reinterpret_cast<const float*>(m->P + L.p_stdz_a);
     d.sc = reinterpret_cast<const float*>(m->P + L.p_stdz_c);
@@ -122,7 +123,7 @@ bool tc_supported(const advisor_model* m) {
     if (!L.tc_ok) return false;
     int nslab_max = 1;
     for (int l = 0; l < L.n_hidden; ++l) nslab_max = L.nslab[l] > nslab_max ? L.nslab[l] : nslab_max;
-    return adv::mlp_tc_smem_bytes(nslab_max, L.nmax) <= 232448;
+    return adv::mlp_tc_smem_bytes(nslab_max, L.nmax, L.n_hidden) <= 232448;
 }
 
 advisor_status check_ready(const advisor_model* m, int64_t n_rows) {
@@ -176,7 +177,7 @@ advisor_status do_select(advisor_model* m, const float* scores, int64_t n_rows, 
     r1.rows = a.cand_rows;
     r1.count_dev = &a.counters[0];
     r1.count = 0;
-    e = adv::launch_mlp_fp32(md, r1, a.y32, m->num_sms, true, s);
+    e = adv::launch_mlp_fp32(md, r1, a.y32, m->num_sms, true, s, a.status_word);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     e = adv::launch_select_tier2(a, s);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
@@ -244,7 +245,7 @@ advisor_status advisor_model_create(const int32_t* h_widths, int32_t n_widths, a
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
     L.p_master = take((size_t)L.n_params * 4);
-    for (int l = 0; l < L.n_layers; ++l) L.p_wT[l] = take((size_t)L.widths[l] * L.widths[l + 1] * 4);
+    for (int l = 0; l < L.n_layers; ++l) L.p_wT[l] = take((size_t)L.widths[l] * ((L.widths[l + 1] + 3) / 4 * 4) * 4);
     for (int l = 0; l < L.n_hidden; ++l) {
         L.p_w16[0][l] = take((size_t)L.npad[l] * L.kpad[l] * 2);
         L.p_w16[1][l] = take((size_t)L.npad[l] * L.kpad[l] * 2);

@@ -75,6 +75,34 @@ __device__ __forceinline__ uint32_t validate_row(const int64_t (&d)[16]) {
     return st;
 }
 
+// Binary logarithms of N values at once: the same digit-by-digit method as
+// log2_q16, with the N squaring chains advanced in lockstep so that their
+// multiplies overlap instead of waiting on each other.
+template <int N>
+__device__ __forceinline__ void log2_q16_batch(const uint64_t (&x)[N], int32_t (&out)[N]) {
+    uint32_t m[N], acc[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const uint64_t v = x[i] ? x[i] : 1;               // L(0) = L(1) = 0
+        const int k = 63 - __clzll((long long)v);
+        m[i] = (k >= 31) ? (uint32_t)(v >> (k - 31)) : (uint32_t)(v << (31 - k));
+        acc[i] = (uint32_t)k;                              // the 16 fraction bits are shifted in below
+    }
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const uint64_t sq = (uint64_t)m[i] * (uint64_t)m[i];
+            const uint32_t hi = (uint32_t)(sq >> 32);
+            const uint32_t bit = hi >> 31;
+            m[i] = bit ? hi : (uint32_t)(sq >> 31);
+            acc[i] = (acc[i] << 1) | bit;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = (int32_t)acc[i];
+}
+
 // The F features of a valid row (F = 32, 64 or 128).
 template <int F>
 __device__ __forceinline__ void row_features(const int64_t (&d)[16], int32_t (&f)[F]) {
@@ -87,8 +115,7 @@ __device__ __forceinline__ void row_features(const int64_t (&d)[16], int32_t (&f
     const int pf = (int)d[11], dc = (int)d[12], pc = (int)d[13], sched = (int)d[14], dmode = (int)d[15];
 
     const uint64_t T = t[0] * t[1] * t[2] * t[3];
-    const uint64_t work_f = T * flops, work_b = T * bytes;
-    const uint64_t mapped = h2d + d2h, par = teams * threads;
+    const uint64_t par = teams * threads;
     // 'teams distribute' covers loops [0, n_dist); combined with 'parallel for' when pf == 0
     const int n_dist = (pf == 0) ? pc : dc;
     uint64_t Dp = 1, Qp = 1;
@@ -97,33 +124,51 @@ __device__ __forceinline__ void row_features(const int64_t (&d)[16], int32_t (&f
         if (i < n_dist) Dp *= t[i];
         if (i >= pf && i < pf + pc) Qp *= t[i];
     }
-    const int32_t lT = log2_q16(T), lP = log2_q16(par);
-    const int32_t lWF = log2_q16(work_f), lWB = log2_q16(work_b), lM = log2_q16(mapped);
-    const int32_t lD = log2_q16(Dp), lQ = log2_q16(Qp);
-    const int32_t lTeams = log2_q16(teams), lThreads = log2_q16(threads);
+    // arguments of every logarithm of the base features
+    enum { A_T0 = 0, A_T = 4, A_FL_IT, A_BY_IT, A_WF, A_WB, A_H2D, A_D2H, A_MAP, A_TEAMS, A_THREADS, A_PAR, A_D, A_Q,
+           A_MIN, NA };
+    uint64_t x[NA];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[A_T0 + i] = t[i];
+    x[A_T] = T;
+    x[A_FL_IT] = flops;
+    x[A_BY_IT] = bytes;
+    x[A_WF] = T * flops;
+    x[A_WB] = T * bytes;
+    x[A_H2D] = h2d;
+    x[A_D2H] = d2h;
+    x[A_MAP] = h2d + d2h;
+    x[A_TEAMS] = teams;
+    x[A_THREADS] = threads;
+    x[A_PAR] = par;
+    x[A_D] = Dp;
+    x[A_Q] = Qp;
+    x[A_MIN] = T < par ? T : par;
+    int32_t L[NA];
+    log2_q16_batch<NA>(x, L);
 
     int32_t base[32];
     base[0] = depth * ONE;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) base[1 + i] = log2_q16(t[i]);
-    base[5] = lT;
-    base[6] = log2_q16(flops);
-    base[7] = log2_q16(bytes);
-    base[8] = lWF;
-    base[9] = lWB;
-    base[10] = log2_q16(h2d);
-    base[11] = log2_q16(d2h);
-    base[12] = lM;
-    base[13] = lTeams;
-    base[14] = lThreads;
-    base[15] = lP;
-    base[16] = lD;
-    base[17] = lQ;
-    base[18] = max(lT - lP, 0);
-    base[19] = max(lD - lTeams, 0);
-    base[20] = max(lQ - lThreads, 0);
-    base[21] = lWF - lWB;
-    base[22] = lWB - lM;
+    for (int i = 0; i < 4; ++i) base[1 + i] = L[A_T0 + i];
+    base[5] = L[A_T];
+    base[6] = L[A_FL_IT];
+    base[7] = L[A_BY_IT];
+    base[8] = L[A_WF];
+    base[9] = L[A_WB];
+    base[10] = L[A_H2D];
+    base[11] = L[A_D2H];
+    base[12] = L[A_MAP];
+    base[13] = L[A_TEAMS];
+    base[14] = L[A_THREADS];
+    base[15] = L[A_PAR];
+    base[16] = L[A_D];
+    base[17] = L[A_Q];
+    base[18] = max(L[A_T] - L[A_PAR], 0);
+    base[19] = max(L[A_D] - L[A_TEAMS], 0);
+    base[20] = max(L[A_Q] - L[A_THREADS], 0);
+    base[21] = L[A_WF] - L[A_WB];
+    base[22] = L[A_WB] - L[A_MAP];
     base[23] = sched == 0 ? ONE : 0;
     base[24] = sched == 1 ? ONE : 0;
     base[25] = sched == 2 ? ONE : 0;
@@ -132,36 +177,45 @@ __device__ __forceinline__ void row_features(const int64_t (&d)[16], int32_t (&f
     base[28] = dc * ONE;
     base[29] = pc * ONE;
     base[30] = pf == 0 ? ONE : 0;
-    base[31] = log2_q16(T < par ? T : par);
+    base[31] = L[A_MIN];
 #pragma unroll
     for (int j = 0; j < 32; ++j) f[j] = base[j];
     if constexpr (F >= 64) {
         // per loop level: log trip, distributed?, parallel-for?, in a collapse
         // group of >= 2 loops?, log prefix product, log suffix product,
-        // log(trip*bytes/iter), log(trip*flops/iter); zero beyond the depth.
+        // log(trip*bytes/iter), log(trip*flops/iter); zero beyond the depth
+        // (arguments of 1 there give logarithms of 0).
+        uint64_t y[16];
         uint64_t prefix = 1;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int o = 32 + 8 * i;
-            if (i < depth) {
-                prefix *= t[i];
-                uint64_t suffix = 1;
-                for (int j = i; j < depth; ++j) suffix *= t[j];
-                const bool in_dist = i < n_dist;
-                const bool in_pf = (i >= pf) && (i < pf + pc);
-                const bool grouped = (in_dist && n_dist >= 2) || (in_pf && pc >= 2);
-                f[o + 0] = log2_q16(t[i]);
-                f[o + 1] = in_dist ? ONE : 0;
-                f[o + 2] = in_pf ? ONE : 0;
-                f[o + 3] = grouped ? ONE : 0;
-                f[o + 4] = log2_q16(prefix);
-                f[o + 5] = log2_q16(suffix);
-                f[o + 6] = log2_q16(t[i] * bytes);
-                f[o + 7] = log2_q16(t[i] * flops);
-            } else {
+            const bool live = i < depth;
+            prefix *= t[i];
+            uint64_t suffix = 1;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) f[o + j] = 0;
-            }
+            for (int j = i; j < 4; ++j) suffix *= (j < depth) ? t[j] : 1;
+            y[4 * i + 0] = live ? prefix : 1;
+            y[4 * i + 1] = live ? suffix : 1;
+            y[4 * i + 2] = live ? t[i] * bytes : 1;
+            y[4 * i + 3] = live ? t[i] * flops : 1;
+        }
+        int32_t Ly[16];
+        log2_q16_batch<16>(y, Ly);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int o = 32 + 8 * i;
+            const bool live = i < depth;
+            const bool in_dist = live && i < n_dist;
+            const bool in_pf = live && (i >= pf) && (i < pf + pc);
+            const bool grouped = (in_dist && n_dist >= 2) || (in_pf && pc >= 2);
+            f[o + 0] = live ? L[A_T0 + i] : 0;
+            f[o + 1] = in_dist ? ONE : 0;
+            f[o + 2] = in_pf ? ONE : 0;
+            f[o + 3] = grouped ? ONE : 0;
+            f[o + 4] = Ly[4 * i + 0];
+            f[o + 5] = Ly[4 * i + 1];
+            f[o + 6] = Ly[4 * i + 2];
+            f[o + 7] = Ly[4 * i + 3];
         }
     }
     if constexpr (F >= 128) {

@@ -11,7 +11,8 @@ struct MlpDesc {
     int widths[ADV_MAX_LAYERS + 1];
     const float* W[ADV_MAX_LAYERS];    // [out][in]
     const float* b[ADV_MAX_LAYERS];    // [out]
-    const float* WT[ADV_MAX_LAYERS];   // [in][out] (transposed copy)
+    const float* WT[ADV_MAX_LAYERS];   // [in][wt_ld] (transposed copy, rows zero-padded to wt_ld)
+    int wt_ld[ADV_MAX_LAYERS];         // out rounded up to a multiple of 4
     const float* sa;                   // z = f * sa - sc (FP32 standardisation)
     const float* sc;
     const double* mu;                  // FP64 standardisation
@@ -48,7 +49,7 @@ cudaError_t launch_fit_standardizer(const int32_t* feat, const uint8_t* status, 
 
 // mlp_simt.cu
 cudaError_t launch_mlp_fp32(const MlpDesc& m, const RowSrc& src, float* out, int num_sms, bool for_list,
-                            cudaStream_t s);
+                            cudaStream_t s, int* status_word = nullptr);
 cudaError_t launch_mlp_fp64(const MlpDesc& m, const RowSrc& src, double* out, int num_sms, cudaStream_t s);
 
 // mlp_tc.cu
@@ -71,7 +72,7 @@ struct TcArgs {
     unsigned long long timeout_ns;
 };
 cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s);
-size_t mlp_tc_smem_bytes(int nslab_max, int nmax);
+size_t mlp_tc_smem_bytes(int nslab_max, int nmax, int n_hidden);
 
 // select.cu
 struct SelectArgs {

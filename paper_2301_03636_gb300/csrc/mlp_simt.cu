@@ -146,6 +146,144 @@ __global__ void __launch_bounds__(256) mlp_fp32_kernel(MlpDesc m, RowSrc src, fl
     }
 }
 
+// FP32 scorer for short row lists (the near-tie re-score): RB rows per block,
+// one output neuron per thread (up to 4 per thread for widths > 256).  The
+// transposed weights WT[k][j] are streamed through shared memory in chunks of
+// KC rows by 1-D bulk copies (a 3-stage ring, one thread issuing), so that
+// the block never waits on single L2 loads; activations are stored
+// transposed act[k][RB], read as broadcast 16-byte shared loads.
+template <int RB, int JPT, int F, bool FROM_DESC>
+__global__ void __launch_bounds__(256) mlp_fp32_list_kernel(MlpDesc m, RowSrc src, float* __restrict__ out,
+                                                            int wmax4, int kc, int* status_word) {
+    constexpr int STAGES = 3;
+    extern __shared__ __align__(16) float smem_l[];
+    float* h0 = smem_l;                    // [wmax4][RB]
+    float* h1 = h0 + wmax4 * RB;
+    float* wbuf = h1 + wmax4 * RB;         // [STAGES][kc * wmax4]
+    __shared__ uint64_t full[STAGES];
+    __shared__ int row_ok[RB];
+    __shared__ int abort_s;
+    const int tid = threadIdx.x;
+    const int64_t count = src.count_dev ? (int64_t)*src.count_dev : src.count;
+    const int64_t ntiles = (count + RB - 1) / RB;
+    const int nh = m.nw - 2;
+    int nchunks = 0;
+    for (int l = 0; l < nh; ++l) nchunks += (m.widths[l] + kc - 1) / kc;
+    if (tid == 0) {
+        for (int i = 0; i < STAGES; ++i) mbar_init(&full[i], 1);
+        abort_s = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // chunk c of the per-tile stream: layer l, rows k0 .. k0 + nk - 1 of WT[l]
+    auto issue = [&](int c, int stage) {
+        int l = 0, k0 = c * 0;
+        for (l = 0; l < nh; ++l) {
+            const int nc = (m.widths[l] + kc - 1) / kc;
+            if (c < nc) { k0 = c * kc; break; }
+            c -= nc;
+        }
+        const int fi = m.widths[l];
+        const int nk = fi - k0 < kc ? fi - k0 : kc;
+        const uint32_t bytes = (uint32_t)(nk * m.wt_ld[l] * 4);
+        mbar_expect_tx(&full[stage], bytes);
+        bulk_g2s(wbuf + (size_t)stage * kc * wmax4, m.WT[l] + (size_t)k0 * m.wt_ld[l], bytes, &full[stage]);
+    };
+    uint32_t used = 0;   // chunks consumed so far by this block (across tiles)
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        __syncthreads();
+        if (tid == 0)
+            for (int c = 0; c < STAGES && c < nchunks; ++c) issue(c, (int)((used + c) % STAGES));
+        if (tid < RB) {
+            const int64_t pos = tile * RB + tid;
+            int ok = 0;
+            int32_t f[F];
+            if (pos < count) {
+                const int64_t row = src.rows ? src.rows[pos] : pos;
+                ok = fetch_row_features<F, FROM_DESC>(src, row, f) ? 1 : 0;
+            } else {
+#pragma unroll
+                for (int k = 0; k < F; ++k) f[k] = 0;
+            }
+#pragma unroll
+            for (int k = 0; k < F; ++k) h0[k * RB + tid] = fmaf((float)f[k], __ldg(m.sa + k), -__ldg(m.sc + k));
+            row_ok[tid] = ok;
+        }
+        __syncthreads();
+        float* in = h0;
+        float* ob = h1;
+        int c = 0;
+        for (int l = 0; l < nh; ++l) {
+            const int fi = m.widths[l], fo = m.widths[l + 1], ld = m.wt_ld[l];
+            float acc[JPT][RB];
+#pragma unroll
+            for (int jj = 0; jj < JPT; ++jj)
+#pragma unroll
+                for (int r = 0; r < RB; ++r) acc[jj][r] = 0.f;
+            for (int k0 = 0; k0 < fi; k0 += kc, ++c) {
+                const int stage = (int)((used + c) % STAGES);
+                const uint32_t par = ((used + c) / STAGES) & 1u;
+                if (!mbar_wait_bounded(&full[stage], par, status_word, &abort_s, 2000000000ull)) break;
+                const float* wk = wbuf + (size_t)stage * kc * wmax4;
+                const int nk = fi - k0 < kc ? fi - k0 : kc;
+                auto step = [&](int kk) {
+                    const float4* hv = reinterpret_cast<const float4*>(in + (k0 + kk) * RB);
+                    float4 hr[RB / 4];
+#pragma unroll
+                    for (int q = 0; q < RB / 4; ++q) hr[q] = hv[q];
+#pragma unroll
+                    for (int jj = 0; jj < JPT; ++jj) {
+                        const int j = tid + 256 * jj;
+                        const float w = wk[kk * ld + (j < ld ? j : 0)];   // zero beyond fo in the padded copy
+#pragma unroll
+                        for (int q = 0; q < RB / 4; ++q) {
+                            acc[jj][4 * q] = fmaf(hr[q].x, w, acc[jj][4 * q]);
+                            acc[jj][4 * q + 1] = fmaf(hr[q].y, w, acc[jj][4 * q + 1]);
+                            acc[jj][4 * q + 2] = fmaf(hr[q].z, w, acc[jj][4 * q + 2]);
+                            acc[jj][4 * q + 3] = fmaf(hr[q].w, w, acc[jj][4 * q + 3]);
+                        }
+                    }
+                };
+                if (nk == 16) {
+#pragma unroll
+                    for (int kk = 0; kk < 16; ++kk) step(kk);
+                } else {
+                    for (int kk = 0; kk < nk; ++kk) step(kk);
+                }
+                __syncthreads();   // every thread is done with this stage
+                if (tid == 0 && c + STAGES < nchunks) issue(c + STAGES, stage);
+            }
+#pragma unroll
+            for (int jj = 0; jj < JPT; ++jj) {
+                const int j = tid + 256 * jj;
+                if (j < fo) {
+                    const float bb = __ldg(m.b[l] + j);
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) ob[j * RB + r] = fmaxf(acc[jj][r] + bb, 0.f);
+                }
+            }
+            __syncthreads();
+            float* t = in; in = ob; ob = t;
+        }
+        used += (uint32_t)nchunks;
+        {
+            const int fi = m.widths[nh];
+            const float* __restrict__ wl = m.W[nh];
+            const int warp = tid >> 5, lane = tid & 31;
+            for (int r = warp; r < RB; r += 8) {
+                float s = 0.f;
+                for (int k = lane; k < fi; k += 32) s = fmaf(in[k * RB + r], __ldg(wl + k), s);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) {
+                    const int64_t pos = tile * RB + r;
+                    if (pos < count) out[pos] = (row_ok[r] && !abort_s) ? s + __ldg(m.b[nh]) : INFINITY;
+                }
+            }
+        }
+    }
+}
+
 // FP64 reference-order scorer: one block per listed row.
 template <int F, bool FROM_DESC>
 __global__ void __launch_bounds__(256) mlp_fp64_kernel(MlpDesc m, RowSrc src, double* __restrict__ out, int wmax) {
@@ -176,11 +314,11 @@ __global__ void __launch_bounds__(256) mlp_fp64_kernel(MlpDesc m, RowSrc src, do
         double* ob = h1;
         for (int l = 0; l + 1 < m.nw; ++l) {
             const int fi = m.widths[l], fo = m.widths[l + 1];
-            const float* __restrict__ WT = m.WT[l];   // [fi][fo]
+            const float* __restrict__ WT = m.WT[l];   // [fi][wt_ld]
             const bool hidden = (l + 2 < m.nw);
             for (int j = threadIdx.x; j < fo; j += blockDim.x) {
                 double s = 0.0;
-                for (int k = 0; k < fi; ++k) s = __dadd_rn(s, __dmul_rn((double)__ldg(WT + (size_t)k * fo + j), in[k]));
+                for (int k = 0; k < fi; ++k) s = __dadd_rn(s, __dmul_rn((double)__ldg(WT + (size_t)k * m.wt_ld[l] + j), in[k]));
                 s = __dadd_rn(s, (double)__ldg(m.b[l] + j));
                 ob[j] = hidden ? (s > 0.0 ? s : 0.0) : s;
             }
@@ -221,8 +359,42 @@ static cudaError_t launch_fp32_f(const MlpDesc& m, const RowSrc& src, float* out
     }
 }
 
+template <int F, bool FD>
+static cudaError_t launch_fp32_list_t(const MlpDesc& m, const RowSrc& src, float* out, int grid, int wmax4,
+                                      int* status_word, cudaStream_t s) {
+    constexpr int RB = 8;
+    int kc = 16384 / (wmax4 * 4);
+    kc = kc < 1 ? 1 : (kc > 16 ? 16 : kc);
+    const size_t smem = (size_t)(2 * wmax4 * RB + 3 * kc * wmax4) * sizeof(float);
+    auto k = wmax4 <= 256 ? mlp_fp32_list_kernel<RB, 1, F, FD> : mlp_fp32_list_kernel<RB, 4, F, FD>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, 256, smem, s>>>(m, src, out, wmax4, kc, status_word);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_fp32_list(const MlpDesc& m, const RowSrc& src, float* out, int num_sms,
+                                    int* status_word, cudaStream_t s) {
+    int wmax = 0;
+    for (int i = 0; i < m.nw; ++i) wmax = wmax > m.widths[i] ? wmax : m.widths[i];
+    const int wmax4 = (wmax + 3) / 4 * 4;
+    const bool fd = (src.feat == nullptr);
+    int grid = num_sms * 2;
+    if (!src.count_dev) {
+        const int64_t tiles = (src.count + 7) / 8;
+        grid = (int)(tiles < 1 ? 1 : (tiles < grid ? tiles : grid));
+    }
+    switch (m.widths[0]) {
+        case 32: return fd ? launch_fp32_list_t<32, true>(m, src, out, grid, wmax4, status_word, s) : launch_fp32_list_t<32, false>(m, src, out, grid, wmax4, status_word, s);
+        case 64: return fd ? launch_fp32_list_t<64, true>(m, src, out, grid, wmax4, status_word, s) : launch_fp32_list_t<64, false>(m, src, out, grid, wmax4, status_word, s);
+        case 128: return fd ? launch_fp32_list_t<128, true>(m, src, out, grid, wmax4, status_word, s) : launch_fp32_list_t<128, false>(m, src, out, grid, wmax4, status_word, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_mlp_fp32(const MlpDesc& m, const RowSrc& src, float* out, int num_sms, bool for_list,
-                            cudaStream_t s) {
+                            cudaStream_t s, int* status_word) {
     int wmax = 0;
     for (int i = 1; i + 1 < m.nw; ++i) wmax = wmax > m.widths[i] ? wmax : m.widths[i];
     const bool fd = (src.feat == nullptr);
@@ -231,10 +403,7 @@ cudaError_t launch_mlp_fp32(const MlpDesc& m, const RowSrc& src, float* out, int
         const int grid = (int)(tiles < 1 ? 1 : tiles);
         return fd ? launch_fp32_f<64, 8, true>(m, src, out, grid, s) : launch_fp32_f<64, 8, false>(m, src, out, grid, s);
     }
-    if (wmax <= 256) {   // latency-oriented: 16-row tiles, 2 rows x 8 columns per thread
-        const int grid = num_sms * 4;
-        return fd ? launch_fp32_f<16, 2, true>(m, src, out, grid, s) : launch_fp32_f<16, 2, false>(m, src, out, grid, s);
-    }
+    if (for_list && status_word) return launch_fp32_list(m, src, out, num_sms, status_word, s);
     int grid = num_sms * 2;
     if (!for_list) {
         const int64_t tiles = (src.count + 15) / 16;

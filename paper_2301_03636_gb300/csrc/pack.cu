@@ -37,11 +37,12 @@ __global__ void pack_w16_kernel(const float* __restrict__ W, int fo, int fi, int
     }
 }
 
-__global__ void transpose_kernel(const float* __restrict__ W, int fo, int fi, float* __restrict__ WT) {
-    const int64_t total = (int64_t)fo * fi;
+// WT[k][n] = W[n][k], rows of ld >= fo floats, zero beyond fo.
+__global__ void transpose_kernel(const float* __restrict__ W, int fo, int fi, int ld, float* __restrict__ WT) {
+    const int64_t total = (int64_t)ld * fi;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int n = (int)(i / fi), k = (int)(i % fi);
-        WT[(size_t)k * fo + n] = W[i];
+        const int k = (int)(i / ld), n = (int)(i % ld);
+        WT[i] = n < fo ? W[(size_t)n * fi + k] : 0.f;
     }
 }
 
@@ -84,7 +85,8 @@ cudaError_t launch_repack(const ModelLayout& L, uint8_t* P, cudaStream_t s) {
     for (int l = 0; l < L.n_layers; ++l) {
         const int fi = L.widths[l], fo = L.widths[l + 1];
         const float* W = master + L.layer_w_off[l];
-        transpose_kernel<<<grid_for((int64_t)fo * fi), 256, 0, s>>>(W, fo, fi,
+        const int ld = (fo + 3) / 4 * 4;
+        transpose_kernel<<<grid_for((int64_t)ld * fi), 256, 0, s>>>(W, fo, fi, ld,
                                                                    reinterpret_cast<float*>(P + L.p_wT[l]));
         if (l < L.n_hidden) {
             const int64_t chunks = (int64_t)L.npad[l] * L.kpad[l] / 8;
