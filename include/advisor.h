@@ -231,6 +231,32 @@ advisor_status advisor_loss_grad(advisor_model_t m, const int32_t* d_feat_q16, c
                                  int64_t n_rows, advisor_precision precision, float* d_grad,
                                  float* d_loss, cudaStream_t stream);
 
+/* Forward pass for training (Sec. 3 training mode), keeping every layer's
+ * output in the workspace for advisor_backward.  d_y [n_rows] (nullable)
+ * receives the predictions.  precision ADVISOR_FP32. */
+advisor_status advisor_forward_saved(advisor_model_t m, const int32_t* d_feat_q16, int64_t n_rows,
+                                     advisor_precision precision, float* d_y, cudaStream_t stream);
+
+/* Hand-written backward of the last advisor_forward_saved (same n_rows):
+ * from d_dy = dL/dy [n_rows] to the parameter gradient d_grad [param_count]
+ * (layout of the master parameters).  ReLU derivative 1 for positive
+ * pre-activations, 0 otherwise. */
+advisor_status advisor_backward(advisor_model_t m, const float* d_dy, int64_t n_rows, float* d_grad,
+                                cudaStream_t stream);
+
+/* Rebuild the derived copies (16-bit tensor-core images, transposed copy,
+ * padded biases) after the FP32 master parameters were changed in place. */
+advisor_status advisor_model_repack(advisor_model_t m, cudaStream_t stream);
+
+/* Byte offset of the FP32 master parameters inside the parameter block (so
+ * that a caller can view them as a tensor, e.g. for an external optimizer). */
+size_t advisor_model_master_offset(advisor_model_t m);
+
+/* Adam step counter of the model (checkpoint / resume; the moments live in
+ * the parameter block). */
+int64_t advisor_model_get_adam_step(advisor_model_t m);
+advisor_status advisor_model_set_adam_step(advisor_model_t m, int64_t step);
+
 /* Read and clear the model's sticky device status word (synchronises
  * `stream`).  Returns ADVISOR_OK, ADVISOR_ERR_TIMEOUT, ADVISOR_ERR_BAD_SEGMENTS
  * or ADVISOR_ERR_CUDA. */

@@ -66,6 +66,12 @@ def lib():
         "advisor_loss_grad": (st, [P, P, P, i64, st, P, P, P]),
         "advisor_get_device_status": (st, [P, P]),
         "advisor_model_set_profile_events": (st, [P, P, P]),
+        "advisor_forward_saved": (st, [P, P, i64, st, P, P]),
+        "advisor_backward": (st, [P, P, i64, P, P]),
+        "advisor_model_repack": (st, [P, P]),
+        "advisor_model_master_offset": (sz, [P]),
+        "advisor_model_get_adam_step": (i64, [P]),
+        "advisor_model_set_adam_step": (st, [P, i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -238,6 +244,39 @@ class Model:
         _check(lib().advisor_model_set_profile_events(self.handle, ctypes.c_void_p(start.cuda_event),
                                                       ctypes.c_void_p(stop.cuda_event)), "set_profile_events")
 
+    # ---- training mode -------------------------------------------------------------
+
+    def master(self) -> torch.Tensor:
+        """The FP32 master parameters as a tensor view into the parameter block
+        (per layer W[out][in] then b[out]).  After changing them in place, call
+        repack() so that the scorers see the new values."""
+        off = int(lib().advisor_model_master_offset(self.handle))
+        return self.param_block[off:off + 4 * self.n_params].view(torch.float32)
+
+    def repack(self, stream=None):
+        _check(lib().advisor_model_repack(self.handle, _stream(stream)), "advisor_model_repack")
+
+    def forward_saved(self, feat, precision="fp32", stream=None) -> torch.Tensor:
+        y = torch.empty(feat.shape[0], dtype=torch.float32, device=self.device)
+        _check(lib().advisor_forward_saved(self.handle, _ptr(feat), feat.shape[0], _prec(precision), _ptr(y),
+                                           _stream(stream)), "advisor_forward_saved")
+        return y
+
+    def backward(self, dy, stream=None) -> torch.Tensor:
+        dy = dy.contiguous().to(torch.float32)
+        grad = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        _check(lib().advisor_backward(self.handle, _ptr(dy), dy.shape[0], _ptr(grad), _stream(stream)),
+               "advisor_backward")
+        return grad
+
+    @property
+    def adam_step(self) -> int:
+        return int(lib().advisor_model_get_adam_step(self.handle))
+
+    @adam_step.setter
+    def adam_step(self, step: int):
+        _check(lib().advisor_model_set_adam_step(self.handle, int(step)), "advisor_model_set_adam_step")
+
     def device_status(self, stream=None) -> int:
         return int(lib().advisor_get_device_status(self.handle, _stream(stream)))
 
@@ -248,3 +287,22 @@ class Model:
         y64 = self.score_fp64(feat, status)
         ok = torch.isfinite(y64)
         return float(safety * (y[ok] - y64[ok]).abs().max().item())
+
+
+class MLPFunction(torch.autograd.Function):
+    """y = MLP(features) with the library's hand-written backward.
+
+    apply(master, feat, model): `master` must be model.master() (the FP32
+    parameters the forward reads); its gradient comes from advisor_backward.
+    The features are integer inputs and get no gradient."""
+
+    @staticmethod
+    def forward(ctx, master, feat, model):
+        ctx.model = model
+        ctx.n = feat.shape[0]
+        return model.forward_saved(feat)
+
+    @staticmethod
+    def backward(ctx, dy):
+        grad = ctx.model.backward(dy)
+        return grad, None, None

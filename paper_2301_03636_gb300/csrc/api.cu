@@ -42,6 +42,7 @@ struct advisor_model {
     bool params_set = false;
     cudaEvent_t prof_start = nullptr, prof_stop = nullptr;   // bracket the tensor-core scorer launch
     int64_t adam_step = 0;
+    int64_t saved_rows = 0;   // rows of the last advisor_forward_saved
 };
 
 namespace {
@@ -479,6 +480,41 @@ advisor_status advisor_model_set_profile_events(advisor_model_t m, void* ev_star
     if (!m || (ev_start == nullptr) != (ev_stop == nullptr)) return ADVISOR_ERR_INVALID_ARGUMENT;
     m->prof_start = static_cast<cudaEvent_t>(ev_start);
     m->prof_stop = static_cast<cudaEvent_t>(ev_stop);
+    return ADVISOR_OK;
+}
+
+advisor_status advisor_forward_saved(advisor_model_t m, const int32_t* d_feat_q16, int64_t n_rows,
+                                     advisor_precision precision, float* d_y, cudaStream_t stream) {
+    if (!m || !d_feat_q16 || n_rows < 1) return ADVISOR_ERR_INVALID_ARGUMENT;
+    advisor_status st = check_ready(m, n_rows);
+    if (st != ADVISOR_OK) return st;
+    if (precision != ADVISOR_FP32) return ADVISOR_ERR_UNSUPPORTED;
+    cudaError_t e = adv::launch_forward_saved(m->L, m->T, m->WS + m->W.train, mlp_desc(m), d_feat_q16, n_rows, d_y,
+                                              stream);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    m->saved_rows = n_rows;
+    return ADVISOR_OK;
+}
+
+advisor_status advisor_backward(advisor_model_t m, const float* d_dy, int64_t n_rows, float* d_grad,
+                                cudaStream_t stream) {
+    if (!m || !d_dy || !d_grad || n_rows < 1) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (n_rows != m->saved_rows) return ADVISOR_ERR_INVALID_ARGUMENT;
+    return cuda_status(adv::launch_backward(m->L, m->T, m->WS + m->W.train, mlp_desc(m), d_dy, n_rows, d_grad, stream));
+}
+
+advisor_status advisor_model_repack(advisor_model_t m, cudaStream_t stream) {
+    if (!m || !m->P) return ADVISOR_ERR_INVALID_ARGUMENT;
+    return cuda_status(adv::launch_repack(m->L, m->P, stream));
+}
+
+size_t advisor_model_master_offset(advisor_model_t m) { return m ? m->L.p_master : 0; }
+
+int64_t advisor_model_get_adam_step(advisor_model_t m) { return m ? m->adam_step : -1; }
+
+advisor_status advisor_model_set_adam_step(advisor_model_t m, int64_t step) {
+    if (!m || step < 0) return ADVISOR_ERR_INVALID_ARGUMENT;
+    m->adam_step = step;
     return ADVISOR_OK;
 }
 

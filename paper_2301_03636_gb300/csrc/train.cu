@@ -203,20 +203,10 @@ size_t train_layout(const ModelLayout& L, int64_t R, TrainLayout* t) {
     return o;
 }
 
-cudaError_t launch_train_step(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
-                              const MlpDesc& md, const int32_t* feat, const float* labels, int64_t n,
-                              const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss, int num_sms,
-                              cudaStream_t s) {
-    (void)num_sms;
+cudaError_t launch_forward_saved(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
+                                 const int32_t* feat, int64_t n, float* d_y, cudaStream_t s) {
     cudaError_t e;
     auto act = [&](int l) { return reinterpret_cast<float*>(TW + T.act[l]); };
-    float* dA = reinterpret_cast<float*>(TW + T.dA);
-    float* dB = reinterpret_cast<float*>(TW + T.dB);
-    float* grad = d_grad_out ? d_grad_out : reinterpret_cast<float*>(TW + T.grad);
-    float* part = reinterpret_cast<float*>(TW + T.part);
-    const int splits = (int)((n + SPLIT_ROWS - 1) / SPLIT_ROWS);
-
-    // forward, keeping every layer's output
     standardize_f32_kernel<<<grid1(n * L.F), 256, 0, s>>>(feat, n, L.F, md.sa, md.sc, act(0));
     adv_count_launch(1);
     for (int l = 0; l < L.n_layers; ++l) {
@@ -230,20 +220,37 @@ cudaError_t launch_train_step(const ModelLayout& L, const TrainLayout& T, uint8_
         e = (l + 1 < L.n_layers) ? gemm<1>(g, 1, s) : gemm<2>(g, 1, s);
         if (e != cudaSuccess) return e;
     }
-    // loss and dL/dy
+    if (d_y) return launch_copy_f32(act(L.n_layers), d_y, n, s);
+    return cudaGetLastError();
+}
+
+// dL/dy of loss = 0.5 mean (y - t)^2 into the gradient buffer, loss to d_loss.
+static cudaError_t launch_mse(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const float* labels,
+                              int64_t n, float* d_loss, cudaStream_t s) {
     const int nb = 256;
-    loss_kernel<<<nb, 256, 0, s>>>(act(L.n_layers), labels, n, dA, reinterpret_cast<float*>(TW + T.loss_part));
+    loss_kernel<<<nb, 256, 0, s>>>(reinterpret_cast<float*>(TW + T.act[L.n_layers]), labels, n,
+                                   reinterpret_cast<float*>(TW + T.dA), reinterpret_cast<float*>(TW + T.loss_part));
     loss_final_kernel<<<1, 32, 0, s>>>(reinterpret_cast<float*>(TW + T.loss_part), nb, n,
                                        reinterpret_cast<float*>(TW + T.loss), d_loss);
     adv_count_launch(2);
-    // backward
-    float* dz = dA;
-    float* dnext = dB;
+    return cudaGetLastError();
+}
+
+// Backward of the saved forward from dL/dy (already in the dA buffer) to the
+// parameter gradient.
+static cudaError_t launch_backward_saved(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
+                                        int64_t n, float* grad, cudaStream_t s) {
+    cudaError_t e;
+    auto act = [&](int l) { return reinterpret_cast<float*>(TW + T.act[l]); };
+    float* dz = reinterpret_cast<float*>(TW + T.dA);
+    float* dnext = reinterpret_cast<float*>(TW + T.dB);
+    float* part = reinterpret_cast<float*>(TW + T.part);
+    const int splits = (int)((n + SPLIT_ROWS - 1) / SPLIT_ROWS);
     for (int l = L.n_layers - 1; l >= 0; --l) {
         const int fi = L.widths[l], fo = L.widths[l + 1];
         float* gW = grad + L.layer_w_off[l];
         float* gb = grad + L.layer_b_off[l];
-        // dW = dZ^T * In, split over rows
+        // dW = dZ^T * In, split over rows in fixed chunks, summed in a fixed order
         GemmArgs g{};
         g.A = dz; g.sam = 1; g.sak = fo;
         g.B = act(l); g.sbk = fi; g.sbn = 1;
@@ -254,9 +261,8 @@ cudaError_t launch_train_step(const ModelLayout& L, const TrainLayout& T, uint8_
         if (e != cudaSuccess) return e;
         split_sum_kernel<<<grid1((int64_t)fo * fi), 256, 0, s>>>(part, splits, (int64_t)fo * fi, (int64_t)fo * fi, gW);
         dim3 cg((unsigned)((fo + 127) / 128), (unsigned)splits);
-        float* bpart = part;   // reuse after the dW sum consumed it (stream order)
-        colsum_kernel<<<cg, 128, 0, s>>>(dz, n, fo, bpart, fo);
-        split_sum_kernel<<<grid1(fo), 256, 0, s>>>(bpart, splits, fo, fo, gb);
+        colsum_kernel<<<cg, 128, 0, s>>>(dz, n, fo, part, fo);   // the dW partials were consumed (stream order)
+        split_sum_kernel<<<grid1(fo), 256, 0, s>>>(part, splits, fo, fo, gb);
         adv_count_launch(3);
         if (l == 0) break;
         // dIn = dZ * W, masked by the ReLU of the input (the previous layer's output)
@@ -270,7 +276,28 @@ cudaError_t launch_train_step(const ModelLayout& L, const TrainLayout& T, uint8_
         if (e != cudaSuccess) return e;
         float* t = dz; dz = dnext; dnext = t;
     }
-    if (!adam) return cudaGetLastError();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
+                            const float* d_dy, int64_t n, float* d_grad, cudaStream_t s) {
+    cudaError_t e = launch_copy_f32(d_dy, reinterpret_cast<float*>(TW + T.dA), n, s);
+    if (e != cudaSuccess) return e;
+    return launch_backward_saved(L, T, TW, md, n, d_grad, s);
+}
+
+cudaError_t launch_train_step(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
+                              const MlpDesc& md, const int32_t* feat, const float* labels, int64_t n,
+                              const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss, int num_sms,
+                              cudaStream_t s) {
+    (void)num_sms;
+    float* grad = d_grad_out ? d_grad_out : reinterpret_cast<float*>(TW + T.grad);
+    cudaError_t e = launch_forward_saved(L, T, TW, md, feat, n, nullptr, s);
+    if (e != cudaSuccess) return e;
+    e = launch_mse(L, T, TW, labels, n, d_loss, s);
+    if (e != cudaSuccess) return e;
+    e = launch_backward_saved(L, T, TW, md, n, grad, s);
+    if (e != cudaSuccess || !adam) return e;
     const float c1 = (float)(1.0 - std::pow((double)adam->beta1, (double)step));
     const float c2 = (float)(1.0 - std::pow((double)adam->beta2, (double)step));
     adam_kernel<<<grid1(L.n_params), 256, 0, s>>>(reinterpret_cast<float*>(P + L.p_master), grad,

@@ -32,4 +32,12 @@ cudaError_t launch_train_step(const ModelLayout& L, const TrainLayout& T, uint8_
                               const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss, int num_sms,
                               cudaStream_t s);
 
+// Forward pass keeping every layer's output in the training region; the
+// output y (n floats) is copied to d_y when non-null.
+cudaError_t launch_forward_saved(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
+                                 const int32_t* feat, int64_t n, float* d_y, cudaStream_t s);
+// Backward of the last saved forward (same n) from dL/dy to d_grad.
+cudaError_t launch_backward(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
+                            const float* d_dy, int64_t n, float* d_grad, cudaStream_t s);
+
 }  // namespace adv

@@ -1,0 +1,131 @@
+"""Training mode on the GPU: the hand-written backward against the FP64 oracle
+gradient (directly and through torch.autograd), one Adam step against the
+oracle's Adam, determinism, checkpoint/resume, and the paper's success
+criterion (validation NRMSE < 0.1, Sec. 5 Exp. 3) on the training workload
+(64-256-256-256-1, Glorot init, labels from the analytic runtime model)."""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2301_03636_gb300 import advisor, metrics, training
+from paper_2301_03636_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+WIDTHS = (64, 256, 256, 256, 1)
+
+
+def _split_rel(a, b, widths):
+    """Relative L2 error per parameter tensor (W_l and b_l)."""
+    out, off = [], 0
+    for i in range(len(widths) - 1):
+        for size in (widths[i] * widths[i + 1], widths[i + 1]):
+            x, y = a[off:off + size], b[off:off + size]
+            out.append(np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-30))
+            off += size
+    return np.array(out)
+
+
+def _setup(n, seed, bias_scale=0.05):
+    d = W.make_descriptors(n, seed)
+    f, st = oracle.extract_features(d, 64)
+    mu, sigma = oracle.fit_standardizer(f, st)
+    p = W.make_weights(WIDTHS, seed, "glorot", bias_scale)
+    t = W.make_labels(d, seed)
+    m = advisor.Model(WIDTHS, max_rows=n, max_kernels=1)
+    m.set_params(p, mu, sigma)
+    return m, d, f, t, p, mu, sigma
+
+
+def test_gradient_matches_oracle(gpu_lib):
+    m, d, f, t, p, mu, sg = _setup(2048, 31)
+    loss_ref, g_ref = oracle.loss_grad(f, t, WIDTHS, p, mu, sg)
+    ft, tt = torch.from_numpy(f).cuda(), torch.from_numpy(t).cuda()
+    loss, g = m.loss_grad(ft, tt)
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(float(loss.item()) - loss_ref) <= 1e-5 * abs(loss_ref)
+    rel = _split_rel(g, g_ref, WIDTHS)
+    cos = float(g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref)))
+    print("per-tensor rel-L2:", np.array2string(rel, precision=2), "cos", cos)
+    assert rel.max() < 1e-4 and cos > 0.999999
+
+
+def test_autograd_function_gradient(gpu_lib):
+    m, d, f, t, p, mu, sg = _setup(1536, 32)
+    _, g_ref = oracle.loss_grad(f, t, WIDTHS, p, mu, sg)
+    master = m.master().clone().requires_grad_(True)
+    ft, tt = torch.from_numpy(f).cuda(), torch.from_numpy(t).cuda()
+    y = advisor.MLPFunction.apply(master, ft, m)
+    loss = 0.5 * ((y - tt) ** 2).mean()
+    loss.backward()
+    rel = _split_rel(master.grad.cpu().numpy().astype(np.float64), g_ref, WIDTHS)
+    assert rel.max() < 1e-4
+    # the forward output is the FP32 prediction of the model
+    y_ref = oracle.mlp_forward(f, WIDTHS, p, mu, sg)
+    assert np.allclose(y.detach().cpu().numpy(), y_ref, atol=2e-4, rtol=2e-4)
+
+
+def test_adam_step_matches_oracle(gpu_lib):
+    m, d, f, t, p, mu, sg = _setup(1024, 33)
+    _, g_ref = oracle.loss_grad(f, t, WIDTHS, p, mu, sg)
+    lr = 1e-3
+    new_ref, _, _ = oracle.adam_step(p.astype(np.float64), g_ref, np.zeros(len(p)), np.zeros(len(p)), lr, 0.9,
+                                     0.999, 1e-8, 1)
+    m.train_step(torch.from_numpy(f).cuda(), torch.from_numpy(t).cuda(), lr=lr)
+    new = m.get_params().cpu().numpy().astype(np.float64)
+    diff = np.abs(new - new_ref)
+    # step 1 moves each parameter by lr * g / (|g| + eps): identical except where
+    # |g| is near eps, where FP32 and FP64 gradients may round differently
+    assert np.mean(diff <= 1e-3 * lr + 1e-7) > 0.999
+    assert diff.max() <= 2 * lr + 1e-6
+
+
+def test_training_is_deterministic_and_resumable(gpu_lib):
+    n = 8192
+    m1, d, f, t, p, mu, sg = _setup(n, 34)
+    ft, tt = torch.from_numpy(f).cuda(), torch.from_numpy(t).cuda()
+    training.train(m1, ft, tt, steps=10, batch=2048, seed=1)
+    with tempfile.TemporaryDirectory() as tmp:
+        ck = os.path.join(tmp, "ck.pt")
+        training.save_checkpoint(m1, ck)
+        training.train(m1, ft, tt, steps=10, batch=2048, seed=2)
+        a = m1.get_params().cpu()
+        m2 = advisor.Model(WIDTHS, max_rows=n, max_kernels=1)
+        m2.set_params(p, mu, sg)
+        training.load_checkpoint(m2, ck)
+        assert m2.adam_step == 10
+        training.train(m2, ft, tt, steps=10, batch=2048, seed=2)
+        b = m2.get_params().cpu()
+    assert torch.equal(a, b)
+    # a second run from the same initial state gives the same bits
+    m3 = advisor.Model(WIDTHS, max_rows=n, max_kernels=1)
+    m3.set_params(p, mu, sg)
+    training.train(m3, ft, tt, steps=10, batch=2048, seed=1)
+    m4 = advisor.Model(WIDTHS, max_rows=n, max_kernels=1)
+    m4.set_params(p, mu, sg)
+    training.train(m4, ft, tt, steps=10, batch=2048, seed=1)
+    assert torch.equal(m3.get_params(), m4.get_params())
+
+
+def test_training_workload_meets_nrmse_criterion(gpu_lib):
+    wl = W.TRAINING
+    d_tr = W.make_descriptors(65536, W.SEEDS["c4"])
+    d_va = W.make_descriptors(16384, W.SEEDS["c4_val"])
+    t_tr, t_va = W.make_labels(d_tr, W.SEEDS["c4"]), W.make_labels(d_va, W.SEEDS["c4_val"])
+    f_tr, s_tr = advisor.advisor_extract_features(torch.from_numpy(d_tr).cuda(), 64)
+    f_va, _ = advisor.advisor_extract_features(torch.from_numpy(d_va).cuda(), 64)
+    mu, sigma = advisor.advisor_fit_standardizer(f_tr, s_tr)   # the training split's statistics
+    m = advisor.Model(wl.widths, max_rows=65536, max_kernels=1)
+    m.set_params(wl.weights(), mu, sigma)
+    tt = torch.from_numpy(t_tr).cuda()
+    losses = []
+    training.train(m, f_tr, tt, steps=400, batch=65536, lr=1e-3, losses=losses)
+    first, last = float(losses[0].item()), float(losses[-1].item())
+    ev = training.evaluate(m, f_va, torch.from_numpy(t_va).cuda())
+    print(f"loss {first:.4f} -> {last:.4f}; validation RMSE {ev['rmse']:.4f} NRMSE {ev['nrmse']:.4f}")
+    assert last < 0.25 * first
+    assert ev["nrmse"] < metrics.SUCCESS_NRMSE
