@@ -144,7 +144,7 @@ def advisor_fit_standardizer(feat: torch.Tensor, status: torch.Tensor | None = N
 class Model:
     """An MLP cost model bound to caller-owned (torch) device memory."""
 
-    def __init__(self, widths, max_rows: int, max_kernels: int, device="cuda"):
+    def __init__(self, widths, max_rows: int, max_kernels: int, device="cuda", param_block=None):
         self.widths = tuple(int(w) for w in widths)
         self.device = torch.device(device)
         w = (ctypes.c_int32 * len(self.widths))(*self.widths)
@@ -156,7 +156,12 @@ class Model:
         self.max_kernels = int(max_kernels)
         pb = lib().advisor_model_param_bytes(h)
         wb = lib().advisor_workspace_bytes(h, self.max_rows, self.max_kernels)
-        self.param_block = torch.empty(pb, dtype=torch.uint8, device=self.device)
+        if param_block is not None:
+            # a second handle on another model's resident parameters (own workspace)
+            assert param_block.numel() >= pb and param_block.dtype == torch.uint8
+            self.param_block = param_block
+        else:
+            self.param_block = torch.empty(pb, dtype=torch.uint8, device=self.device)
         self.workspace = torch.empty(wb, dtype=torch.uint8, device=self.device)
         _check(lib().advisor_model_bind(h, _ptr(self.param_block), pb, _ptr(self.workspace), wb, self.max_rows,
                                         self.max_kernels), "advisor_model_bind")

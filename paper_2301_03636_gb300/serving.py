@@ -1,0 +1,253 @@
+"""Prediction-mode serving (Sec. 3: a query is one kernel's generated variants;
+the answer is the variant the cost model predicts to be fastest).
+
+Continuous batching: queries arriving while earlier batches are on the GPU
+wait in a FIFO queue; whenever one of the pipelines (a model handle with its
+own workspace, CUDA stream and pinned buffers, all sharing one resident
+parameter block) is idle, the queued queries are packed into its next batch
+up to its row capacity (admission by device memory), copied host->device,
+ranked with one advisor_rank call and copied back.  Several batches are in
+flight at once on different streams.  Every kernel of the path computes each
+row and each kernel segment independently of the rest of the batch, so a
+query's answer is the same alone and in any mix.
+
+The host logic (Batcher) has no GPU dependency and is tested on the CPU with
+a fake executor.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Query:
+    qid: int
+    desc: np.ndarray            # [n][16] int64
+    arrival: float              # seconds (serving clock)
+    admitted: float = -1.0
+    done: float = -1.0
+    best: int = -2
+    score: float = float("nan")
+    status: str = "queued"      # queued | running | done | rejected | cancelled
+
+    @property
+    def rows(self) -> int:
+        return int(self.desc.shape[0])
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+class Batcher:
+    """FIFO admission into batches bounded by rows and queries."""
+
+    def __init__(self, max_rows: int, max_queries: int):
+        self.max_rows = int(max_rows)
+        self.max_queries = int(max_queries)
+        self.queue: collections.deque[Query] = collections.deque()
+        self.rejected: list[Query] = []
+        self.cancelled: list[Query] = []
+
+    def submit(self, q: Query) -> bool:
+        if q.rows < 1 or q.rows > self.max_rows:
+            q.status = "rejected"          # can never fit a batch: refused at admission
+            self.rejected.append(q)
+            return False
+        self.queue.append(q)
+        return True
+
+    def cancel(self, qid: int) -> bool:
+        """Cancel a query that has not been admitted to a batch yet."""
+        for q in self.queue:
+            if q.qid == qid:
+                self.queue.remove(q)
+                q.status = "cancelled"
+                self.cancelled.append(q)
+                return True
+        return False
+
+    def next_batch(self) -> list[Query]:
+        """Queued queries, oldest first, while they fit the row capacity.  A
+        query that does not fit waits for the next batch (no overtaking)."""
+        out, rows = [], 0
+        while self.queue and len(out) < self.max_queries:
+            q = self.queue[0]
+            if rows + q.rows > self.max_rows:
+                break
+            out.append(self.queue.popleft())
+            rows += q.rows
+        return out
+
+    def __len__(self):
+        return len(self.queue)
+
+
+def pack(batch: list[Query], desc_out: np.ndarray, off_out: np.ndarray) -> tuple[int, int]:
+    """Concatenate the batch's descriptors and write segment offsets; returns
+    (rows, kernels)."""
+    n = 0
+    off_out[0] = 0
+    for i, q in enumerate(batch):
+        desc_out[n:n + q.rows] = q.desc
+        n += q.rows
+        off_out[i + 1] = n
+    return n, len(batch)
+
+
+class Server:
+    """Drives a Batcher and a set of executors (pipelines) on a serving clock.
+
+    An executor provides: idle() -> bool, launch(batch) and poll() -> list of
+    finished (batch, best[], score[]) results.  The GPU executor is
+    GpuPipeline; tests use a fake one."""
+
+    def __init__(self, batcher: Batcher, executors: list, clock=time.perf_counter):
+        self.batcher = batcher
+        self.executors = executors
+        self.clock = clock
+        self.finished: list[Query] = []
+
+    def step(self, now: float):
+        for ex in self.executors:
+            for batch, best, score in ex.poll():
+                t = self.clock() - self.t0
+                for q, b, s in zip(batch, best, score):
+                    q.best, q.score, q.done, q.status = int(b), float(s), t, "done"
+                    self.finished.append(q)
+        for ex in self.executors:
+            if ex.idle() and len(self.batcher):
+                batch = self.batcher.next_batch()
+                if not batch:
+                    break
+                for q in batch:
+                    q.admitted, q.status = now, "running"
+                ex.launch(batch)
+
+    def run(self, queries: list[Query], cancel_at: dict | None = None, timeout_s: float = 60.0):
+        """Open-loop replay: query i becomes visible at its arrival time."""
+        self.t0 = self.clock()
+        pending = sorted(queries, key=lambda q: q.arrival)
+        i = 0
+        cancel_at = dict(cancel_at or {})
+        total = len(pending)
+        while True:
+            now = self.clock() - self.t0
+            while i < total and pending[i].arrival <= now:
+                self.batcher.submit(pending[i])
+                i += 1
+            for qid, t in list(cancel_at.items()):
+                if now >= t:
+                    self.batcher.cancel(qid)
+                    del cancel_at[qid]
+            self.step(now)
+            settled = len(self.finished) + len(self.batcher.rejected) + len(self.batcher.cancelled)
+            if i >= total and settled >= total:
+                break
+            if now > timeout_s:
+                raise TimeoutError("serving replay did not finish in time")
+        return self.finished
+
+
+class GpuPipeline:
+    """One in-flight batch at a time on its own stream, with its own model
+    handle (sharing the parameter block of `base`) and workspace."""
+
+    def __init__(self, base, max_rows: int, max_queries: int, params, mu, sigma, precision="bf16",
+                 eps=-1.0, eps32=0.0):
+        import torch
+        from . import advisor
+        self.torch = torch
+        self.model = advisor.Model(base.widths, max_rows, max_queries, device=base.device,
+                                   param_block=base.param_block)
+        self.model.set_params(params, mu, sigma)
+        self.precision, self.eps, self.eps32 = precision, eps, eps32
+        self.stream = torch.cuda.Stream(device=base.device)
+        dev = base.device
+        self.h_desc = torch.empty((max_rows, 16), dtype=torch.int64).pin_memory()
+        self.h_off = torch.empty(max_queries + 1, dtype=torch.int64).pin_memory()
+        self.h_best = torch.empty(max_queries, dtype=torch.int32).pin_memory()
+        self.h_score = torch.empty(max_queries, dtype=torch.float64).pin_memory()
+        self.d_desc = torch.empty((max_rows, 16), dtype=torch.int64, device=dev)
+        self.d_off = torch.empty(max_queries + 1, dtype=torch.int64, device=dev)
+        self.d_best = torch.empty(max_queries, dtype=torch.int32, device=dev)
+        self.d_score = torch.empty(max_queries, dtype=torch.float64, device=dev)
+        self.event = torch.cuda.Event()
+        self.batch = None
+        self.nk = 0
+
+    def idle(self) -> bool:
+        return self.batch is None
+
+    def launch(self, batch):
+        torch = self.torch
+        n, k = pack(batch, self.h_desc.numpy(), self.h_off.numpy())
+        with torch.cuda.stream(self.stream):
+            self.d_desc[:n].copy_(self.h_desc[:n], non_blocking=True)
+            self.d_off[:k + 1].copy_(self.h_off[:k + 1], non_blocking=True)
+            self.model.rank(self.d_desc[:n], self.d_off[:k + 1], self.precision, self.eps, self.eps32,
+                            best=self.d_best[:k], best_score=self.d_score[:k], stream=self.stream)
+            self.h_best[:k].copy_(self.d_best[:k], non_blocking=True)
+            self.h_score[:k].copy_(self.d_score[:k], non_blocking=True)
+            self.event.record(self.stream)
+        self.batch, self.nk = batch, k
+
+    def poll(self):
+        if self.batch is None or not self.event.query():
+            return []
+        out = [(self.batch, self.h_best[:self.nk].numpy().copy(), self.h_score[:self.nk].numpy().copy())]
+        self.batch = None
+        return out
+
+
+def latency_stats(finished: list[Query]) -> dict:
+    lat = np.array([q.latency for q in finished if q.status == "done"]) * 1e3
+    if lat.size == 0:
+        return {"p50_ms": None, "p99_ms": None, "n": 0}
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()), "n": int(lat.size)}
+
+
+def make_queries(n_queries: int, rate_per_s: float, seed: int) -> list[Query]:
+    """Poisson arrivals of queries of floor(2^U(2, 9)) variants (4..512) each,
+    descriptors from the plain-method distribution."""
+    from . import workloads
+    sizes = workloads.make_query_sizes(n_queries, seed)
+    arrivals = workloads.make_arrivals(n_queries, rate_per_s, seed)
+    desc = workloads.make_descriptors(int(sizes.sum()), seed)
+    out, pos = [], 0
+    for i, (n, t) in enumerate(zip(sizes, arrivals)):
+        out.append(Query(i, desc[pos:pos + n], float(t)))
+        pos += n
+    return out
+
+
+def run_serving(base, params, mu, sigma, queries: list[Query], precision="bf16", eps=-1.0, eps32=0.0,
+                pipelines: int = 3, max_rows: int = 8192, max_queries: int = 128, warmup: bool = True):
+    """Serve `queries` (open loop, real clock) with `pipelines` batches in
+    flight; returns (finished queries, stats)."""
+    import torch
+    pipes = [GpuPipeline(base, max_rows, max_queries, params, mu, sigma, precision, eps, eps32)
+             for _ in range(pipelines)]
+    if warmup:   # first launches (module load, attribute setup) outside the replay
+        w = [Query(-1 - i, q.desc, 0.0) for i, q in enumerate(queries[:pipelines])]
+        for p, qq in zip(pipes, w):
+            p.launch([qq])
+        torch.cuda.synchronize()
+        for p in pipes:
+            p.poll()
+    batcher = Batcher(max_rows, max_queries)
+    srv = Server(batcher, pipes)
+    t0 = time.perf_counter()
+    done = srv.run(queries)
+    wall = time.perf_counter() - t0
+    st = latency_stats(done)
+    st["queries_per_s"] = len(done) / wall
+    st["variants_per_s"] = sum(q.rows for q in done) / wall
+    st["rejected"] = len(batcher.rejected)
+    st["pipelines"] = pipelines
+    return done, st
