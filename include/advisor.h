@@ -262,6 +262,27 @@ advisor_status advisor_model_set_adam_step(advisor_model_t m, int64_t step);
  * or ADVISOR_ERR_CUDA. */
 advisor_status advisor_get_device_status(advisor_model_t m, cudaStream_t stream);
 
+/* Tensor-core scoring that allocates nothing: the same computation and
+ * result as advisor_score_variants with ADVISOR_BF16 or ADVISOR_FP16, for
+ * callers that cannot provide device memory for a workspace (code where
+ * cudaMalloc is not allowed, e.g. host callbacks or hosts that forbid device
+ * allocations after start-up).  The paper has no counterpart: this is an
+ * interface convenience.  The 16-bit activation image lives in a fixed
+ * device array inside the library: 16,384 rows of up to 128 features
+ * (4 MiB on every GPU that loads the library, held until exit); n_rows
+ * beyond 16,384 returns ADVISOR_ERR_OUT_OF_MEMORY before anything is
+ * enqueued.  The model must be bound and loaded (set_params); its workspace
+ * is not used.  The first call on a device looks up the array's device
+ * address (once per device, with that device current), so make that first
+ * call before any stream capture.  All calls on a device share the array;
+ * each call rewrites every part it reads, but calls whose kernels overlap on
+ * the GPU (e.g. on two streams) race and must be ordered by the caller.
+ * ADVISOR_FP32 / ADVISOR_FP64 return ADVISOR_ERR_UNSUPPORTED. */
+advisor_status advisor_score_variants_noalloc(advisor_model_t m, const int32_t* d_feat_q16,
+                                              const uint8_t* d_row_status, int64_t n_rows,
+                                              advisor_precision precision, float* d_scores,
+                                              cudaStream_t stream);
+
 /* Measurement hook: when ev_start / ev_stop (cudaEvent_t handles created by
  * the caller with timing enabled) are non-NULL, every later launch of the
  * tensor-core scorer by this model is bracketed by cudaEventRecord on the

@@ -67,6 +67,7 @@ def lib():
         "advisor_get_device_status": (st, [P, P]),
         "advisor_model_set_profile_events": (st, [P, P, P]),
         "advisor_forward_saved": (st, [P, P, i64, st, P, P]),
+        "advisor_score_variants_noalloc": (st, [P, P, P, i64, st, P, P]),
         "advisor_backward": (st, [P, P, i64, P, P]),
         "advisor_model_repack": (st, [P, P]),
         "advisor_model_master_offset": (sz, [P]),
@@ -198,6 +199,21 @@ class Model:
         out = torch.empty(n, dtype=torch.float32, device=self.device) if out is None else out
         _check(lib().advisor_score_variants(self.handle, _ptr(feat), _ptr(status), n, _prec(precision), _ptr(out),
                                             _stream(stream)), "advisor_score_variants")
+        return out
+
+    NOALLOC_MAX_ROWS = 16384
+
+    def score_noalloc(self, feat, status=None, precision="bf16", out=None, stream=None) -> torch.Tensor:
+        """Tensor-core scores without using the model's workspace: the
+        library's fixed device scratch holds the 16-bit activations (at most
+        NOALLOC_MAX_ROWS rows; calls overlapping on the GPU race)."""
+        n = feat.shape[0]
+        if n > self.NOALLOC_MAX_ROWS:
+            raise AdvisorError(3, f"advisor_score_variants_noalloc: {n} rows exceed the fixed scratch of "
+                                  f"{self.NOALLOC_MAX_ROWS} rows")
+        out = torch.empty(n, dtype=torch.float32, device=self.device) if out is None else out
+        _check(lib().advisor_score_variants_noalloc(self.handle, _ptr(feat), _ptr(status), n, _prec(precision),
+                                                    _ptr(out), _stream(stream)), "advisor_score_variants_noalloc")
         return out
 
     def score_fp64(self, feat, status=None, stream=None) -> torch.Tensor:

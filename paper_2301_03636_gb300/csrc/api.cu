@@ -9,6 +9,7 @@
 #include "mlp.cuh"
 #include "pack.cuh"
 #include "train.cuh"
+#include "noalloc.cuh"
 
 namespace {
 
@@ -528,6 +529,22 @@ advisor_status advisor_get_device_status(advisor_model_t m, cudaStream_t stream)
     if (h & ADV_DEV_TIMEOUT) return ADVISOR_ERR_TIMEOUT;
     if (h & ADV_DEV_BAD_SEGMENTS) return ADVISOR_ERR_BAD_SEGMENTS;
     return ADVISOR_OK;
+}
+
+// Read-only view of a bound model for the no-allocation scoring entry point
+// (noalloc.cu); allocates nothing.
+int adv_model_noalloc_view(advisor_model_t m, int fmt_idx, adv::NoallocModelView* out) {
+    if (!m || !out) return 0;
+    out->ready = (m->P != nullptr && m->params_set) ? 1 : 0;
+    out->F = m->L.F;
+    out->nslab0 = m->L.n_hidden > 0 ? m->L.nslab[0] : 0;
+    out->tc_ok = tc_supported(m) ? 1 : 0;
+    out->num_sms = m->num_sms;
+    if (!out->ready) return 1;
+    out->sa = reinterpret_cast<const float*>(m->P + m->L.p_stdz_a);
+    out->sc = reinterpret_cast<const float*>(m->P + m->L.p_stdz_c);
+    out->tc = tc_args(m, nullptr, 0, nullptr, nullptr, fmt_idx);
+    return 1;
 }
 
 }  // extern "C"
