@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
-    ap.add_argument("--no-extras", action="store_true", help="skip the FP16/FP32 comparison and CPU baseline legs")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the precision comparison, serving, training and CPU baseline legs")
     return ap.parse_args()
 
 
@@ -56,17 +57,22 @@ def peaks():
 
 def traffic_for(kernel_file: str):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None when the kernel source changed since the capture."""
-    p = os.path.join(ROOT, "profiles", "mlp_tc_traffic.json")
+    summary (profiles/mlp_tc_kernel_batched_4096k.md), or None when the kernel
+    source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "mlp_tc_kernel_batched_4096k.md")
     if not os.path.exists(p):
         return None
-    with open(p) as f:
-        j = json.load(f)
+    fields = {}
+    for line in open(p):
+        line = line.strip()
+        if ":" in line and line.split(":")[0] in ("source_sha256_16", "dram_bytes_per_launch"):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
     src = os.path.join(ROOT, "paper_2301_03636_gb300", "csrc", kernel_file)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if j.get("source_sha") != sha:
+    if fields.get("source_sha256_16") != sha or "dram_bytes_per_launch" not in fields:
         return None
-    return j.get("dram_bytes_per_launch_full")
+    return int(fields["dram_bytes_per_launch"])
 
 
 class ClockSampler:
@@ -143,6 +149,63 @@ def cpu_baseline(desc, off, params, mu, sigma, min_seconds=10.0):
     return {"value": rows / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"first {K} kernels ({len(sub)} variants) of the batched workload, FP64 C oracle "
                       f"(extract + MLP + argmin), repeated for {el:.1f} s"}
+
+
+def serving_leg(dev):
+    """Queries of 4..512 variants (plain-method distribution and network,
+    BF16 scorer with the near-tie re-score) arriving as a Poisson process;
+    continuous batching with three batches in flight.  Latency = arrival ->
+    answer on the host."""
+    import torch
+
+    from paper_2301_03636_gb300 import advisor, serving
+    wl = W.SERVING
+    cal = torch.from_numpy(W.calibration_descriptors(16384)).to(dev)
+    fcal, scal = advisor.advisor_extract_features(cal, wl.n_features)
+    mu, sigma = advisor.advisor_fit_standardizer(fcal, scal)
+    params = wl.weights()
+    base = advisor.Model(wl.widths, max_rows=16384, max_kernels=128, device=dev)
+    base.set_params(params, mu, sigma)
+    eps = base.calibrate_eps(fcal, scal, "bf16")
+    eps32 = base.calibrate_eps(fcal, scal, "fp32")
+    runs = []
+    for rate in (2000, 10000, 50000):
+        n = int(min(4000, rate * 0.5))
+        qs = serving.make_queries(n, float(rate), W.SEEDS["c3"] + rate)
+        _, st = serving.run_serving(base, params, mu, sigma, qs, "bf16", eps, eps32, pipelines=3)
+        st["rate_per_s"] = rate
+        runs.append(st)
+    return {"workload": "queries of 4..512 variants, 32-128-128-1, bf16 + re-score", "runs": runs}
+
+
+def training_leg(dev, steps=20):
+    """Training steps of the 64-256-256-256-1 network on 65,536-row batches
+    (forward, MSE on ln runtime, hand-written backward, Adam)."""
+    import torch
+
+    from paper_2301_03636_gb300 import advisor
+    wl = W.TRAINING
+    d = torch.from_numpy(W.make_descriptors(65536, W.SEEDS["c4"])).to(dev)
+    t = torch.from_numpy(W.make_labels(d.cpu().numpy(), W.SEEDS["c4"])).to(dev)
+    f, st = advisor.advisor_extract_features(d, wl.n_features)
+    mu, sigma = advisor.advisor_fit_standardizer(f, st)
+    m = advisor.Model(wl.widths, max_rows=65536, max_kernels=1, device=dev)
+    m.set_params(wl.weights(), mu, sigma)
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        m.train_step(f, t, loss=loss)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        m.train_step(f, t, loss=loss)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    flop = 3 * 65536 * FLOP_PER_ROW   # forward + two backward GEMMs per layer (first-layer dX skipped)
+    return {"workload": "batch 65,536, 64-256-256-256-1, FP32 SIMT forward/backward + Adam",
+            "ms_per_step": ms, "steps_per_s": 1000.0 / ms, "tflops": flop / (ms / 1000.0) / 1e12,
+            "loss_after": float(loss.item())}
 
 
 def run_reference(args):
@@ -339,6 +402,10 @@ def main():
             extras[p] = {"variants_per_s": n / (msp / 1000.0), "ms_per_step": msp,
                          "max_abs_err_vs_fp64": float((y - y64).abs().max().item()), "eps": e_p}
         out["precisions"] = extras
+        out["serving"] = serving_leg(dev)
+        srv10 = [r for r in out["serving"]["runs"] if r["rate_per_s"] == 10000]
+        out["p99_query_ms"] = srv10[0]["p99_ms"] if srv10 else None
+        out["training"] = training_leg(dev)
         # the CPU oracle on the host cores (bounded sample)
         import oracle
         fc, sc = oracle.extract_features(W.calibration_descriptors(65536), WL.n_features)
