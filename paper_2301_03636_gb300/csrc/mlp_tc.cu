@@ -11,15 +11,15 @@
 //                ring (a bulk copy costs a fixed ~550 cycles, so copies are
 //                kept as large as the ring allows);
 //   warp 1       MMA issuer (one thread) and tensor-memory owner;
-//   warps 2-17   two epilogue groups of eight warps; group g owns "slot" g:
-//                one 128-row tile, its activation buffer in shared memory and
-//                its accumulator columns in tensor memory.  Warp w reads TMEM
-//                lanes 32*(w%4) .. 32*(w%4)+31 (one row per thread); the two
-//                warps of a lane quadrant split the columns in halves.
-// The CTA works on two tiles at once (slots 0 and 1) and issues each layer
-// slot by slot, so that the epilogue of one slot (TMEM -> registers -> bias,
-// ReLU, 16-bit -> shared memory) runs while the tensor core computes the
-// same layer for the other slot.  The activations never leave shared memory
+//   warps 2-17   sixteen epilogue warps.  Warp w reads TMEM lanes
+//                32*(w%4) .. 32*(w%4)+31 (one row per thread); the four warps
+//                of a lane quadrant take one quarter of the columns each.
+// The CTA works on two 128-row tiles at once ("slots" 0 and 1: an activation
+// buffer in shared memory and accumulator columns in tensor memory each) and
+// issues each layer slot by slot.  All sixteen epilogue warps turn one slot's
+// accumulator into the next layer's activations (TMEM -> registers -> bias,
+// ReLU, 16-bit -> shared memory) while the tensor core computes the same
+// layer for the other slot, then move on to that slot.  The activations never leave shared memory
 // between layers.  Activation and weight images are 64-column slabs of
 // 128-byte rows with the 128B swizzle, the K-major layout the UMMA
 // shared-memory descriptors read.  All waits are bounded by %globaltimer and
@@ -64,8 +64,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
     uint8_t* act[2] = {base, base + act_bytes};
     uint8_t* wst = base + 2 * act_bytes;
     const uint32_t stage_bytes = (uint32_t)a.nmax * ADV_SLAB_ROW_BYTES;   // one K slab of all N rows
-    float* red = reinterpret_cast<float*>(wst + TC_STAGES * stage_bytes);     // [2][128] partial sums
-    uint64_t* bars = reinterpret_cast<uint64_t*>(red + 2 * ADV_TILE_M);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wst + TC_STAGES * stage_bytes);
     uint64_t* w_full = bars;
     uint64_t* w_empty = bars + TC_STAGES;
     uint64_t* x_full = bars + 2 * TC_STAGES;
@@ -88,8 +87,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
         for (int s = 0; s < 2; ++s) {
             mbar_init(&x_full[s], 1);
             mbar_init(&acc_full[s], 1);
-            mbar_init(&act_ready[s], 256);
-            mbar_init(&red_full[s], 128);
+            mbar_init(&act_ready[s], 512);
+            mbar_init(&red_full[s], 384);   // column quarters 1..3 of all four lane quadrants
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -195,101 +194,133 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
             }
         }
     } else {
-        // ---------------- epilogue groups ----------------
+        // ---------------- epilogue warps ----------------
         const int e = warp - 2;                     // 0..15
-        const int g = e >> 3;                       // slot
-        const int j = (e >> 2) & 1;                 // which part of each N-half
+        const int j = e >> 2;                       // column quarter
         const int quad = warp & 3;                  // TMEM lane quadrant
         const uint32_t r = (uint32_t)(quad * 32 + lane);
-        const bool leader = (e & 7) == 0 && lane == 0;
+        const bool leader = e == 0 && lane == 0;
         const bool tr = (e & 3) == 0 && lane == 0;
         const int nslab0 = a.nslab[0];
         const uint32_t x_bytes = (uint32_t)nslab0 * ADV_X_SLAB_BYTES;
-        uint8_t* my_act = act[g];
-        const uint32_t t_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * a.nmax);
-        uint32_t accph = 0, redph = 0, xph = 0;
-        int x_pending = 0;
-        auto load_x = [&](int tile) {
-            mbar_expect_tx(&x_full[g], x_bytes);
+        uint32_t accph[2] = {0, 0}, redph[2] = {0, 0}, xph[2] = {0, 0};
+        int x_pending[2] = {0, 0};
+        auto load_x = [&](int s, int tile) {
+            mbar_expect_tx(&x_full[s], x_bytes);
             const uint8_t* src = a.x_img + (size_t)tile * x_bytes;
             for (int k = 0; k < nslab0; ++k)
-                bulk_g2s(my_act + (size_t)k * ADV_X_SLAB_BYTES, src + (size_t)k * ADV_X_SLAB_BYTES,
-                         ADV_X_SLAB_BYTES, &x_full[g]);
+                bulk_g2s(act[s] + (size_t)k * ADV_X_SLAB_BYTES, src + (size_t)k * ADV_X_SLAB_BYTES,
+                         ADV_X_SLAB_BYTES, &x_full[s]);
         };
-        if (leader && g < n_my) { load_x(b + g * G); x_pending = 1; }
+        if (leader) {
+            for (int s = 0; s < 2 && s < n_my; ++s) { load_x(s, b + s * G); x_pending[s] = 1; }
+        }
         bool ok = true;
-        for (int i = g; i < n_my && ok; i += 2) {
-            const int tile = b + i * G;
-            const int64_t row = (int64_t)tile * ADV_TILE_M + r;
-            for (int l = 0; l < a.n_hidden; ++l) {
-                if (tr) TC_TRACE(4096 + ((i * 8 + l) * 2 + j) * 4 + 0);
-                const bool got = mbar_wait_bounded(&acc_full[g], accph, a.status_word, abort_flag, lim);
-                __syncwarp();   // tcgen05.ld / wait::ld are warp-collective (.sync.aligned)
-                if (!got) { ok = false; break; }
-                accph ^= 1u;
-                if (l == 0) { x_pending = 0; xph ^= 1u; }   // the MMAs consumed the X tile
-                if (tr) TC_TRACE(4096 + ((i * 8 + l) * 2 + j) * 4 + 1);
-                tc_fence_after();
-                const float* __restrict__ bias = a.bias[l];
-                const int cw = a.npad[l] >> 1;              // columns of this warp: [cb, cb + cw)
-                const int cb = j * cw;
+        for (int p = 0; p < n_pairs && ok; ++p) {
+            const int ns = (2 * p + 1 < n_my) ? 2 : 1;
+            for (int l = 0; l < a.n_hidden && ok; ++l) {
                 const bool last = (l + 1 == a.n_hidden);
-                float y4[4] = {0.f, 0.f, 0.f, 0.f};
-                if (last && leader && i + 2 < n_my) { load_x(b + (i + 2) * G); x_pending = 1; }   // X buffer is free
-                for (int c0 = cb; c0 < cb + cw; c0 += 32) {
-                    float4 bv[8];
+                const float* __restrict__ bias = a.bias[l];
+                const int cw = a.npad[l] >> 2;              // this warp's columns: [cb, cb + cw), cw % 16 == 0
+                const int cb = j * cw;
+                for (int s = 0; s < ns; ++s) {
+                    const int i = 2 * p + s;                // tile index within this CTA
+                    if (tr) TC_TRACE(4096 + ((i * 8 + l) * 2 + (j & 1)) * 4 + 0);
+                    const bool got = mbar_wait_bounded(&acc_full[s], accph[s], a.status_word, abort_flag, lim);
+                    __syncwarp();   // tcgen05.ld / st / wait are warp-collective (.sync.aligned)
+                    if (!got) { ok = false; break; }
+                    accph[s] ^= 1u;
+                    if (l == 0) { x_pending[s] = 0; xph[s] ^= 1u; }   // the MMAs consumed the X tile
+                    if (tr) TC_TRACE(4096 + ((i * 8 + l) * 2 + (j & 1)) * 4 + 1);
+                    tc_fence_after();
+                    // the X buffer of this slot is free: every MMA that read it has completed
+                    if (last && leader && i + 2 < n_my) { load_x(s, b + (i + 2) * G); x_pending[s] = 1; }
+                    const uint32_t t_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * a.nmax);
+                    uint8_t* my_act = act[s];
+                    float y4[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int c0 = cb; c0 < cb + cw; c0 += 32) {
+                        const bool two = c0 + 16 < cb + cw;     // a second 16-column group in this step
+                        uint32_t v0[16], v1[16];
+                        tmem_ld_32x32b_x16(t_base + (uint32_t)c0, v0);
+                        if (two) tmem_ld_32x32b_x16(t_base + (uint32_t)(c0 + 16), v1);
+                        float4 bq[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) bv[q] = __ldg(reinterpret_cast<const float4*>(bias + c0) + q);
-                    uint32_t v[32];
-                    tmem_ld_32x32b_x32(t_base + (uint32_t)c0, v);
-                    tmem_wait_ld();
-                    const float* bf = reinterpret_cast<const float*>(bv);
-                    if (!last) {
-                        uint8_t* slab = my_act + (size_t)(c0 >> 6) * ADV_X_SLAB_BYTES;
+                        for (int q = 0; q < 8; ++q)
+                            bq[q] = (q < 4 || two) ? __ldg(reinterpret_cast<const float4*>(bias + c0) + q)
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                        tmem_wait_ld();
+                        const float* bf = reinterpret_cast<const float*>(bq);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            uint32_t pk[4];
+                        for (int h = 0; h < 2; ++h) {
+                            if (h == 1 && !two) break;
+                            const uint32_t* v = h ? v1 : v0;
+                            const int c = c0 + 16 * h;
+                            if (!last) {
+                                uint8_t* slab = my_act + (size_t)(c >> 6) * ADV_X_SLAB_BYTES;
 #pragma unroll
-                            for (int t = 0; t < 4; ++t) {
-                                const int cc = 8 * q + 2 * t;
-                                pk[t] = relu_pack<FMT>(__uint_as_float(v[cc]) + bf[cc], __uint_as_float(v[cc + 1]) + bf[cc + 1]);
+                                for (int q = 0; q < 2; ++q) {
+                                    uint32_t pk[4];
+#pragma unroll
+                                    for (int t = 0; t < 4; ++t) {
+                                        const int cc = 8 * q + 2 * t;
+                                        pk[t] = relu_pack<FMT>(__uint_as_float(v[cc]) + bf[16 * h + cc],
+                                                               __uint_as_float(v[cc + 1]) + bf[16 * h + cc + 1]);
+                                    }
+                                    const uint32_t chunk = (uint32_t)(((c & 63) >> 3) + q);
+                                    *reinterpret_cast<uint4*>(slab + sw128_offset(r, chunk)) =
+                                        make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                                }
+                            } else {
+                                const float4* w4 = reinterpret_cast<const float4*>(a.w_out + c);
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    const float4 wq = __ldg(w4 + u);
+                                    const float* bb = bf + 16 * h + 4 * u;
+                                    y4[0] = fmaf(fmaxf(__uint_as_float(v[4 * u + 0]) + bb[0], 0.f), wq.x, y4[0]);
+                                    y4[1] = fmaf(fmaxf(__uint_as_float(v[4 * u + 1]) + bb[1], 0.f), wq.y, y4[1]);
+                                    y4[2] = fmaf(fmaxf(__uint_as_float(v[4 * u + 2]) + bb[2], 0.f), wq.z, y4[2]);
+                                    y4[3] = fmaf(fmaxf(__uint_as_float(v[4 * u + 3]) + bb[3], 0.f), wq.w, y4[3]);
+                                }
                             }
-                            const uint32_t chunk = (uint32_t)(((c0 & 63) >> 3) + q);
-                            *reinterpret_cast<uint4*>(slab + sw128_offset(r, chunk)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                        }
-                    } else {
-                        float4 wv[8];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) wv[q] = __ldg(reinterpret_cast<const float4*>(a.w_out + c0) + q);
-                        const float* wf = reinterpret_cast<const float*>(wv);
-#pragma unroll
-                        for (int cc = 0; cc < 32; ++cc)
-                            y4[cc & 3] = fmaf(fmaxf(__uint_as_float(v[cc]) + bf[cc], 0.f), wf[cc], y4[cc & 3]);
-                    }
-                }
-                if (!last) {
-                    fence_proxy_async_smem();   // make the generic stores visible to the tensor core
-                } else {
-                    float y = (y4[0] + y4[1]) + (y4[2] + y4[3]);
-                    // combine the two column halves of each row (fixed order: low half + high half)
-                    if (j == 1) {
-                        red[g * ADV_TILE_M + r] = y;
-                        mbar_arrive(&red_full[g]);
-                    } else {
-                        const bool gr = mbar_wait_bounded(&red_full[g], redph, a.status_word, abort_flag, lim);
-                        if (gr) {
-                            y = y + red[g * ADV_TILE_M + r] + __ldg(a.b_out);
-                            if (row < a.n_rows) a.scores[row] = (a.status && a.status[row]) ? INFINITY : y;
                         }
                     }
-                    redph ^= 1u;
+                    if (!last) {
+                        fence_proxy_async_smem();   // make the generic stores visible to the tensor core
+                    } else {
+                        // combine the four column quarters of each row in a fixed order: quarters
+                        // 1..3 park their partial sums in their own (already read) TMEM columns
+                        float y = (y4[0] + y4[1]) + (y4[2] + y4[3]);
+                        if (j != 0) {
+                            tmem_st_32x32b_x1(t_base + (uint32_t)cb, __float_as_uint(y));
+                            tmem_wait_st();
+                            tc_fence_before();
+                            mbar_arrive(&red_full[s]);
+                        } else {
+                            const bool gr = mbar_wait_bounded(&red_full[s], redph[s], a.status_word, abort_flag, lim);
+                            __syncwarp();
+                            if (gr) {
+                                tc_fence_after();
+                                const float y1 = __uint_as_float(tmem_ld_32x32b_x1(t_base + (uint32_t)cw));
+                                const float y2 = __uint_as_float(tmem_ld_32x32b_x1(t_base + (uint32_t)(2 * cw)));
+                                const float y3 = __uint_as_float(tmem_ld_32x32b_x1(t_base + (uint32_t)(3 * cw)));
+                                tmem_wait_ld();
+                                y = ((y + y1) + y2) + y3 + __ldg(a.b_out);
+                                const int64_t row = (int64_t)(b + i * G) * ADV_TILE_M + r;
+                                if (row < a.n_rows) a.scores[row] = (a.status && a.status[row]) ? INFINITY : y;
+                            }
+                        }
+                        redph[s] ^= 1u;
+                    }
+                    if (tr) TC_TRACE(4096 + ((i * 8 + l) * 2 + (j & 1)) * 4 + 2);
+                    tc_fence_before();
+                    mbar_arrive(&act_ready[s]);
                 }
-                if (tr) TC_TRACE(4096 + ((i * 8 + l) * 2 + j) * 4 + 2);
-                tc_fence_before();
-                mbar_arrive(&act_ready[g]);
             }
         }
-        if (leader && x_pending) mbar_wait_bounded(&x_full[g], xph, a.status_word, abort_flag, lim);
+        if (leader) {
+            for (int s = 0; s < 2; ++s)
+                if (x_pending[s]) mbar_wait_bounded(&x_full[s], xph[s], a.status_word, abort_flag, lim);
+        }
     }
 
     tc_fence_before();
@@ -303,7 +334,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
 size_t mlp_tc_smem_bytes(int nslab_max, int nmax, int n_hidden) {
     (void)n_hidden;
     return (size_t)2 * nslab_max * ADV_X_SLAB_BYTES + (size_t)TC_STAGES * nmax * ADV_SLAB_ROW_BYTES +
-           (2 * TC_STAGES + 9) * sizeof(uint64_t) + 2 * ADV_TILE_M * sizeof(float) + 16 + 1024;
+           (2 * TC_STAGES + 9) * sizeof(uint64_t) + 16 + 1024;
 }
 
 cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s) {
