@@ -212,6 +212,58 @@ advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_des
                             int32_t* d_best_local, double* d_best_score, float* d_scores,
                             uint8_t* d_row_status, cudaStream_t stream);
 
+/* Launch shapes of the hot path (the batching of many kernels' variants
+ * into persistent launches).  Every setting gives bit-identical results:
+ * rows, tiles and segments run the same per-row / per-segment code whatever
+ * the grid or block, and no summation order depends on them. */
+typedef struct {
+    int32_t extract_block;      /* threads per block of the extraction kernel: 64, 128 or 256 */
+    int32_t tc_ctas;            /* CTAs of the persistent tensor-core scorer (at most one per SM; 0 = one per SM) */
+    int32_t list_blocks_per_sm; /* FP32 near-tie scorer: persistent 16-row blocks per SM, 1 or 2 */
+    int32_t list_chunk_kb;      /* FP32 near-tie scorer: weight chunk per bulk copy, 16 or 32 (KB) */
+    int32_t select_block;       /* threads per block of the selection kernels (a warp per kernel): 128 or 256 */
+} advisor_launch_config;
+
+/* The model's launch shapes (defaults 128, 0, 1, 32, 256), used by every
+ * later call.  set returns ADVISOR_ERR_INVALID_ARGUMENT for a value outside
+ * the lists above and leaves the configuration unchanged. */
+advisor_status advisor_model_get_launch_config(advisor_model_t m, advisor_launch_config* out);
+advisor_status advisor_model_set_launch_config(advisor_model_t m, const advisor_launch_config* cfg);
+
+/* Batching under a CUDA graph: advisor_rank with these arguments, captured
+ * once into a graph ("plan") that later calls replay with one launch.  The
+ * plan binds every pointer as given: a replay reads the current contents of
+ * d_desc and d_seg_off (same n_rows and n_kernels) and writes the same
+ * outputs, so a caller refills the input buffers in place between replays.
+ * autotune != 0: first time each launch configuration of a small candidate
+ * set (one setting at a time, in path order; each candidate captured and
+ * replayed on `stream`, which runs the path and overwrites the outputs) and
+ * capture the fastest; autotune == 0 captures the model's current
+ * configuration.  Either way the model's own configuration is left as it
+ * was.  Creating a plan synchronises `stream`; capture happens on a private
+ * stream.  The model must stay alive, bound to the same buffers, while the
+ * plan exists; profile events set on the model are recorded by every
+ * replay.  Errors: those of advisor_rank, and ADVISOR_ERR_CUDA when the
+ * capture or instantiation fails. */
+typedef struct advisor_plan* advisor_plan_t;
+advisor_status advisor_plan_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                                 const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
+                                 float eps_scores, float eps_fp32, int32_t* d_best_local,
+                                 double* d_best_score, float* d_scores, uint8_t* d_row_status,
+                                 int32_t autotune, cudaStream_t stream, advisor_plan_t* out);
+
+/* Replay the plan on `stream` (asynchronous: one graph launch). */
+advisor_status advisor_plan_launch(advisor_plan_t p, cudaStream_t stream);
+
+/* The configuration the plan was captured with; *replay_us (nullable) the
+ * median replay time the autotuner measured for it (0 without autotuning);
+ * *kernels_per_replay (nullable) the kernel nodes in the graph. */
+advisor_status advisor_plan_info(advisor_plan_t p, advisor_launch_config* cfg, float* replay_us,
+                                 int32_t* kernels_per_replay);
+
+/* Release the graph (NULL is a no-op). */
+advisor_status advisor_plan_destroy(advisor_plan_t p);
+
 /* a8: one training step (Sec. 3 training mode; Sec. 5 Exp. 3): forward,
  * loss = 0.5 * mean (y - label)^2 over the n_rows rows (labels: ln runtime),
  * hand-written backward, Adam update of the FP32 master weights followed by

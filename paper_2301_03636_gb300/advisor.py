@@ -73,6 +73,12 @@ def lib():
         "advisor_model_master_offset": (sz, [P]),
         "advisor_model_get_adam_step": (i64, [P]),
         "advisor_model_set_adam_step": (st, [P, i64]),
+        "advisor_model_get_launch_config": (st, [P, P]),
+        "advisor_model_set_launch_config": (st, [P, P]),
+        "advisor_plan_rank": (st, [P, P, i64, P, i64, st, f32, f32, P, P, P, P, i32, P, ctypes.POINTER(P)]),
+        "advisor_plan_launch": (st, [P, P]),
+        "advisor_plan_info": (st, [P, P, P, P]),
+        "advisor_plan_destroy": (st, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -80,6 +86,16 @@ def lib():
         fn.argtypes = args
     _lib = L
     return L
+
+
+class LaunchConfig(ctypes.Structure):
+    """advisor_launch_config: launch shapes of the hot path (results do not depend on them)."""
+    _fields_ = [("extract_block", ctypes.c_int32), ("tc_ctas", ctypes.c_int32),
+                ("list_blocks_per_sm", ctypes.c_int32), ("list_chunk_kb", ctypes.c_int32),
+                ("select_block", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 def header_functions() -> list[str]:
@@ -242,6 +258,20 @@ class Model:
                                   _stream(stream)), "advisor_rank")
         return best, best_score
 
+    @property
+    def launch_config(self) -> LaunchConfig:
+        c = LaunchConfig()
+        _check(lib().advisor_model_get_launch_config(self.handle, ctypes.byref(c)), "get_launch_config")
+        return c
+
+    @launch_config.setter
+    def launch_config(self, c: LaunchConfig):
+        _check(lib().advisor_model_set_launch_config(self.handle, ctypes.byref(c)), "set_launch_config")
+
+    def plan_rank(self, desc, offsets, precision="bf16", eps=-1.0, eps32=0.0, autotune=False, stream=None):
+        """A Plan replaying rank() on these buffers (refill desc / offsets in place between launches)."""
+        return Plan(self, desc, offsets, precision, eps, eps32, autotune, stream)
+
     def train_step(self, feat, labels, precision="fp32", lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
                    weight_decay=0.0, loss=None, stream=None):
         h = (ctypes.c_float * 5)(lr, beta1, beta2, eps, weight_decay)
@@ -308,6 +338,53 @@ class Model:
         y64 = self.score_fp64(feat, status)
         ok = torch.isfinite(y64)
         return float(safety * (y[ok] - y64[ok]).abs().max().item())
+
+
+class Plan:
+    """advisor_plan_rank: Model.rank captured into a CUDA graph, replayed by launch().
+
+    The plan keeps the input and output tensors alive; launch() reads the
+    current contents of `desc` and `offsets` and writes best / best_score /
+    scores / status in place."""
+
+    def __init__(self, model: Model, desc, offsets, precision="bf16", eps=-1.0, eps32=0.0, autotune=False,
+                 stream=None):
+        self.model = model
+        self.desc, self.offsets = desc, offsets
+        K = offsets.shape[0] - 1
+        self.best = torch.empty(K, dtype=torch.int32, device=model.device)
+        self.best_score = torch.empty(K, dtype=torch.float64, device=model.device)
+        self.scores = torch.empty(desc.shape[0], dtype=torch.float32, device=model.device)
+        self.status = torch.empty(desc.shape[0], dtype=torch.uint8, device=model.device)
+        h = ctypes.c_void_p()
+        _check(lib().advisor_plan_rank(model.handle, _ptr(desc), desc.shape[0], _ptr(offsets), K, _prec(precision),
+                                       float(eps), float(eps32), _ptr(self.best), _ptr(self.best_score),
+                                       _ptr(self.scores), _ptr(self.status), 1 if autotune else 0, _stream(stream),
+                                       ctypes.byref(h)), "advisor_plan_rank")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib().advisor_plan_launch(self.handle, _stream(stream)), "advisor_plan_launch")
+        return self.best, self.best_score
+
+    def info(self):
+        c = LaunchConfig()
+        us = ctypes.c_float()
+        k = ctypes.c_int32()
+        _check(lib().advisor_plan_info(self.handle, ctypes.byref(c), ctypes.byref(us), ctypes.byref(k)),
+               "advisor_plan_info")
+        return {"config": c.as_dict(), "replay_us": float(us.value), "kernels_per_replay": int(k.value)}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.advisor_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class MLPFunction(torch.autograd.Function):

@@ -44,6 +44,7 @@ struct advisor_model {
     cudaEvent_t prof_start = nullptr, prof_stop = nullptr;   // bracket the tensor-core scorer launch
     int64_t adam_step = 0;
     int64_t saved_rows = 0;   // rows of the last advisor_forward_saved
+    adv::LaunchConfig cfg{};  // launch shapes of the hot path (a plan may set them)
 };
 
 namespace {
@@ -134,13 +135,23 @@ advisor_status check_ready(const advisor_model* m, int64_t n_rows) {
     return ADVISOR_OK;
 }
 
+// Inside a stream capture the records become event nodes of the graph, so a
+// replayed plan still brackets the scorer.
+cudaError_t record_event(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev, s);
+}
+
 cudaError_t launch_tc_profiled(advisor_model* m, const adv::TcArgs& a, cudaStream_t s) {
     if (m->prof_start) {
-        cudaError_t e = cudaEventRecord(m->prof_start, s);
+        cudaError_t e = record_event(m->prof_start, s);
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e = adv::launch_mlp_tc(a, m->num_sms, s);
-    if (e == cudaSuccess && m->prof_stop) e = cudaEventRecord(m->prof_stop, s);
+    cudaError_t e = adv::launch_mlp_tc(a, m->num_sms, s, m->cfg.tc_ctas);
+    if (e == cudaSuccess && m->prof_stop) e = record_event(m->prof_stop, s);
     return e;
 }
 
@@ -172,16 +183,17 @@ advisor_status do_select(advisor_model* m, const float* scores, int64_t n_rows, 
         e = cudaMemsetAsync(a.counters, 0, 2 * sizeof(int), s);
         if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     }
-    e = adv::launch_select_tier1(a, s);
+    e = adv::launch_select_tier1(a, s, m->cfg.select_block);
     if (e != cudaSuccess || !rescore) return cuda_status(e);
     const adv::MlpDesc md = mlp_desc(m);
     adv::RowSrc r1 = src;
     r1.rows = a.cand_rows;
     r1.count_dev = &a.counters[0];
     r1.count = 0;
-    e = adv::launch_mlp_fp32(md, r1, a.y32, m->num_sms, true, s, a.status_word);
+    e = adv::launch_mlp_fp32(md, r1, a.y32, m->num_sms, true, s, a.status_word, m->cfg.list_blocks_per_sm,
+                             m->cfg.list_chunk_kb);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
-    e = adv::launch_select_tier2(a, s);
+    e = adv::launch_select_tier2(a, s, m->cfg.select_block);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     adv::RowSrc r2 = src;
     r2.rows = a.cand2_rows;
@@ -189,7 +201,7 @@ advisor_status do_select(advisor_model* m, const float* scores, int64_t n_rows, 
     r2.count = 0;
     e = adv::launch_mlp_fp64(md, r2, a.y64, m->num_sms, s);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
-    return cuda_status(adv::launch_select_final(a, s));
+    return cuda_status(adv::launch_select_final(a, s, m->cfg.select_block));
 }
 
 }  // namespace
@@ -211,6 +223,29 @@ const char* advisor_status_string(advisor_status s) {
 }
 
 int64_t advisor_launch_count(void) { return (int64_t)g_launches.load(); }
+
+advisor_status advisor_model_get_launch_config(advisor_model_t m, advisor_launch_config* out) {
+    if (!m || !out) return ADVISOR_ERR_INVALID_ARGUMENT;
+    out->extract_block = m->cfg.extract_block;
+    out->tc_ctas = m->cfg.tc_ctas;
+    out->list_blocks_per_sm = m->cfg.list_blocks_per_sm;
+    out->list_chunk_kb = m->cfg.list_chunk_kb;
+    out->select_block = m->cfg.select_block;
+    return ADVISOR_OK;
+}
+
+advisor_status advisor_model_set_launch_config(advisor_model_t m, const advisor_launch_config* c) {
+    if (!m || !c) return ADVISOR_ERR_INVALID_ARGUMENT;
+    adv::LaunchConfig n;
+    n.extract_block = c->extract_block;
+    n.tc_ctas = c->tc_ctas;
+    n.list_blocks_per_sm = c->list_blocks_per_sm;
+    n.list_chunk_kb = c->list_chunk_kb;
+    n.select_block = c->select_block;
+    if (!adv::launch_config_valid(n)) return ADVISOR_ERR_INVALID_ARGUMENT;
+    m->cfg = n;
+    return ADVISOR_OK;
+}
 
 advisor_status advisor_model_create(const int32_t* h_widths, int32_t n_widths, advisor_model_t* out) {
     if (!h_widths || !out || n_widths < 3 || n_widths > ADV_MAX_LAYERS) return ADVISOR_ERR_INVALID_ARGUMENT;
@@ -425,7 +460,7 @@ advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_des
         if (precision == ADVISOR_FP32) {
             a.n_rows_padded = n_rows;
             a.feat = reinterpret_cast<int32_t*>(m->WS + m->W.feat32);
-            e = adv::launch_extract(a, L.F, 0, stream);
+            e = adv::launch_extract(a, L.F, 0, stream, m->cfg.extract_block);
             if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
             adv::RowSrc src{a.feat, nullptr, nullptr, nullptr, n_rows, status};
             e = adv::launch_mlp_fp32(mlp_desc(m), src, scores, m->num_sms, false, stream);
@@ -440,7 +475,7 @@ advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_des
         a.n_rows_padded = ((n_rows + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
         a.x_img = m->WS + m->W.x_img;
         a.nslab = L.nslab[0];
-        e = adv::launch_extract(a, L.F, fi == 0 ? 1 : 2, stream);
+        e = adv::launch_extract(a, L.F, fi == 0 ? 1 : 2, stream, m->cfg.extract_block);
         if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
         e = launch_tc_profiled(m, tc_args(m, a.x_img, n_rows, status, scores, fi), stream);
         if (e != cudaSuccess) return ADVISOR_ERR_CUDA;

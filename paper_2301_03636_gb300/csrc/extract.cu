@@ -66,7 +66,7 @@ __device__ __forceinline__ void write_x_row(uint8_t* x_img, int nslab, int64_t r
 
 
 template <int F, int FMT>
-__global__ void __launch_bounds__(128) extract_kernel(ExtractArgs a) {
+__global__ void __launch_bounds__(256) extract_kernel(ExtractArgs a) {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= a.n_rows_padded) return;
     int32_t f[F];
@@ -173,22 +173,23 @@ __global__ void __launch_bounds__(256) fit_standardizer_kernel(const int32_t* __
 
 // ---- host launchers ------------------------------------------------------------
 template <int F>
-static cudaError_t launch_extract_f(const ExtractArgs& a, int fmt, cudaStream_t s) {
+static cudaError_t launch_extract_f(const ExtractArgs& a, int fmt, cudaStream_t s, int block) {
     const int64_t rows = a.n_rows_padded;
-    const unsigned grid = (unsigned)((rows + 127) / 128);
+    const unsigned grid = (unsigned)((rows + block - 1) / block);
     if (grid == 0) return cudaSuccess;
-    if (fmt == 1) extract_kernel<F, 1><<<grid, 128, 0, s>>>(a);
-    else if (fmt == 2) extract_kernel<F, 2><<<grid, 128, 0, s>>>(a);
-    else extract_kernel<F, 0><<<grid, 128, 0, s>>>(a);
+    if (fmt == 1) extract_kernel<F, 1><<<grid, block, 0, s>>>(a);
+    else if (fmt == 2) extract_kernel<F, 2><<<grid, block, 0, s>>>(a);
+    else extract_kernel<F, 0><<<grid, block, 0, s>>>(a);
     adv_count_launch(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_extract(const ExtractArgs& a, int F, int fmt, cudaStream_t s) {
+cudaError_t launch_extract(const ExtractArgs& a, int F, int fmt, cudaStream_t s, int block) {
+    if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;
     switch (F) {
-        case 32: return launch_extract_f<32>(a, fmt, s);
-        case 64: return launch_extract_f<64>(a, fmt, s);
-        case 128: return launch_extract_f<128>(a, fmt, s);
+        case 32: return launch_extract_f<32>(a, fmt, s, block);
+        case 64: return launch_extract_f<64>(a, fmt, s, block);
+        case 128: return launch_extract_f<128>(a, fmt, s, block);
         default: return cudaErrorInvalidValue;
     }
 }

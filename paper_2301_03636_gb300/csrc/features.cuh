@@ -103,31 +103,51 @@ __device__ __forceinline__ void log2_q16_batch(const uint64_t (&x)[N], int32_t (
     for (int i = 0; i < N; ++i) out[i] = (int32_t)acc[i];
 }
 
-// The F features of a valid row (F = 32, 64 or 128).
+// Number of logarithms behind the F features of a row: 19 for the 32 base
+// features, 16 more for the per-loop-level block (F >= 64).
 template <int F>
-__device__ __forceinline__ void row_features(const int64_t (&d)[16], int32_t (&f)[F]) {
-    constexpr int32_t ONE = 65536;
-    const int depth = (int)d[0];
+struct FeatureLogs {
+    static constexpr int N = F >= 64 ? 35 : 19;
+};
+
+// Indices of the base logarithm arguments (0 .. 18); the per-level block
+// follows at 19 + 4 * level + {prefix, suffix, trip*bytes, trip*flops}.
+enum { A_T0 = 0, A_T = 4, A_FL_IT, A_BY_IT, A_WF, A_WB, A_H2D, A_D2H, A_MAP, A_TEAMS, A_THREADS, A_PAR, A_D, A_Q,
+       A_MIN, A_BASE_N, A_LEVEL = A_BASE_N };
+
+struct RowFields {
+    int depth, pf, dc, pc, sched, dmode, n_dist;
+};
+
+__device__ __forceinline__ RowFields row_fields(const int64_t (&d)[16]) {
+    RowFields r;
+    r.depth = (int)d[0];
+    r.pf = (int)d[11];
+    r.dc = (int)d[12];
+    r.pc = (int)d[13];
+    r.sched = (int)d[14];
+    r.dmode = (int)d[15];
+    // 'teams distribute' covers loops [0, n_dist); combined with 'parallel for' when pf == 0
+    r.n_dist = (r.pf == 0) ? r.pc : r.dc;
+    return r;
+}
+
+// The arguments of every logarithm the F features of a valid row take.
+template <int F>
+__device__ __forceinline__ void row_log_args(const int64_t (&d)[16], uint64_t (&x)[FeatureLogs<F>::N]) {
+    const RowFields r = row_fields(d);
     const uint64_t t[4] = {(uint64_t)d[1], (uint64_t)d[2], (uint64_t)d[3], (uint64_t)d[4]};
     const uint64_t flops = (uint64_t)d[5], bytes = (uint64_t)d[6];
     const uint64_t h2d = (uint64_t)d[7], d2h = (uint64_t)d[8];
     const uint64_t teams = (uint64_t)d[9], threads = (uint64_t)d[10];
-    const int pf = (int)d[11], dc = (int)d[12], pc = (int)d[13], sched = (int)d[14], dmode = (int)d[15];
-
     const uint64_t T = t[0] * t[1] * t[2] * t[3];
     const uint64_t par = teams * threads;
-    // 'teams distribute' covers loops [0, n_dist); combined with 'parallel for' when pf == 0
-    const int n_dist = (pf == 0) ? pc : dc;
     uint64_t Dp = 1, Qp = 1;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        if (i < n_dist) Dp *= t[i];
-        if (i >= pf && i < pf + pc) Qp *= t[i];
+        if (i < r.n_dist) Dp *= t[i];
+        if (i >= r.pf && i < r.pf + r.pc) Qp *= t[i];
     }
-    // arguments of every logarithm of the base features
-    enum { A_T0 = 0, A_T = 4, A_FL_IT, A_BY_IT, A_WF, A_WB, A_H2D, A_D2H, A_MAP, A_TEAMS, A_THREADS, A_PAR, A_D, A_Q,
-           A_MIN, NA };
-    uint64_t x[NA];
 #pragma unroll
     for (int i = 0; i < 4; ++i) x[A_T0 + i] = t[i];
     x[A_T] = T;
@@ -144,11 +164,34 @@ __device__ __forceinline__ void row_features(const int64_t (&d)[16], int32_t (&f
     x[A_D] = Dp;
     x[A_Q] = Qp;
     x[A_MIN] = T < par ? T : par;
-    int32_t L[NA];
-    log2_q16_batch<NA>(x, L);
+    if constexpr (F >= 64) {
+        // per loop level: prefix product, suffix product, trip*bytes/iter,
+        // trip*flops/iter; arguments of 1 beyond the depth (logarithm 0)
+        uint64_t prefix = 1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool live = i < r.depth;
+            prefix *= t[i];
+            uint64_t suffix = 1;
+#pragma unroll
+            for (int j = i; j < 4; ++j) suffix *= (j < r.depth) ? t[j] : 1;
+            x[A_LEVEL + 4 * i + 0] = live ? prefix : 1;
+            x[A_LEVEL + 4 * i + 1] = live ? suffix : 1;
+            x[A_LEVEL + 4 * i + 2] = live ? t[i] * bytes : 1;
+            x[A_LEVEL + 4 * i + 3] = live ? t[i] * flops : 1;
+        }
+    }
+}
 
+// The F features of a valid row from its fields and the logarithms of the
+// arguments row_log_args lists.
+template <int F>
+__device__ __forceinline__ void row_features_from_logs(const int64_t (&d)[16], const int32_t (&L)[FeatureLogs<F>::N],
+                                                       int32_t (&f)[F]) {
+    constexpr int32_t ONE = 65536;
+    const RowFields r = row_fields(d);
     int32_t base[32];
-    base[0] = depth * ONE;
+    base[0] = r.depth * ONE;
 #pragma unroll
     for (int i = 0; i < 4; ++i) base[1 + i] = L[A_T0 + i];
     base[5] = L[A_T];
@@ -169,53 +212,36 @@ __device__ __forceinline__ void row_features(const int64_t (&d)[16], int32_t (&f
     base[20] = max(L[A_Q] - L[A_THREADS], 0);
     base[21] = L[A_WF] - L[A_WB];
     base[22] = L[A_WB] - L[A_MAP];
-    base[23] = sched == 0 ? ONE : 0;
-    base[24] = sched == 1 ? ONE : 0;
-    base[25] = sched == 2 ? ONE : 0;
-    base[26] = dmode * ONE;
-    base[27] = pf * ONE;
-    base[28] = dc * ONE;
-    base[29] = pc * ONE;
-    base[30] = pf == 0 ? ONE : 0;
+    base[23] = r.sched == 0 ? ONE : 0;
+    base[24] = r.sched == 1 ? ONE : 0;
+    base[25] = r.sched == 2 ? ONE : 0;
+    base[26] = r.dmode * ONE;
+    base[27] = r.pf * ONE;
+    base[28] = r.dc * ONE;
+    base[29] = r.pc * ONE;
+    base[30] = r.pf == 0 ? ONE : 0;
     base[31] = L[A_MIN];
 #pragma unroll
     for (int j = 0; j < 32; ++j) f[j] = base[j];
     if constexpr (F >= 64) {
         // per loop level: log trip, distributed?, parallel-for?, in a collapse
         // group of >= 2 loops?, log prefix product, log suffix product,
-        // log(trip*bytes/iter), log(trip*flops/iter); zero beyond the depth
-        // (arguments of 1 there give logarithms of 0).
-        uint64_t y[16];
-        uint64_t prefix = 1;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const bool live = i < depth;
-            prefix *= t[i];
-            uint64_t suffix = 1;
-#pragma unroll
-            for (int j = i; j < 4; ++j) suffix *= (j < depth) ? t[j] : 1;
-            y[4 * i + 0] = live ? prefix : 1;
-            y[4 * i + 1] = live ? suffix : 1;
-            y[4 * i + 2] = live ? t[i] * bytes : 1;
-            y[4 * i + 3] = live ? t[i] * flops : 1;
-        }
-        int32_t Ly[16];
-        log2_q16_batch<16>(y, Ly);
+        // log(trip*bytes/iter), log(trip*flops/iter); zero beyond the depth.
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int o = 32 + 8 * i;
-            const bool live = i < depth;
-            const bool in_dist = live && i < n_dist;
-            const bool in_pf = live && (i >= pf) && (i < pf + pc);
-            const bool grouped = (in_dist && n_dist >= 2) || (in_pf && pc >= 2);
+            const bool live = i < r.depth;
+            const bool in_dist = live && i < r.n_dist;
+            const bool in_pf = live && (i >= r.pf) && (i < r.pf + r.pc);
+            const bool grouped = (in_dist && r.n_dist >= 2) || (in_pf && r.pc >= 2);
             f[o + 0] = live ? L[A_T0 + i] : 0;
             f[o + 1] = in_dist ? ONE : 0;
             f[o + 2] = in_pf ? ONE : 0;
             f[o + 3] = grouped ? ONE : 0;
-            f[o + 4] = Ly[4 * i + 0];
-            f[o + 5] = Ly[4 * i + 1];
-            f[o + 6] = Ly[4 * i + 2];
-            f[o + 7] = Ly[4 * i + 3];
+            f[o + 4] = L[A_LEVEL + 4 * i + 0];
+            f[o + 5] = L[A_LEVEL + 4 * i + 1];
+            f[o + 6] = L[A_LEVEL + 4 * i + 2];
+            f[o + 7] = L[A_LEVEL + 4 * i + 3];
         }
     }
     if constexpr (F >= 128) {
@@ -228,6 +254,63 @@ __device__ __forceinline__ void row_features(const int64_t (&d)[16], int32_t (&f
             f[64 + u] = base[a] - base[b];
         }
     }
+}
+
+// The F features of a valid row (F = 32, 64 or 128), one thread.
+template <int F>
+__device__ __forceinline__ void row_features(const int64_t (&d)[16], int32_t (&f)[F]) {
+    constexpr int N = FeatureLogs<F>::N;
+    uint64_t x[N];
+    row_log_args<F>(d, x);
+    int32_t L[N];
+    log2_q16_batch<N>(x, L);
+    row_features_from_logs<F>(d, L, f);
+}
+
+// The same features computed by a group of G lanes for one row (G = 16 or
+// 32; every lane of the warp must take part, each group with its own row):
+// lane g of the group takes the logarithms of arguments g, g + G, ..., the
+// results are exchanged by shuffles inside the group, and every lane of the
+// group assembles the (identical) feature vector, keeping features g + G q
+// in mine[q].
+template <int F, int G>
+__device__ __forceinline__ void row_features_lanes(const int64_t (&d)[16], int g, int32_t (&mine)[F / G]) {
+    static_assert(G == 8 || G == 16 || G == 32, "lane group size");
+    constexpr int N = FeatureLogs<F>::N;
+    constexpr int NL = (N + G - 1) / G;   // logarithms per lane
+    uint64_t x[N];
+    row_log_args<F>(d, x);
+    uint64_t a[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) a[q] = 1;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        if (i % G == g) a[i / G] = x[i];
+    int32_t l[NL];
+    log2_q16_batch<NL>(a, l);
+    int32_t L[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) L[i] = __shfl_sync(0xffffffffu, l[i / G], i % G, G);
+    int32_t f[F];
+    row_features_from_logs<F>(d, L, f);
+#pragma unroll
+    for (int q = 0; q < F / G; ++q) mine[q] = 0;
+#pragma unroll
+    for (int j = 0; j < F; ++j)
+        if (j % G == g) mine[j / G] = f[j];
+}
+
+// A valid placeholder descriptor (depth 1, every count 1, nothing mapped),
+// used where a lane group has no valid row but must still join the shuffles.
+__device__ __forceinline__ void placeholder_desc(int64_t (&d)[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) d[i] = 1;
+    d[7] = 0;    // h2d bytes
+    d[8] = 0;    // d2h bytes
+    d[11] = 0;   // pf_pos: combined construct
+    d[12] = 0;   // dist_collapse
+    d[14] = 0;   // schedule static
+    d[15] = 0;   // data mode
 }
 
 __device__ __forceinline__ void load_desc(const advisor_variant_desc* desc, int64_t row, int64_t (&d)[16]) {

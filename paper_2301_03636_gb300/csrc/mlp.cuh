@@ -41,7 +41,20 @@ struct ExtractArgs {
     const float* sa;         // standardisation: z = f * sa - sc
     const float* sc;
 };
-cudaError_t launch_extract(const ExtractArgs& a, int F, int fmt, cudaStream_t s);
+// Launch shapes of the hot path that a plan's autotuner may vary.  Every
+// choice gives bit-identical results: rows, segments and tiles are processed
+// by the same per-row / per-segment code whatever the grid or block shape,
+// and no summation order depends on them.
+struct LaunchConfig {
+    int extract_block = 128;       // threads per block of the extraction kernel: 64, 128 or 256
+    int tc_ctas = 0;               // CTAs of the persistent tensor-core scorer: 0 = one per SM
+    int list_blocks_per_sm = 1;    // FP32 near-tie scorer: blocks per SM, 1 or 2
+    int list_chunk_kb = 32;        // FP32 near-tie scorer: weight chunk per bulk copy, 16 or 32 KB
+    int select_block = 256;        // threads per block of the selection kernels: 128 or 256
+};
+bool launch_config_valid(const LaunchConfig& c);
+
+cudaError_t launch_extract(const ExtractArgs& a, int F, int fmt, cudaStream_t s, int block = 128);
 cudaError_t launch_standardize(const int32_t* feat, const uint8_t* status, int64_t n, int64_t npad, uint8_t* x_img,
                                int nslab, const float* sa, const float* sc, int F, int fmt, cudaStream_t s);
 cudaError_t launch_fit_standardizer(const int32_t* feat, const uint8_t* status, int64_t n, int F, double* mu,
@@ -49,7 +62,8 @@ cudaError_t launch_fit_standardizer(const int32_t* feat, const uint8_t* status, 
 
 // mlp_simt.cu
 cudaError_t launch_mlp_fp32(const MlpDesc& m, const RowSrc& src, float* out, int num_sms, bool for_list,
-                            cudaStream_t s, int* status_word = nullptr);
+                            cudaStream_t s, int* status_word = nullptr, int list_blocks_per_sm = 1,
+                            int list_chunk_kb = 32);
 cudaError_t launch_mlp_fp64(const MlpDesc& m, const RowSrc& src, double* out, int num_sms, cudaStream_t s);
 
 // mlp_tc.cu
@@ -71,7 +85,7 @@ struct TcArgs {
     int* status_word;
     unsigned long long timeout_ns;
 };
-cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s, int ctas = 0);
 size_t mlp_tc_smem_bytes(int nslab_max, int nmax, int n_hidden);
 
 // select.cu
@@ -94,8 +108,8 @@ struct SelectArgs {
     double* y64;
     int* status_word;
 };
-cudaError_t launch_select_tier1(const SelectArgs& a, cudaStream_t s);
-cudaError_t launch_select_tier2(const SelectArgs& a, cudaStream_t s);
-cudaError_t launch_select_final(const SelectArgs& a, cudaStream_t s);
+cudaError_t launch_select_tier1(const SelectArgs& a, cudaStream_t s, int block = 256);
+cudaError_t launch_select_tier2(const SelectArgs& a, cudaStream_t s, int block = 256);
+cudaError_t launch_select_final(const SelectArgs& a, cudaStream_t s, int block = 256);
 
 }  // namespace adv

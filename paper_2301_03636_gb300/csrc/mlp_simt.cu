@@ -36,6 +36,39 @@ __device__ __forceinline__ bool fetch_row_features(const RowSrc& src, int64_t ro
     }
 }
 
+// A group of G lanes fetches one row (row < 0: none): lane g of the group
+// keeps features g + G q in mine[q] (zeros for an invalid or absent row).
+// Returns the row's validity; every lane of the warp must call it.
+template <int F, int G, bool FROM_DESC>
+__device__ __forceinline__ bool fetch_row_features_lanes(const RowSrc& src, int64_t row, int g,
+                                                         int32_t (&mine)[F / G]) {
+    bool ok = false;
+    if constexpr (FROM_DESC) {
+        int64_t d[16];
+        if (row >= 0) {
+            load_desc(src.desc, row, d);
+            ok = validate_row(d) == 0;
+        }
+        if (!ok) placeholder_desc(d);
+        row_features_lanes<F, G>(d, g, mine);
+        if (!ok) {
+#pragma unroll
+            for (int q = 0; q < F / G; ++q) mine[q] = 0;
+        }
+    } else {
+        if (row >= 0) {
+            const int32_t* p = src.feat + (size_t)row * F;
+#pragma unroll
+            for (int q = 0; q < F / G; ++q) mine[q] = __ldg(p + G * q + g);
+            ok = true;
+        } else {
+#pragma unroll
+            for (int q = 0; q < F / G; ++q) mine[q] = 0;
+        }
+    }
+    return ok && !(src.status && src.status[row]);
+}
+
 // TM rows per tile, RPT rows per thread, 8 columns per thread, 256 threads.
 template <int TM, int RPT, int F, bool FROM_DESC>
 __global__ void __launch_bounds__(256) mlp_fp32_kernel(MlpDesc m, RowSrc src, float* __restrict__ out, int ws) {
@@ -146,21 +179,28 @@ __global__ void __launch_bounds__(256) mlp_fp32_kernel(MlpDesc m, RowSrc src, fl
     }
 }
 
-// FP32 scorer for short row lists (the near-tie re-score): RB rows per block,
-// one output neuron per thread (up to 4 per thread for widths > 256).  The
-// transposed weights WT[k][j] are streamed through shared memory in chunks of
-// KC rows by 1-D bulk copies (a 3-stage ring, one thread issuing), so that
-// the block never waits on single L2 loads; activations are stored
-// transposed act[k][RB], read as broadcast 16-byte shared loads.
-template <int RB, int JPT, int F, bool FROM_DESC>
+// FP32 scorer for short row lists (the near-tie re-score).  A block takes
+// LIST_RB = 16 rows as two groups of 8 (threads 0-127 and 128-255); each
+// thread computes two adjacent output neurons of its group (JP pairs, 256
+// columns apart, for widths > 256), summing over the input index in order
+// with FMA -- the same order as the plain FP32 path.  The transposed weights
+// WT[k][j] stream through shared memory in chunks of kc rows by 1-D bulk
+// copies (a ring of `stages`, one thread issuing), so the block never waits
+// on single L2 loads; activations are stored transposed act[k][16] and read
+// as broadcast 16-byte shared loads: two broadcasts and one 8-byte weight
+// load feed 16 FMAs.  Features are computed by 16 lanes per row.
+constexpr int LIST_RB = 16;
+
+template <int JP, int F, bool FROM_DESC>
 __global__ void __launch_bounds__(256) mlp_fp32_list_kernel(MlpDesc m, RowSrc src, float* __restrict__ out,
-                                                            int wmax4, int kc, int* status_word) {
-    constexpr int STAGES = 3;
+                                                            int wmax4, int kc, int stages, int* status_word) {
+    constexpr int RB = LIST_RB;
+    constexpr int MAX_STAGES = 4;
     extern __shared__ __align__(16) float smem_l[];
     float* h0 = smem_l;                    // [wmax4][RB]
     float* h1 = h0 + wmax4 * RB;
-    float* wbuf = h1 + wmax4 * RB;         // [STAGES][kc * wmax4]
-    __shared__ uint64_t full[STAGES];
+    float* wbuf = h1 + wmax4 * RB;         // [stages][kc * wmax4]
+    __shared__ uint64_t full[MAX_STAGES];
     __shared__ int row_ok[RB];
     __shared__ int abort_s;
     const int tid = threadIdx.x;
@@ -170,14 +210,14 @@ __global__ void __launch_bounds__(256) mlp_fp32_list_kernel(MlpDesc m, RowSrc sr
     int nchunks = 0;
     for (int l = 0; l < nh; ++l) nchunks += (m.widths[l] + kc - 1) / kc;
     if (tid == 0) {
-        for (int i = 0; i < STAGES; ++i) mbar_init(&full[i], 1);
+        for (int i = 0; i < stages; ++i) mbar_init(&full[i], 1);
         abort_s = 0;
         fence_mbar_init();
     }
     __syncthreads();
     // chunk c of the per-tile stream: layer l, rows k0 .. k0 + nk - 1 of WT[l]
     auto issue = [&](int c, int stage) {
-        int l = 0, k0 = c * 0;
+        int l = 0, k0 = 0;
         for (l = 0; l < nh; ++l) {
             const int nc = (m.widths[l] + kc - 1) / kc;
             if (c < nc) { k0 = c * kc; break; }
@@ -189,25 +229,26 @@ __global__ void __launch_bounds__(256) mlp_fp32_list_kernel(MlpDesc m, RowSrc sr
         mbar_expect_tx(&full[stage], bytes);
         bulk_g2s(wbuf + (size_t)stage * kc * wmax4, m.WT[l] + (size_t)k0 * m.wt_ld[l], bytes, &full[stage]);
     };
-    uint32_t used = 0;   // chunks consumed so far by this block (across tiles)
+    const int rg = tid >> 7;        // row group: rows 8 rg .. 8 rg + 7
+    const int cp = tid & 127;       // column pair: 2 cp, 2 cp + 1 (+ 256 p)
+    uint32_t used = 0;              // chunks consumed so far by this block (across tiles)
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();
         if (tid == 0)
-            for (int c = 0; c < STAGES && c < nchunks; ++c) issue(c, (int)((used + c) % STAGES));
-        if (tid < RB) {
-            const int64_t pos = tile * RB + tid;
-            int ok = 0;
-            int32_t f[F];
-            if (pos < count) {
-                const int64_t row = src.rows ? src.rows[pos] : pos;
-                ok = fetch_row_features<F, FROM_DESC>(src, row, f) ? 1 : 0;
-            } else {
+            for (int c = 0; c < stages && c < nchunks; ++c) issue(c, (int)((used + c) % stages));
+        {
+            // half-warp h of warp w fetches row 2 w + h of the tile
+            const int lane = tid & 31, r = 2 * (tid >> 5) + (lane >> 4), g = lane & 15;
+            const int64_t pos = tile * RB + r;
+            const int64_t row = pos < count ? (src.rows ? src.rows[pos] : pos) : -1;
+            int32_t mine[F / 16];
+            const bool ok = fetch_row_features_lanes<F, 16, FROM_DESC>(src, row, g, mine);
 #pragma unroll
-                for (int k = 0; k < F; ++k) f[k] = 0;
+            for (int q = 0; q < F / 16; ++q) {
+                const int k = 16 * q + g;
+                h0[k * RB + r] = fmaf((float)mine[q], __ldg(m.sa + k), -__ldg(m.sc + k));
             }
-#pragma unroll
-            for (int k = 0; k < F; ++k) h0[k * RB + tid] = fmaf((float)f[k], __ldg(m.sa + k), -__ldg(m.sc + k));
-            row_ok[tid] = ok;
+            if (g == 0) row_ok[r] = ok ? 1 : 0;
         }
         __syncthreads();
         float* in = h0;
@@ -215,51 +256,55 @@ __global__ void __launch_bounds__(256) mlp_fp32_list_kernel(MlpDesc m, RowSrc sr
         int c = 0;
         for (int l = 0; l < nh; ++l) {
             const int fi = m.widths[l], fo = m.widths[l + 1], ld = m.wt_ld[l];
-            float acc[JPT][RB];
+            float acc[JP][2][8];
 #pragma unroll
-            for (int jj = 0; jj < JPT; ++jj)
+            for (int p = 0; p < JP; ++p)
 #pragma unroll
-                for (int r = 0; r < RB; ++r) acc[jj][r] = 0.f;
+                for (int r = 0; r < 8; ++r) acc[p][0][r] = acc[p][1][r] = 0.f;
             for (int k0 = 0; k0 < fi; k0 += kc, ++c) {
-                const int stage = (int)((used + c) % STAGES);
-                const uint32_t par = ((used + c) / STAGES) & 1u;
+                const int stage = (int)((used + c) % stages);
+                const uint32_t par = ((used + c) / stages) & 1u;
                 if (!mbar_wait_bounded(&full[stage], par, status_word, &abort_s, 2000000000ull)) break;
                 const float* wk = wbuf + (size_t)stage * kc * wmax4;
                 const int nk = fi - k0 < kc ? fi - k0 : kc;
                 auto step = [&](int kk) {
-                    const float4* hv = reinterpret_cast<const float4*>(in + (k0 + kk) * RB);
-                    float4 hr[RB / 4];
+                    const float4* hv = reinterpret_cast<const float4*>(in + (k0 + kk) * RB + 8 * rg);
+                    const float4 ha = hv[0], hb = hv[1];
+                    const float hr[8] = {ha.x, ha.y, ha.z, ha.w, hb.x, hb.y, hb.z, hb.w};
 #pragma unroll
-                    for (int q = 0; q < RB / 4; ++q) hr[q] = hv[q];
+                    for (int p = 0; p < JP; ++p) {
+                        const int j = 2 * cp + 256 * p;
+                        // columns past the padded width read column 0; their sums are never stored
+                        const float2 w = *reinterpret_cast<const float2*>(wk + kk * ld + (j < ld ? j : 0));
 #pragma unroll
-                    for (int jj = 0; jj < JPT; ++jj) {
-                        const int j = tid + 256 * jj;
-                        const float w = wk[kk * ld + (j < ld ? j : 0)];   // zero beyond fo in the padded copy
-#pragma unroll
-                        for (int q = 0; q < RB / 4; ++q) {
-                            acc[jj][4 * q] = fmaf(hr[q].x, w, acc[jj][4 * q]);
-                            acc[jj][4 * q + 1] = fmaf(hr[q].y, w, acc[jj][4 * q + 1]);
-                            acc[jj][4 * q + 2] = fmaf(hr[q].z, w, acc[jj][4 * q + 2]);
-                            acc[jj][4 * q + 3] = fmaf(hr[q].w, w, acc[jj][4 * q + 3]);
+                        for (int r = 0; r < 8; ++r) {
+                            acc[p][0][r] = fmaf(hr[r], w.x, acc[p][0][r]);
+                            acc[p][1][r] = fmaf(hr[r], w.y, acc[p][1][r]);
                         }
                     }
                 };
-                if (nk == 16) {
+                int kk = 0;
+                for (; kk + 16 <= nk; kk += 16) {
 #pragma unroll
-                    for (int kk = 0; kk < 16; ++kk) step(kk);
-                } else {
-                    for (int kk = 0; kk < nk; ++kk) step(kk);
+                    for (int u = 0; u < 16; ++u) step(kk + u);
                 }
+                for (; kk < nk; ++kk) step(kk);
                 __syncthreads();   // every thread is done with this stage
-                if (tid == 0 && c + STAGES < nchunks) issue(c + STAGES, stage);
+                if (tid == 0 && c + stages < nchunks) issue(c + stages, stage);
             }
 #pragma unroll
-            for (int jj = 0; jj < JPT; ++jj) {
-                const int j = tid + 256 * jj;
-                if (j < fo) {
-                    const float bb = __ldg(m.b[l] + j);
+            for (int p = 0; p < JP; ++p) {
 #pragma unroll
-                    for (int r = 0; r < RB; ++r) ob[j * RB + r] = fmaxf(acc[jj][r] + bb, 0.f);
+                for (int e = 0; e < 2; ++e) {
+                    const int j = 2 * cp + 256 * p + e;
+                    if (j < fo) {
+                        const float bb = __ldg(m.b[l] + j);
+                        float4* o4 = reinterpret_cast<float4*>(ob + j * RB + 8 * rg);
+                        o4[0] = make_float4(fmaxf(acc[p][e][0] + bb, 0.f), fmaxf(acc[p][e][1] + bb, 0.f),
+                                            fmaxf(acc[p][e][2] + bb, 0.f), fmaxf(acc[p][e][3] + bb, 0.f));
+                        o4[1] = make_float4(fmaxf(acc[p][e][4] + bb, 0.f), fmaxf(acc[p][e][5] + bb, 0.f),
+                                            fmaxf(acc[p][e][6] + bb, 0.f), fmaxf(acc[p][e][7] + bb, 0.f));
+                    }
                 }
             }
             __syncthreads();
@@ -296,11 +341,13 @@ __global__ void __launch_bounds__(256) mlp_fp64_kernel(MlpDesc m, RowSrc src, do
     for (int64_t pos = blockIdx.x; pos < count; pos += gridDim.x) {
         __syncthreads();
         const int64_t row = src.rows ? src.rows[pos] : pos;
-        if (threadIdx.x == 0) {
-            int32_t f[F];
-            okf = fetch_row_features<F, FROM_DESC>(src, row, f) ? 1 : 0;
+        if (threadIdx.x < 32) {   // warp 0 fetches the row, its lanes sharing the logarithms
+            const int lane = threadIdx.x;
+            int32_t mine[F / 32];
+            const bool ok = fetch_row_features_lanes<F, 32, FROM_DESC>(src, row, lane, mine);
 #pragma unroll
-            for (int k = 0; k < F; ++k) fs[k] = f[k];
+            for (int q = 0; q < F / 32; ++q) fs[32 * q + lane] = mine[q];
+            if (lane == 0) okf = ok ? 1 : 0;
         }
         __syncthreads();
         if (!okf) {
@@ -361,40 +408,47 @@ static cudaError_t launch_fp32_f(const MlpDesc& m, const RowSrc& src, float* out
 
 template <int F, bool FD>
 static cudaError_t launch_fp32_list_t(const MlpDesc& m, const RowSrc& src, float* out, int grid, int wmax4,
-                                      int* status_word, cudaStream_t s) {
-    constexpr int RB = 8;
-    int kc = 16384 / (wmax4 * 4);
-    kc = kc < 1 ? 1 : (kc > 16 ? 16 : kc);
-    const size_t smem = (size_t)(2 * wmax4 * RB + 3 * kc * wmax4) * sizeof(float);
-    auto k = wmax4 <= 256 ? mlp_fp32_list_kernel<RB, 1, F, FD> : mlp_fp32_list_kernel<RB, 4, F, FD>;
+                                      int* status_word, int blocks_per_sm, int chunk_kb, cudaStream_t s) {
+    int kc = chunk_kb * 1024 / (wmax4 * 4);   // weight rows per bulk copy (16 or 32 KB chunks)
+    kc = kc < 1 ? 1 : (kc > 32 ? 32 : kc);
+    const size_t act = (size_t)2 * wmax4 * LIST_RB * sizeof(float);
+    const size_t chunk = (size_t)kc * wmax4 * sizeof(float);
+    // shared memory per block: at most 200 KB, or 100 KB when two blocks share an SM
+    const size_t budget = blocks_per_sm > 1 ? 100 * 1024 : 200 * 1024;
+    int stages = 3;
+    while (stages > 2 && act + stages * chunk > budget) --stages;
+    if (act + stages * chunk > budget) return cudaErrorInvalidValue;
+    const size_t smem = act + stages * chunk;
+    auto k = wmax4 <= 256 ? mlp_fp32_list_kernel<1, F, FD> : mlp_fp32_list_kernel<4, F, FD>;
+    if (wmax4 > 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, 256, smem, s>>>(m, src, out, wmax4, kc, status_word);
+    k<<<grid, 256, smem, s>>>(m, src, out, wmax4, kc, stages, status_word);
     adv_count_launch(1);
     return cudaGetLastError();
 }
 
 static cudaError_t launch_fp32_list(const MlpDesc& m, const RowSrc& src, float* out, int num_sms,
-                                    int* status_word, cudaStream_t s) {
+                                    int* status_word, int blocks_per_sm, int chunk_kb, cudaStream_t s) {
     int wmax = 0;
     for (int i = 0; i < m.nw; ++i) wmax = wmax > m.widths[i] ? wmax : m.widths[i];
     const int wmax4 = (wmax + 3) / 4 * 4;
     const bool fd = (src.feat == nullptr);
-    int grid = num_sms * 2;
+    int grid = num_sms * blocks_per_sm;   // persistent 16-row blocks; longer lists loop
     if (!src.count_dev) {
-        const int64_t tiles = (src.count + 7) / 8;
+        const int64_t tiles = (src.count + LIST_RB - 1) / LIST_RB;
         grid = (int)(tiles < 1 ? 1 : (tiles < grid ? tiles : grid));
     }
     switch (m.widths[0]) {
-        case 32: return fd ? launch_fp32_list_t<32, true>(m, src, out, grid, wmax4, status_word, s) : launch_fp32_list_t<32, false>(m, src, out, grid, wmax4, status_word, s);
-        case 64: return fd ? launch_fp32_list_t<64, true>(m, src, out, grid, wmax4, status_word, s) : launch_fp32_list_t<64, false>(m, src, out, grid, wmax4, status_word, s);
-        case 128: return fd ? launch_fp32_list_t<128, true>(m, src, out, grid, wmax4, status_word, s) : launch_fp32_list_t<128, false>(m, src, out, grid, wmax4, status_word, s);
+        case 32: return fd ? launch_fp32_list_t<32, true>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s) : launch_fp32_list_t<32, false>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s);
+        case 64: return fd ? launch_fp32_list_t<64, true>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s) : launch_fp32_list_t<64, false>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s);
+        case 128: return fd ? launch_fp32_list_t<128, true>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s) : launch_fp32_list_t<128, false>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_mlp_fp32(const MlpDesc& m, const RowSrc& src, float* out, int num_sms, bool for_list,
-                            cudaStream_t s, int* status_word) {
+                            cudaStream_t s, int* status_word, int list_blocks_per_sm, int list_chunk_kb) {
     int wmax = 0;
     for (int i = 1; i + 1 < m.nw; ++i) wmax = wmax > m.widths[i] ? wmax : m.widths[i];
     const bool fd = (src.feat == nullptr);
@@ -403,7 +457,8 @@ cudaError_t launch_mlp_fp32(const MlpDesc& m, const RowSrc& src, float* out, int
         const int grid = (int)(tiles < 1 ? 1 : tiles);
         return fd ? launch_fp32_f<64, 8, true>(m, src, out, grid, s) : launch_fp32_f<64, 8, false>(m, src, out, grid, s);
     }
-    if (for_list && status_word) return launch_fp32_list(m, src, out, num_sms, status_word, s);
+    if (for_list && status_word)
+        return launch_fp32_list(m, src, out, num_sms, status_word, list_blocks_per_sm, list_chunk_kb, s);
     int grid = num_sms * 2;
     if (!for_list) {
         const int64_t tiles = (src.count + 15) / 16;

@@ -337,7 +337,7 @@ size_t mlp_tc_smem_bytes(int nslab_max, int nmax, int n_hidden) {
            (2 * TC_STAGES + 9) * sizeof(uint64_t) + 16 + 1024;
 }
 
-cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s) {
+cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s, int ctas) {
     if (a.n_tiles <= 0) return cudaSuccess;
     int nslab_max = 1;
     for (int l = 0; l < a.n_hidden; ++l) nslab_max = a.nslab[l] > nslab_max ? a.nslab[l] : nslab_max;
@@ -345,7 +345,8 @@ cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s) {
     auto kern = a.fmt == 1 ? mlp_tc_kernel<1> : mlp_tc_kernel<0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = a.n_tiles < num_sms ? a.n_tiles : num_sms;
+    const int cap = (ctas > 0 && ctas < num_sms) ? ctas : num_sms;   // at most one resident CTA per SM
+    const int grid = a.n_tiles < cap ? a.n_tiles : cap;
     kern<<<grid, TC_THREADS, smem, s>>>(a);
     adv_count_launch(1);
     return cudaGetLastError();

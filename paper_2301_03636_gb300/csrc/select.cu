@@ -180,25 +180,39 @@ __global__ void __launch_bounds__(256) select_final_kernel(SelectArgs a) {
     }
 }
 
-static int select_grid(int64_t n_kernels) {
-    const int64_t blocks = (n_kernels + 7) / 8;   // 8 warps per block
+// One warp per segment; the kernels stride over segments, so any grid and
+// any whole number of warps per block covers them.
+static int select_grid(int64_t n_kernels, int block) {
+    const int wpb = block / 32;
+    const int64_t blocks = (n_kernels + wpb - 1) / wpb;
     return (int)(blocks < 1 ? 1 : (blocks > 65535 ? 65535 : blocks));
 }
 
-cudaError_t launch_select_tier1(const SelectArgs& a, cudaStream_t s) {
-    select_tier1_kernel<<<select_grid(a.n_kernels), 256, 0, s>>>(a);
+static bool select_block_ok(int block) { return block == 128 || block == 256; }
+
+cudaError_t launch_select_tier1(const SelectArgs& a, cudaStream_t s, int block) {
+    if (!select_block_ok(block)) return cudaErrorInvalidValue;
+    select_tier1_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
     adv_count_launch(1);
     return cudaGetLastError();
 }
-cudaError_t launch_select_tier2(const SelectArgs& a, cudaStream_t s) {
-    select_tier2_kernel<<<select_grid(a.n_kernels), 256, 0, s>>>(a);
+cudaError_t launch_select_tier2(const SelectArgs& a, cudaStream_t s, int block) {
+    if (!select_block_ok(block)) return cudaErrorInvalidValue;
+    select_tier2_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
     adv_count_launch(1);
     return cudaGetLastError();
 }
-cudaError_t launch_select_final(const SelectArgs& a, cudaStream_t s) {
-    select_final_kernel<<<select_grid(a.n_kernels), 256, 0, s>>>(a);
+cudaError_t launch_select_final(const SelectArgs& a, cudaStream_t s, int block) {
+    if (!select_block_ok(block)) return cudaErrorInvalidValue;
+    select_final_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
     adv_count_launch(1);
     return cudaGetLastError();
+}
+
+bool launch_config_valid(const LaunchConfig& c) {
+    return (c.extract_block == 64 || c.extract_block == 128 || c.extract_block == 256) && c.tc_ctas >= 0 &&
+           (c.list_blocks_per_sm == 1 || c.list_blocks_per_sm == 2) &&
+           (c.list_chunk_kb == 16 || c.list_chunk_kb == 32) && select_block_ok(c.select_block);
 }
 
 }  // namespace adv
