@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(256) mlp_fp32_kernel(MlpDesc m, RowSrc src, fl
 constexpr int LIST_RB = 16;
 
 template <int JP, int F, bool FROM_DESC>
-__global__ void __launch_bounds__(256) mlp_fp32_list_kernel(MlpDesc m, RowSrc src, float* __restrict__ out,
+__global__ void __launch_bounds__(256, 1) mlp_fp32_list_kernel(MlpDesc m, RowSrc src, float* __restrict__ out,
                                                             int wmax4, int kc, int stages, int* status_word) {
     constexpr int RB = LIST_RB;
     constexpr int MAX_STAGES = 4;

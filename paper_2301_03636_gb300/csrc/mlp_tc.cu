@@ -4,12 +4,14 @@
 // layer (one neuron, Sec. 5 Exp. 3) fused into the last hidden layer's
 // epilogue in FP32.
 //
-// Persistent kernel, one CTA per SM, 576 threads:
-//   warp 0       weight producer: streams 64-column K slabs of each hidden
-//                layer's weights (pre-packed in the shared-memory image order,
-//                one 1-D bulk copy of up to 32 KB per slab) through a 3-stage
-//                ring (a bulk copy costs a fixed ~550 cycles, so copies are
-//                kept as large as the ring allows);
+// Persistent kernel, one CTA per SM, 640 threads:
+//   warps 0, 18, 19  weight producers: stream 64-column K slabs of each
+//                hidden layer's weights (pre-packed in the shared-memory image
+//                order, one 1-D bulk copy of up to 32 KB per slab) through a
+//                3-stage ring, producer q owning stage q.  Bulk copies issued
+//                by one thread complete one after another (~450-800 cycles
+//                each whatever their size), so one issuing thread per stage
+//                keeps three copies in flight;
 //   warp 1       MMA issuer (one thread) and tensor-memory owner;
 //   warps 2-17   sixteen epilogue warps.  Warp w reads TMEM lanes
 //                32*(w%4) .. 32*(w%4)+31 (one row per thread); the four warps
@@ -28,8 +30,8 @@
 
 namespace adv {
 
-constexpr int TC_THREADS = 576;
 constexpr int TC_STAGES = 3;
+constexpr int TC_THREADS = 32 * (2 + 16 + (TC_STAGES - 1));   // producer 0, MMA, 16 epilogue, producers 1..
 
 // Diagnostic timeline of CTA 0 (clock64 stamps), compiled in only with
 // -DADV_TC_TRACE; the library build never defines it.
@@ -109,39 +111,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
     const int n_pairs = (n_my + 1) / 2;
     const uint64_t lim = a.timeout_ns;
 
-    if (warp == 0) {
-        // ---------------- weight producer ----------------
+    if (warp == 0 || warp >= 18) {
+        // ---------------- weight producers ----------------
+        // The chunks (pair, layer, slot, K slab) form one sequence that the
+        // MMA thread consumes through stages 0, 1, 2, 0, ...; producer q
+        // fills stage q with every chunk whose index is q modulo TC_STAGES.
+        const int q = warp == 0 ? 0 : warp - 17;
         if (lane == 0) {
-            uint32_t stage = 0, phase = 0;
-            int issued = 0;
+            uint32_t phase = 0;
+            int idx = 0, mine = 0;
             bool ok = true;
             for (int p = 0; p < n_pairs && ok; ++p) {
                 const int ns = (2 * p + 1 < n_my) ? 2 : 1;
                 for (int l = 0; l < a.n_hidden && ok; ++l) {
                     const uint32_t sb = (uint32_t)a.npad[l] * ADV_SLAB_ROW_BYTES;   // one 64-column K slab
                     for (int s = 0; s < ns && ok; ++s) {
-                        for (int k = 0; k < a.nslab[l]; ++k) {
-                            TC_TRACE(8192 + 2 * (issued & 4095));
-                            if (!mbar_wait_bounded(&w_empty[stage], phase ^ 1u, a.status_word, abort_flag, lim)) {
+                        for (int k = 0; k < a.nslab[l]; ++k, ++idx) {
+                            if (idx % TC_STAGES != q) continue;
+                            TC_TRACE(8192 + 2 * (idx & 4095));
+                            if (!mbar_wait_bounded(&w_empty[q], phase ^ 1u, a.status_word, abort_flag, lim)) {
                                 ok = false;
                                 break;
                             }
-                            TC_TRACE(8192 + 2 * (issued & 4095) + 1);
-                            mbar_expect_tx(&w_full[stage], sb);
-                            bulk_g2s(wst + stage * stage_bytes, a.w_img[l] + (size_t)k * sb, sb, &w_full[stage]);
-                            ++issued;
-                            if (++stage == TC_STAGES) { stage = 0; phase ^= 1u; }
+                            TC_TRACE(8192 + 2 * (idx & 4095) + 1);
+                            mbar_expect_tx(&w_full[q], sb);
+                            bulk_g2s(wst + q * stage_bytes, a.w_img[l] + (size_t)k * sb, sb, &w_full[q]);
+                            ++mine;
+                            phase ^= 1u;
                         }
                     }
                 }
             }
-            // copies in flight end before the CTA does (on the normal path the
-            // MMA thread has consumed them already)
-            for (int i = 0; i < TC_STAGES && i < issued; ++i) {
-                if (stage == 0) { stage = TC_STAGES; phase ^= 1u; }
-                --stage;
-                mbar_wait_bounded(&w_full[stage], phase, a.status_word, abort_flag, lim);
-            }
+            // this producer's last copy ends before the CTA does (on the
+            // normal path the MMA thread has consumed it already)
+            if (mine > 0) mbar_wait_bounded(&w_full[q], phase ^ 1u, a.status_word, abort_flag, lim);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
