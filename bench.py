@@ -209,6 +209,82 @@ def training_leg(dev, steps=20):
             "loss_after": float(loss.item())}
 
 
+def large_sweep_leg(dev, reps=5):
+    """The large sweep: 2^20 variants of 65,536 kernels (2..64 each), F = 128,
+    MLP 128-1024-1024-1024-1, scored on the tensor cores one launch per hidden
+    layer (BF16, FP16) and on the FP32 SIMT path, then ranked with the near-tie
+    re-score.  Inputs resident in HBM; the ~4 GB of activations between the
+    layers exceed L2 on their own."""
+    import torch
+
+    from paper_2301_03636_gb300 import advisor
+    wl = W.LARGE_SWEEP
+    off = wl.offsets()
+    n, K = int(off[-1]), wl.n_kernels
+    flop_row = 2 * sum(wl.widths[i] * wl.widths[i + 1] for i in range(len(wl.widths) - 1))
+    d = torch.from_numpy(wl.descriptors()).to(dev)
+    o = torch.from_numpy(off).to(dev)
+    cal = torch.from_numpy(W.calibration_descriptors(16384)).to(dev)
+    fcal, scal = advisor.advisor_extract_features(cal, wl.n_features)
+    mu, sigma = advisor.advisor_fit_standardizer(fcal, scal)
+    m = advisor.Model(wl.widths, max_rows=n, max_kernels=K, device=dev)
+    m.set_params(wl.weights(), mu, sigma)
+    f, st = advisor.advisor_extract_features(d, wl.n_features)
+    sample = 16384
+    y64 = m.score_fp64(f[:sample], st[:sample])
+    kev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    kev[0].record(); kev[1].record()
+    torch.cuda.synchronize()
+    hbm, tf, src = peaks()
+    out = {"workload": "large sweep: 2^20 variants of 65,536 kernels, F=128, MLP 128-1024-1024-1024-1",
+           "variants": n, "flop_per_row": flop_row,
+           "error_sample_rows": sample}
+    for p in ("bf16", "fp16"):
+        m.set_profile_events(*kev)
+        for _ in range(2):
+            y = m.score(f, st, p)
+        torch.cuda.synchronize()
+        tk = []
+        for _ in range(reps):
+            y = m.score(f, st, p)
+            torch.cuda.synchronize()
+            tk.append(kev[0].elapsed_time(kev[1]))
+        m.set_profile_events(None, None)
+        ms = float(np.median(tk))
+        ach = n * flop_row / (ms / 1000.0) / 1e12
+        out[p] = {"layers_ms": ms, "variants_per_s": n / (ms / 1000.0), "tflops": ach, "frac_of_peak": ach / tf,
+                  "peak": tf, "peak_source": src + " dense bf16 (fp16 runs at the bf16 rate)",
+                  "max_abs_err_vs_fp64": float((y[:sample].double() - y64).abs().max().item())}
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    y = m.score(f, st, "fp32")
+    a.record()
+    y = m.score(f, st, "fp32")
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    out["fp32"] = {"ms": ms, "variants_per_s": n / (ms / 1000.0), "tflops": n * flop_row / (ms / 1000.0) / 1e12,
+                   "max_abs_err_vs_fp64": float((y[:sample].double() - y64).abs().max().item())}
+    eps = m.calibrate_eps(fcal, scal, "bf16")
+    eps32 = m.calibrate_eps(fcal, scal, "fp32")
+    best = torch.empty(K, dtype=torch.int32, device=dev)
+    bsc = torch.empty(K, dtype=torch.float64, device=dev)
+    m.rank(d, o, "bf16", eps, eps32, best=best, best_score=bsc)
+    torch.cuda.synchronize()
+    tt = []
+    for _ in range(3):
+        a.record()
+        m.rank(d, o, "bf16", eps, eps32, best=best, best_score=bsc)
+        b.record()
+        torch.cuda.synchronize()
+        tt.append(a.elapsed_time(b))
+    c32, c64 = m.rescore_counts()
+    ms = float(np.median(tt))
+    out["rank_bf16"] = {"ms": ms, "variants_per_s": n / (ms / 1000.0), "eps": eps, "eps32": eps32,
+                        "near_tie_fp32_rows": c32, "near_tie_fp64_rows": c64,
+                        "near_tie_fraction": c32 / n}
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -411,6 +487,7 @@ def main():
         srv10 = [r for r in out["serving"]["runs"] if r["rate_per_s"] == 10000]
         out["p99_query_ms"] = srv10[0]["p99_ms"] if srv10 else None
         out["training"] = training_leg(dev)
+        out["large_sweep"] = large_sweep_leg(dev)
         # the CPU oracle on the host cores (bounded sample)
         import oracle
         fc, sc = oracle.extract_features(W.calibration_descriptors(65536), WL.n_features)

@@ -314,6 +314,13 @@ advisor_status advisor_model_set_adam_step(advisor_model_t m, int64_t step);
  * or ADVISOR_ERR_CUDA. */
 advisor_status advisor_get_device_status(advisor_model_t m, cudaStream_t stream);
 
+/* Near-tie statistics of the last selection with re-score on this model
+ * (advisor_select_best / advisor_rank with eps_scores >= 0): h_counts[0] =
+ * rows re-scored in FP32, h_counts[1] = rows re-scored in FP64 (host
+ * int64[2]).  Synchronises `stream`.  Values are undefined before the first
+ * such call. */
+advisor_status advisor_get_rescore_counts(advisor_model_t m, int64_t* h_counts, cudaStream_t stream);
+
 /* Tensor-core scoring that allocates nothing: the same computation and
  * result as advisor_score_variants with ADVISOR_BF16 or ADVISOR_FP16, for
  * callers that cannot provide device memory for a workspace (code where

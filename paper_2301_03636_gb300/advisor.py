@@ -74,6 +74,7 @@ def lib():
         "advisor_model_get_adam_step": (i64, [P]),
         "advisor_model_set_adam_step": (st, [P, i64]),
         "advisor_model_get_launch_config": (st, [P, P]),
+        "advisor_get_rescore_counts": (st, [P, P, P]),
         "advisor_model_set_launch_config": (st, [P, P]),
         "advisor_plan_rank": (st, [P, P, i64, P, i64, st, f32, f32, P, P, P, P, i32, P, ctypes.POINTER(P)]),
         "advisor_plan_launch": (st, [P, P]),
@@ -257,6 +258,13 @@ class Model:
                                   float(eps), float(eps32), _ptr(best), _ptr(best_score), _ptr(scores), _ptr(status),
                                   _stream(stream)), "advisor_rank")
         return best, best_score
+
+    def rescore_counts(self, stream=None):
+        """(rows re-scored in FP32, rows re-scored in FP64) by the last selection with re-score."""
+        c = (ctypes.c_int64 * 2)()
+        _check(lib().advisor_get_rescore_counts(self.handle, ctypes.cast(c, ctypes.c_void_p), _stream(stream)),
+               "advisor_get_rescore_counts")
+        return int(c[0]), int(c[1])
 
     @property
     def launch_config(self) -> LaunchConfig:

@@ -20,7 +20,7 @@ int roundup(int x, int m) { return ((x + m - 1) / m) * m; }
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 struct WsLayout {
-    size_t x_img, feat32, status, scores, counters, seg_state, seg_start, seg_cnt;
+    size_t x_img, h_img[2], partial, feat32, status, scores, counters, seg_state, seg_start, seg_cnt;
     size_t cand_rows, y32, cand2_rows, y64;
     size_t train;   // start of the training region
     size_t bytes;
@@ -57,6 +57,12 @@ WsLayout ws_layout(const adv::ModelLayout& L, int64_t R, int64_t K, adv::TrainLa
     const int64_t tiles = (R + ADV_TILE_M - 1) / ADV_TILE_M;
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
     w.x_img = take((size_t)tiles * L.nslab[0] * ADV_X_SLAB_BYTES);
+    // models too wide for the fused scorer run layer by layer through two
+    // activation images and per-chunk partial sums of the output layer
+    const bool wide = !L.tc_ok && L.n_hidden >= 1;
+    for (int i = 0; i < 2; ++i) w.h_img[i] = take(wide ? (size_t)tiles * (L.nmax / 64) * ADV_X_SLAB_BYTES : 0);
+    const int last_chunks = (L.npad[L.n_hidden > 0 ? L.n_hidden - 1 : 0] + 255) / 256;
+    w.partial = take(wide ? (size_t)2 * last_chunks * tiles * ADV_TILE_M * 4 : 0);
     w.feat32 = take((size_t)R * L.F * 4);
     w.status = take((size_t)R);
     w.scores = take((size_t)R * 4);
@@ -129,6 +135,12 @@ bool tc_supported(const advisor_model* m) {
     return adv::mlp_tc_smem_bytes(nslab_max, L.nmax, L.n_hidden) <= 232448;
 }
 
+// Models whose hidden layers exceed the fused scorer: one launch per layer.
+bool wide_supported(const advisor_model* m) { return !m->L.tc_ok && m->L.n_hidden >= 1; }
+
+cudaError_t launch_wide(advisor_model* m, const uint8_t* x_img, int64_t n_rows, const uint8_t* status, float* scores,
+                        int fi, cudaStream_t s);
+
 advisor_status check_ready(const advisor_model* m, int64_t n_rows) {
     if (!m || !m->P || !m->WS || !m->params_set) return ADVISOR_ERR_INVALID_ARGUMENT;
     if (n_rows > m->max_rows) return ADVISOR_ERR_OUT_OF_MEMORY;
@@ -151,6 +163,46 @@ cudaError_t launch_tc_profiled(advisor_model* m, const adv::TcArgs& a, cudaStrea
         if (e != cudaSuccess) return e;
     }
     cudaError_t e = adv::launch_mlp_tc(a, m->num_sms, s, m->cfg.tc_ctas);
+    if (e == cudaSuccess && m->prof_stop) e = record_event(m->prof_stop, s);
+    return e;
+}
+
+cudaError_t launch_wide(advisor_model* m, const uint8_t* x_img, int64_t n_rows, const uint8_t* status, float* scores,
+                        int fi, cudaStream_t s) {
+    const adv::ModelLayout& L = m->L;
+    const int tiles = (int)((n_rows + ADV_TILE_M - 1) / ADV_TILE_M);
+    if (m->prof_start) {
+        cudaError_t e = record_event(m->prof_start, s);
+        if (e != cudaSuccess) return e;
+    }
+    const uint8_t* in = x_img;
+    int last_chunks = 1;
+    for (int l = 0; l < L.n_hidden; ++l) {
+        adv::LayerArgs a{};
+        a.a_img = in;
+        a.a_slabs = L.nslab[l];
+        a.w_img = m->P + L.p_w16[fi][l];
+        a.npad = L.npad[l];
+        a.n_chunks = (L.npad[l] + 255) / 256;
+        a.n_tiles = tiles;
+        a.bias = reinterpret_cast<const float*>(m->P + L.p_bias_off[l]);
+        a.mode = l + 1 == L.n_hidden ? 1 : 0;
+        a.out_img = m->WS + m->W.h_img[l & 1];
+        a.w_out = reinterpret_cast<const float*>(m->P + L.p_wout_pad);
+        a.partial = reinterpret_cast<float*>(m->WS + m->W.partial);
+        a.fmt = fi == 0 ? 1 : 0;   // instruction-descriptor code: 1 = BF16, 0 = F16
+        a.status_word = status_word(m);
+        a.timeout_ns = 2000000000ull;
+        cudaError_t e = adv::launch_mlp_layer_tc(a, m->num_sms, s);
+        if (e != cudaSuccess) return e;
+        in = a.out_img;
+        last_chunks = a.n_chunks;
+    }
+    cudaError_t e = adv::launch_sum_partials(reinterpret_cast<const float*>(m->WS + m->W.partial), 2 * last_chunks,
+                                             (int64_t)tiles * ADV_TILE_M, n_rows,
+                                             reinterpret_cast<const float*>(m->P + L.p_master) +
+                                                 L.layer_b_off[L.n_layers - 1],
+                                             status, scores, m->num_sms, s);
     if (e == cudaSuccess && m->prof_stop) e = record_event(m->prof_stop, s);
     return e;
 }
@@ -223,6 +275,17 @@ const char* advisor_status_string(advisor_status s) {
 }
 
 int64_t advisor_launch_count(void) { return (int64_t)g_launches.load(); }
+
+advisor_status advisor_get_rescore_counts(advisor_model_t m, int64_t* h_counts, cudaStream_t stream) {
+    if (!m || !h_counts || !m->WS) return ADVISOR_ERR_INVALID_ARGUMENT;
+    int c[2] = {0, 0};
+    if (cudaMemcpyAsync(c, m->WS + m->W.counters, sizeof(c), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return ADVISOR_ERR_CUDA;
+    h_counts[0] = c[0];
+    h_counts[1] = c[1];
+    return ADVISOR_OK;
+}
 
 advisor_status advisor_model_get_launch_config(advisor_model_t m, advisor_launch_config* out) {
     if (!m || !out) return ADVISOR_ERR_INVALID_ARGUMENT;
@@ -396,7 +459,8 @@ advisor_status advisor_score_variants(advisor_model_t m, const int32_t* d_feat_q
         return cuda_status(adv::launch_mlp_fp32(mlp_desc(m), src, d_scores, m->num_sms, false, stream));
     }
     if (precision != ADVISOR_BF16 && precision != ADVISOR_FP16) return ADVISOR_ERR_UNSUPPORTED;
-    if (!tc_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
+    const bool fused = tc_supported(m);
+    if (!fused && !wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
     const int fi = precision == ADVISOR_BF16 ? 0 : 1;
     const int64_t npad = ((n_rows + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
     uint8_t* x = m->WS + m->W.x_img;
@@ -405,6 +469,7 @@ advisor_status advisor_score_variants(advisor_model_t m, const int32_t* d_feat_q
                                             reinterpret_cast<const float*>(m->P + m->L.p_stdz_c), m->L.F,
                                             fi == 0 ? 1 : 2, stream);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    if (!fused) return cuda_status(launch_wide(m, x, n_rows, d_row_status, d_scores, fi, stream));
     return cuda_status(launch_tc_profiled(m, tc_args(m, x, n_rows, d_row_status, d_scores, fi), stream));
 }
 
@@ -470,14 +535,16 @@ advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_des
                              d_best_local, d_best_score, stream);
         }
         if (precision != ADVISOR_BF16 && precision != ADVISOR_FP16) return ADVISOR_ERR_UNSUPPORTED;
-        if (!tc_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
+        const bool fused = tc_supported(m);
+        if (!fused && !wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
         const int fi = precision == ADVISOR_BF16 ? 0 : 1;
         a.n_rows_padded = ((n_rows + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
         a.x_img = m->WS + m->W.x_img;
         a.nslab = L.nslab[0];
         e = adv::launch_extract(a, L.F, fi == 0 ? 1 : 2, stream, m->cfg.extract_block);
         if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
-        e = launch_tc_profiled(m, tc_args(m, a.x_img, n_rows, status, scores, fi), stream);
+        e = fused ? launch_tc_profiled(m, tc_args(m, a.x_img, n_rows, status, scores, fi), stream)
+                  : launch_wide(m, a.x_img, n_rows, status, scores, fi, stream);
         if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     }
     adv::RowSrc rs{nullptr, d_desc, nullptr, nullptr, 0, nullptr};

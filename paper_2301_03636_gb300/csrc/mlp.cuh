@@ -86,6 +86,28 @@ struct TcArgs {
     unsigned long long timeout_ns;
 };
 cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s, int ctas = 0);
+
+// One hidden layer of a wide MLP on the tensor cores (csrc/mlp_layer_tc.cu).
+struct LayerArgs {
+    const uint8_t* a_img;     // input image: [tile][a_slabs][128 rows x 128 B], 128B swizzle
+    int a_slabs;              // input slabs (kpad / 64)
+    const uint8_t* w_img;     // weights: [a_slabs][npad rows][128 B] (the packed 16-bit image)
+    int npad;                 // output width rounded up to 64
+    int n_chunks;             // ceil(npad / 256)
+    int n_tiles;              // 128-row tiles
+    const float* bias;        // [npad]
+    int mode;                 // 0: ReLU -> out_img; 1: ReLU, dot with w_out -> partial
+    uint8_t* out_img;         // mode 0: [tile][npad / 64][128 x 128 B]
+    const float* w_out;       // mode 1: [npad]
+    float* partial;           // mode 1: [n_chunks][2][n_tiles * 128]
+    int fmt;                  // instruction-descriptor operand format: 1 BF16, 0 F16
+    int* status_word;
+    uint64_t timeout_ns;
+};
+size_t mlp_layer_tc_smem_bytes();
+cudaError_t launch_mlp_layer_tc(const LayerArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_sum_partials(const float* partial, int n_parts, int64_t stride, int64_t n_rows, const float* b_out,
+                                const uint8_t* status, float* scores, int num_sms, cudaStream_t s);
 size_t mlp_tc_smem_bytes(int nslab_max, int nmax, int n_hidden);
 
 // select.cu
