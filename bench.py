@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the precision comparison, serving, training and CPU baseline legs")
+    ap.add_argument("--sweep-only", action="store_true",
+                    help="run only the large-sweep leg and print its JSON (for profiling its kernels)")
+    ap.add_argument("--sweep-rows", type=int, default=0,
+                    help="with --sweep-only: keep the first kernels of the large sweep up to this many variants")
     return ap.parse_args()
 
 
@@ -209,7 +213,7 @@ def training_leg(dev, steps=20):
             "loss_after": float(loss.item())}
 
 
-def large_sweep_leg(dev, reps=5):
+def large_sweep_leg(dev, reps=5, rows=0):
     """The large sweep: 2^20 variants of 65,536 kernels (2..64 each), F = 128,
     MLP 128-1024-1024-1024-1, scored on the tensor cores one launch per hidden
     layer (BF16, FP16) and on the FP32 SIMT path, then ranked with the near-tie
@@ -220,9 +224,11 @@ def large_sweep_leg(dev, reps=5):
     from paper_2301_03636_gb300 import advisor
     wl = W.LARGE_SWEEP
     off = wl.offsets()
-    n, K = int(off[-1]), wl.n_kernels
+    if rows:   # a prefix of whole kernels (profiling runs)
+        off = off[:int(np.searchsorted(off, rows, side="right"))]
+    n, K = int(off[-1]), len(off) - 1
     flop_row = 2 * sum(wl.widths[i] * wl.widths[i + 1] for i in range(len(wl.widths) - 1))
-    d = torch.from_numpy(wl.descriptors()).to(dev)
+    d = torch.from_numpy(wl.descriptors()[:n]).to(dev)
     o = torch.from_numpy(off).to(dev)
     cal = torch.from_numpy(W.calibration_descriptors(16384)).to(dev)
     fcal, scal = advisor.advisor_extract_features(cal, wl.n_features)
@@ -230,13 +236,13 @@ def large_sweep_leg(dev, reps=5):
     m = advisor.Model(wl.widths, max_rows=n, max_kernels=K, device=dev)
     m.set_params(wl.weights(), mu, sigma)
     f, st = advisor.advisor_extract_features(d, wl.n_features)
-    sample = 16384
+    sample = min(16384, n)
     y64 = m.score_fp64(f[:sample], st[:sample])
     kev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     kev[0].record(); kev[1].record()
     torch.cuda.synchronize()
     hbm, tf, src = peaks()
-    out = {"workload": "large sweep: 2^20 variants of 65,536 kernels, F=128, MLP 128-1024-1024-1024-1",
+    out = {"workload": f"large sweep: {n} variants of {K} kernels (2..64 each), F=128, MLP 128-1024-1024-1024-1",
            "variants": n, "flop_per_row": flop_row,
            "error_sample_rows": sample}
     for p in ("bf16", "fp16"):
@@ -255,6 +261,24 @@ def large_sweep_leg(dev, reps=5):
         out[p] = {"layers_ms": ms, "variants_per_s": n / (ms / 1000.0), "tflops": ach, "frac_of_peak": ach / tf,
                   "peak": tf, "peak_source": src + " dense bf16 (fp16 runs at the bf16 rate)",
                   "max_abs_err_vs_fp64": float((y[:sample].double() - y64).abs().max().item())}
+    # E4M3: static activation scales from the calibration sample; peak = the
+    # measured dense BF16 peak x the nominal FP8 / BF16 ratio (4.5 / 2.25)
+    m.calibrate_fp8(fcal)
+    m.set_profile_events(*kev)
+    for _ in range(2):
+        y = m.score(f, st, "fp8")
+    torch.cuda.synchronize()
+    tk = []
+    for _ in range(reps):
+        y = m.score(f, st, "fp8")
+        torch.cuda.synchronize()
+        tk.append(kev[0].elapsed_time(kev[1]))
+    m.set_profile_events(None, None)
+    ms = float(np.median(tk))
+    ach = n * flop_row / (ms / 1000.0) / 1e12
+    out["fp8"] = {"layers_ms": ms, "variants_per_s": n / (ms / 1000.0), "tflops": ach, "frac_of_peak": ach / (2 * tf),
+                  "peak": 2 * tf, "peak_source": src + " dense bf16 x 2 (nominal fp8 / bf16 ratio)",
+                  "max_abs_err_vs_fp64": float((y[:sample].double() - y64).abs().max().item())}
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     y = m.score(f, st, "fp32")
     a.record()
@@ -264,24 +288,25 @@ def large_sweep_leg(dev, reps=5):
     ms = a.elapsed_time(b)
     out["fp32"] = {"ms": ms, "variants_per_s": n / (ms / 1000.0), "tflops": n * flop_row / (ms / 1000.0) / 1e12,
                    "max_abs_err_vs_fp64": float((y[:sample].double() - y64).abs().max().item())}
-    eps = m.calibrate_eps(fcal, scal, "bf16")
     eps32 = m.calibrate_eps(fcal, scal, "fp32")
     best = torch.empty(K, dtype=torch.int32, device=dev)
     bsc = torch.empty(K, dtype=torch.float64, device=dev)
-    m.rank(d, o, "bf16", eps, eps32, best=best, best_score=bsc)
-    torch.cuda.synchronize()
-    tt = []
-    for _ in range(3):
-        a.record()
-        m.rank(d, o, "bf16", eps, eps32, best=best, best_score=bsc)
-        b.record()
+    for p in ("bf16", "fp8"):
+        eps = m.calibrate_eps(fcal, scal, p)
+        m.rank(d, o, p, eps, eps32, best=best, best_score=bsc)
         torch.cuda.synchronize()
-        tt.append(a.elapsed_time(b))
-    c32, c64 = m.rescore_counts()
-    ms = float(np.median(tt))
-    out["rank_bf16"] = {"ms": ms, "variants_per_s": n / (ms / 1000.0), "eps": eps, "eps32": eps32,
-                        "near_tie_fp32_rows": c32, "near_tie_fp64_rows": c64,
-                        "near_tie_fraction": c32 / n}
+        tt = []
+        for _ in range(3):
+            a.record()
+            m.rank(d, o, p, eps, eps32, best=best, best_score=bsc)
+            b.record()
+            torch.cuda.synchronize()
+            tt.append(a.elapsed_time(b))
+        c32, c64 = m.rescore_counts()
+        ms = float(np.median(tt))
+        out["rank_" + p] = {"ms": ms, "variants_per_s": n / (ms / 1000.0), "eps": eps, "eps32": eps32,
+                            "near_tie_fp32_rows": c32, "near_tie_fp64_rows": c64,
+                            "near_tie_fraction": c32 / n}
     return out
 
 
@@ -340,6 +365,10 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
+
+    if args.sweep_only:
+        print(json.dumps(large_sweep_leg(dev, rows=args.sweep_rows)), flush=True)
+        return
 
     # ---- setup (untimed): workload, model, standardiser, error bounds ----
     off = WL.offsets()

@@ -55,12 +55,16 @@ typedef enum {
  * BF16 / FP16: tcgen05 tensor cores, 16-bit operands, FP32 accumulation in
  * tensor memory, FP32 bias/ReLU epilogue, output layer in FP32.
  * FP64: SIMT FP64 with the oracle's summation order (slow; used for the
- * near-tie re-score and for error calibration). */
+ * near-tie re-score and for error calibration).  FP8_E4M3: tensor cores
+ * with E4M3 operands and per-tensor scales (kind::f8f6f4), FP32
+ * accumulation and epilogue; models with a hidden width above 256 only,
+ * after advisor_model_calibrate_fp8. */
 typedef enum {
     ADVISOR_FP32 = 0,
     ADVISOR_BF16 = 1,
     ADVISOR_FP16 = 2,
-    ADVISOR_FP64 = 3
+    ADVISOR_FP64 = 3,
+    ADVISOR_FP8_E4M3 = 4
 } advisor_precision;
 
 /* One generated variant of one kernel: 16 x int64 = 128 bytes, array of
@@ -211,6 +215,20 @@ advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_des
                             advisor_precision precision, float eps_scores, float eps_fp32,
                             int32_t* d_best_local, double* d_best_score, float* d_scores,
                             uint8_t* d_row_status, cudaStream_t stream);
+
+/* FP8 (E4M3) operands for models whose hidden layers run one launch per
+ * layer (a hidden width above 256): per-tensor scales, scale = amax / 448.
+ * Weight scales come from the exact amax of each weight matrix (computed by
+ * set_params / repack); activation scales are static, from the amax of each
+ * hidden layer's input over a calibration sample: this call runs the FP32
+ * forward on d_feat_q16 [n_rows][F] (n_rows <= the bound max_rows; the
+ * standardised features for the first layer, the ReLU outputs for the
+ * others) and stores the scales with the model.  set_params clears them;
+ * ADVISOR_FP8_E4M3 scoring before this call returns
+ * ADVISOR_ERR_INVALID_ARGUMENT.  Models that fit the fused 16-bit scorer
+ * (every hidden width <= 256) return ADVISOR_ERR_UNSUPPORTED. */
+advisor_status advisor_model_calibrate_fp8(advisor_model_t m, const int32_t* d_feat_q16, int64_t n_rows,
+                                           cudaStream_t stream);
 
 /* Launch shapes of the hot path (the batching of many kernels' variants
  * into persistent launches).  Every setting gives bit-identical results:

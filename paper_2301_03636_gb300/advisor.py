@@ -18,8 +18,8 @@ from . import build as _build
 OK = 0
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "bad descriptor", 3: "out of memory", 4: "CUDA error",
                 5: "device wait timed out", 6: "unsupported", 7: "malformed segment offsets"}
-FP32, BF16, FP16, FP64 = 0, 1, 2, 3
-PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp16": FP16, "fp64": FP64}
+FP32, BF16, FP16, FP64, FP8 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp16": FP16, "fp64": FP64, "fp8": FP8}
 
 _lib = None
 
@@ -75,6 +75,7 @@ def lib():
         "advisor_model_set_adam_step": (st, [P, i64]),
         "advisor_model_get_launch_config": (st, [P, P]),
         "advisor_get_rescore_counts": (st, [P, P, P]),
+        "advisor_model_calibrate_fp8": (st, [P, P, i64, P]),
         "advisor_model_set_launch_config": (st, [P, P]),
         "advisor_plan_rank": (st, [P, P, i64, P, i64, st, f32, f32, P, P, P, P, i32, P, ctypes.POINTER(P)]),
         "advisor_plan_launch": (st, [P, P]),
@@ -338,6 +339,12 @@ class Model:
 
     def device_status(self, stream=None) -> int:
         return int(lib().advisor_get_device_status(self.handle, _stream(stream)))
+
+    def calibrate_fp8(self, feat, stream=None):
+        """Static per-tensor activation scales for FP8 scoring from a calibration
+        sample of features (see advisor_model_calibrate_fp8)."""
+        _check(lib().advisor_model_calibrate_fp8(self.handle, _ptr(feat), feat.shape[0], _stream(stream)),
+               "advisor_model_calibrate_fp8")
 
     def calibrate_eps(self, feat, status=None, precision="bf16", safety=2.0):
         """Measured error bound of a precision against the FP64 scorer on a

@@ -45,6 +45,7 @@ struct advisor_model {
     int64_t adam_step = 0;
     int64_t saved_rows = 0;   // rows of the last advisor_forward_saved
     adv::LaunchConfig cfg{};  // launch shapes of the hot path (a plan may set them)
+    bool fp8_calibrated = false;   // activation scales stored (advisor_model_calibrate_fp8)
 };
 
 namespace {
@@ -177,20 +178,23 @@ cudaError_t launch_wide(advisor_model* m, const uint8_t* x_img, int64_t n_rows, 
     }
     const uint8_t* in = x_img;
     int last_chunks = 1;
+    const bool f8 = fi == 2;   // E4M3 images: 128 K per 128-byte row
     for (int l = 0; l < L.n_hidden; ++l) {
         adv::LayerArgs a{};
         a.a_img = in;
-        a.a_slabs = L.nslab[l];
-        a.w_img = m->P + L.p_w16[fi][l];
-        a.npad = L.npad[l];
-        a.n_chunks = (L.npad[l] + 255) / 256;
+        a.a_slabs = f8 ? L.nslab8[l] : L.nslab[l];
+        a.w_img = m->P + (f8 ? L.p_w8[l] : L.p_w16[fi][l]);
+        a.npad = f8 ? L.npad8[l] : L.npad[l];
+        a.n_chunks = (a.npad + 255) / 256;
         a.n_tiles = tiles;
         a.bias = reinterpret_cast<const float*>(m->P + L.p_bias_off[l]);
         a.mode = l + 1 == L.n_hidden ? 1 : 0;
         a.out_img = m->WS + m->W.h_img[l & 1];
         a.w_out = reinterpret_cast<const float*>(m->P + L.p_wout_pad);
         a.partial = reinterpret_cast<float*>(m->WS + m->W.partial);
-        a.fmt = fi == 0 ? 1 : 0;   // instruction-descriptor code: 1 = BF16, 0 = F16
+        a.fmt = f8 ? 2 : (fi == 0 ? 1 : 0);   // 2 = E4M3; instruction-descriptor codes 1 = BF16, 0 = F16
+        a.fp8 = reinterpret_cast<const float*>(m->P + L.p_fp8);
+        a.layer = l;
         a.status_word = status_word(m);
         a.timeout_ns = 2000000000ull;
         cudaError_t e = adv::launch_mlp_layer_tc(a, m->num_sms, s);
@@ -276,6 +280,23 @@ const char* advisor_status_string(advisor_status s) {
 
 int64_t advisor_launch_count(void) { return (int64_t)g_launches.load(); }
 
+advisor_status advisor_model_calibrate_fp8(advisor_model_t m, const int32_t* d_feat_q16, int64_t n_rows,
+                                           cudaStream_t stream) {
+    if (!m || !d_feat_q16 || n_rows < 1) return ADVISOR_ERR_INVALID_ARGUMENT;
+    advisor_status st = check_ready(m, n_rows);
+    if (st != ADVISOR_OK) return st;
+    if (!wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
+    uint8_t* TW = m->WS + m->W.train;
+    cudaError_t e = adv::launch_forward_saved(m->L, m->T, TW, mlp_desc(m), d_feat_q16, n_rows, nullptr, stream);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    const float* acts[ADV_MAX_LAYERS] = {};
+    for (int l = 0; l < m->L.n_hidden; ++l) acts[l] = reinterpret_cast<const float*>(TW + m->T.act[l]);
+    e = adv::launch_fp8_calibrate(m->L, m->P, acts, n_rows, stream);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    m->fp8_calibrated = true;
+    return ADVISOR_OK;
+}
+
 advisor_status advisor_get_rescore_counts(advisor_model_t m, int64_t* h_counts, cudaStream_t stream) {
     if (!m || !h_counts || !m->WS) return ADVISOR_ERR_INVALID_ARGUMENT;
     int c[2] = {0, 0};
@@ -341,6 +362,8 @@ advisor_status advisor_model_create(const int32_t* h_widths, int32_t n_widths, a
         L.nslab[l] = L.kpad[l] / 64;
         if (L.widths[l + 1] > 256) L.tc_ok = 0;
         L.nmax = L.npad[l] > L.nmax ? L.npad[l] : L.nmax;
+        L.npad8[l] = roundup(L.widths[l + 1], 128);
+        L.nslab8[l] = roundup(L.widths[l], 128) / 128;
     }
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
@@ -349,9 +372,12 @@ advisor_status advisor_model_create(const int32_t* h_widths, int32_t n_widths, a
     for (int l = 0; l < L.n_hidden; ++l) {
         L.p_w16[0][l] = take((size_t)L.npad[l] * L.kpad[l] * 2);
         L.p_w16[1][l] = take((size_t)L.npad[l] * L.kpad[l] * 2);
-        L.p_bias_off[l] = take((size_t)L.npad[l] * 4);
+        // E4M3 copies only for models that run layer by layer
+        L.p_w8[l] = take(L.tc_ok ? 0 : (size_t)L.npad8[l] * L.nslab8[l] * ADV_SLAB_ROW_BYTES);
+        L.p_bias_off[l] = take((size_t)L.npad8[l] * 4);
     }
-    L.p_wout_pad = take((size_t)L.npad[L.n_hidden - 1] * 4);
+    L.p_fp8 = take(32 * 4);
+    L.p_wout_pad = take((size_t)L.npad8[L.n_hidden - 1] * 4);
     L.p_stdz_a = take((size_t)F * 4);
     L.p_stdz_c = take((size_t)F * 4);
     L.p_mu = take((size_t)F * 8);
@@ -413,6 +439,7 @@ advisor_status advisor_model_set_params(advisor_model_t m, const float* d_params
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     m->params_set = true;
     m->adam_step = 0;
+    m->fp8_calibrated = false;
     return ADVISOR_OK;
 }
 
@@ -458,16 +485,23 @@ advisor_status advisor_score_variants(advisor_model_t m, const int32_t* d_feat_q
         adv::RowSrc src{d_feat_q16, nullptr, nullptr, nullptr, n_rows, d_row_status};
         return cuda_status(adv::launch_mlp_fp32(mlp_desc(m), src, d_scores, m->num_sms, false, stream));
     }
-    if (precision != ADVISOR_BF16 && precision != ADVISOR_FP16) return ADVISOR_ERR_UNSUPPORTED;
-    const bool fused = tc_supported(m);
+    if (precision == ADVISOR_FP8_E4M3) {
+        if (!wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
+        if (!m->fp8_calibrated) return ADVISOR_ERR_INVALID_ARGUMENT;
+    } else if (precision != ADVISOR_BF16 && precision != ADVISOR_FP16) {
+        return ADVISOR_ERR_UNSUPPORTED;
+    }
+    const bool fused = tc_supported(m) && precision != ADVISOR_FP8_E4M3;
     if (!fused && !wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
-    const int fi = precision == ADVISOR_BF16 ? 0 : 1;
+    const int fi = precision == ADVISOR_BF16 ? 0 : (precision == ADVISOR_FP16 ? 1 : 2);
     const int64_t npad = ((n_rows + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
     uint8_t* x = m->WS + m->W.x_img;
-    cudaError_t e = adv::launch_standardize(d_feat_q16, d_row_status, n_rows, npad, x, m->L.nslab[0],
+    cudaError_t e = adv::launch_standardize(d_feat_q16, d_row_status, n_rows, npad, x,
+                                            fi == 2 ? m->L.nslab8[0] : m->L.nslab[0],
                                             reinterpret_cast<const float*>(m->P + m->L.p_stdz_a),
                                             reinterpret_cast<const float*>(m->P + m->L.p_stdz_c), m->L.F,
-                                            fi == 0 ? 1 : 2, stream);
+                                            fi + 1, stream,
+                                            reinterpret_cast<const float*>(m->P + m->L.p_fp8) + ADV_FP8_X_SCALE);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     if (!fused) return cuda_status(launch_wide(m, x, n_rows, d_row_status, d_scores, fi, stream));
     return cuda_status(launch_tc_profiled(m, tc_args(m, x, n_rows, d_row_status, d_scores, fi), stream));
@@ -534,14 +568,20 @@ advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_des
             return do_select(m, scores, n_rows, d_seg_off, n_kernels, rs, rescore, eps_scores, eps_fp32,
                              d_best_local, d_best_score, stream);
         }
-        if (precision != ADVISOR_BF16 && precision != ADVISOR_FP16) return ADVISOR_ERR_UNSUPPORTED;
-        const bool fused = tc_supported(m);
+        if (precision == ADVISOR_FP8_E4M3) {
+            if (!wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
+            if (!m->fp8_calibrated) return ADVISOR_ERR_INVALID_ARGUMENT;
+        } else if (precision != ADVISOR_BF16 && precision != ADVISOR_FP16) {
+            return ADVISOR_ERR_UNSUPPORTED;
+        }
+        const bool fused = tc_supported(m) && precision != ADVISOR_FP8_E4M3;
         if (!fused && !wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
-        const int fi = precision == ADVISOR_BF16 ? 0 : 1;
+        const int fi = precision == ADVISOR_BF16 ? 0 : (precision == ADVISOR_FP16 ? 1 : 2);
         a.n_rows_padded = ((n_rows + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
         a.x_img = m->WS + m->W.x_img;
-        a.nslab = L.nslab[0];
-        e = adv::launch_extract(a, L.F, fi == 0 ? 1 : 2, stream, m->cfg.extract_block);
+        a.nslab = fi == 2 ? L.nslab8[0] : L.nslab[0];
+        a.x8_scale = reinterpret_cast<const float*>(m->P + L.p_fp8) + ADV_FP8_X_SCALE;
+        e = adv::launch_extract(a, L.F, fi + 1, stream, m->cfg.extract_block);
         if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
         e = fused ? launch_tc_profiled(m, tc_args(m, a.x_img, n_rows, status, scores, fi), stream)
                   : launch_wide(m, a.x_img, n_rows, status, scores, fi, stream);

@@ -15,6 +15,14 @@
 #define ADV_SLAB_K 64           // 16-bit K elements per 128-byte swizzle row
 #define ADV_SLAB_ROW_BYTES 128
 #define ADV_X_SLAB_BYTES (ADV_TILE_M * ADV_SLAB_ROW_BYTES)   // 16 KB
+#define ADV_SLAB_K8 128         // 8-bit K elements per 128-byte swizzle row
+#define ADV_E4M3_MAX 448.0f     // largest finite E4M3 value
+// FP8 scale block (floats, in the parameter block): [0, 8) weight amax per
+// hidden layer (bit patterns of non-negative floats, reduced by atomicMax),
+// [8, 16) activation scale per hidden-layer input, [16] calibrated flag.
+#define ADV_FP8_W_AMAX 0
+#define ADV_FP8_X_SCALE 8
+#define ADV_FP8_CALIBRATED 16
 
 // Device status word bits (sticky, per model).
 #define ADV_DEV_TIMEOUT 1
@@ -41,12 +49,16 @@ struct ModelLayout {
     int nslab[ADV_MAX_LAYERS];      // kpad / 64
     int tc_ok;                      // every hidden width <= 256
     int nmax;                       // max npad over hidden layers
+    int npad8[ADV_MAX_LAYERS];      // output width rounded up to 128 (8-bit images)
+    int nslab8[ADV_MAX_LAYERS];     // input width rounded up to 128, / 128
     // parameter block
     size_t p_master, p_wout_pad, p_stdz_a, p_stdz_c, p_mu, p_sigma;
     size_t p_wT[ADV_MAX_LAYERS];       // transposed FP32 copy [in][out] of every layer
     size_t p_w16[2][ADV_MAX_LAYERS];   // [bf16, fp16] smem-image weights of hidden layers
+    size_t p_w8[ADV_MAX_LAYERS];       // E4M3 images (wide models only), [nslab8][npad8 rows][128 B]
+    size_t p_fp8;                      // FP8 scale block (ADV_FP8_*)
     size_t p_adam_m, p_adam_v, p_status, p_misc;
-    size_t p_bias_off[ADV_MAX_LAYERS]; // per hidden layer: bias zero-padded to npad (floats)
+    size_t p_bias_off[ADV_MAX_LAYERS]; // per hidden layer: bias zero-padded to npad8 >= npad (floats)
     size_t param_bytes;
 };
 
@@ -153,6 +165,26 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// Same with 8-bit operands (kind::f8f6f4; E4M3 x E4M3 with the format codes
+// of f16_idesc(0, ...)), K = 32 per instruction.
+__device__ __forceinline__ void umma_f8f6f4(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Two FP32 values -> two E4M3 bytes (lo in the low byte), round to nearest
+// even, saturating at +-448.
+__device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
+    uint16_t d;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
 // Arrive once on `bar` when every tcgen05 op issued so far by this thread completes.
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(

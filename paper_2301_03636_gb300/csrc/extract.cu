@@ -36,6 +36,41 @@ __device__ __forceinline__ uint4 pack8(const float (&z)[8]) {
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// Write one row of the E4M3 activation image: one slab per 128 features
+// (128-byte rows of 8-bit values, 16-byte chunk c = features 16c..16c+15 of
+// row r at chunk position c ^ (r % 8)), standardised values times inv_s
+// (the reciprocal of the first layer's per-tensor activation scale).
+template <int F>
+__device__ __forceinline__ void write_x_row_e4m3(uint8_t* x_img, int nslab, int64_t row, const int32_t (&f)[F],
+                                                 bool valid_row, const float* __restrict__ sa,
+                                                 const float* __restrict__ sc, float inv_s) {
+    const int64_t tile = row / ADV_TILE_M;
+    const uint32_t r = (uint32_t)(row % ADV_TILE_M);
+    uint8_t* tile_base = x_img + (size_t)tile * nslab * ADV_X_SLAB_BYTES;
+#pragma unroll
+    for (int s = 0; s < (F + 127) / 128; ++s) {
+        if (s >= nslab) break;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float z[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int k = s * 128 + c * 16 + 4 * i + e;
+                    z[e] = (valid_row && k < F)
+                               ? fmaf((float)f[k < F ? k : 0], __ldg(sa + (k < F ? k : 0)), -__ldg(sc + (k < F ? k : 0))) * inv_s
+                               : 0.f;
+                }
+                w[i] = e4m3x2(z[0], z[1]) | (e4m3x2(z[2], z[3]) << 16);
+            }
+            *reinterpret_cast<uint4*>(tile_base + (size_t)s * ADV_X_SLAB_BYTES + sw128_offset(r, c)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
 // Write one row of the 16-bit activation image: row `row` of the tile grid,
 // kpad = nslab * 64 columns, features beyond F (and rows beyond n) are zero.
 template <int F, int FMT>
@@ -92,7 +127,9 @@ __global__ void __launch_bounds__(256) extract_kernel(ExtractArgs a) {
 #pragma unroll
         for (int j = 0; j < F; ++j) f[j] = 0;
     }
-    if constexpr (FMT != 0) {
+    if constexpr (FMT == 3) {
+        if (a.x_img) write_x_row_e4m3<F>(a.x_img, a.nslab, row, f, valid, a.sa, a.sc, 1.f / __ldg(a.x8_scale));
+    } else if constexpr (FMT != 0) {
         if (a.x_img) write_x_row<F, FMT>(a.x_img, a.nslab, row, f, valid, a.sa, a.sc);
     }
 }
@@ -103,7 +140,8 @@ __global__ void __launch_bounds__(128) standardize_kernel(const int32_t* __restr
                                                           const uint8_t* __restrict__ status, int64_t n_rows,
                                                           int64_t n_rows_padded, uint8_t* x_img, int nslab,
                                                           const float* __restrict__ sa,
-                                                          const float* __restrict__ sc) {
+                                                          const float* __restrict__ sc,
+                                                          const float* __restrict__ x8_scale) {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= n_rows_padded) return;
     int32_t f[F];
@@ -120,7 +158,8 @@ __global__ void __launch_bounds__(128) standardize_kernel(const int32_t* __restr
         for (int j = 0; j < F; ++j) f[j] = 0;
     }
     (void)status;  // invalid rows are scored +inf by the scorer's epilogue
-    write_x_row<F, FMT>(x_img, nslab, row, f, valid, sa, sc);
+    if constexpr (FMT == 3) write_x_row_e4m3<F>(x_img, nslab, row, f, valid, sa, sc, 1.f / __ldg(x8_scale));
+    else write_x_row<F, FMT>(x_img, nslab, row, f, valid, sa, sc);
 }
 
 // Mean and population standard deviation of feature/65536 per column over
@@ -179,6 +218,7 @@ static cudaError_t launch_extract_f(const ExtractArgs& a, int fmt, cudaStream_t 
     if (grid == 0) return cudaSuccess;
     if (fmt == 1) extract_kernel<F, 1><<<grid, block, 0, s>>>(a);
     else if (fmt == 2) extract_kernel<F, 2><<<grid, block, 0, s>>>(a);
+    else if (fmt == 3) extract_kernel<F, 3><<<grid, block, 0, s>>>(a);
     else extract_kernel<F, 0><<<grid, block, 0, s>>>(a);
     adv_count_launch(1);
     return cudaGetLastError();
@@ -197,21 +237,24 @@ cudaError_t launch_extract(const ExtractArgs& a, int F, int fmt, cudaStream_t s,
 template <int F>
 static cudaError_t launch_standardize_f(const int32_t* feat, const uint8_t* status, int64_t n, int64_t npad,
                                         uint8_t* x_img, int nslab, const float* sa, const float* sc, int fmt,
-                                        cudaStream_t s) {
+                                        const float* x8_scale, cudaStream_t s) {
     const unsigned grid = (unsigned)((npad + 127) / 128);
     if (grid == 0) return cudaSuccess;
-    if (fmt == 1) standardize_kernel<F, 1><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc);
-    else standardize_kernel<F, 2><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc);
+    if (fmt == 3 && !x8_scale) return cudaErrorInvalidValue;
+    if (fmt == 1) standardize_kernel<F, 1><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc, x8_scale);
+    else if (fmt == 3) standardize_kernel<F, 3><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc, x8_scale);
+    else standardize_kernel<F, 2><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc, x8_scale);
     adv_count_launch(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_standardize(const int32_t* feat, const uint8_t* status, int64_t n, int64_t npad, uint8_t* x_img,
-                               int nslab, const float* sa, const float* sc, int F, int fmt, cudaStream_t s) {
+                               int nslab, const float* sa, const float* sc, int F, int fmt, cudaStream_t s,
+                               const float* x8_scale) {
     switch (F) {
-        case 32: return launch_standardize_f<32>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, s);
-        case 64: return launch_standardize_f<64>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, s);
-        case 128: return launch_standardize_f<128>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, s);
+        case 32: return launch_standardize_f<32>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, s);
+        case 64: return launch_standardize_f<64>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, s);
+        case 128: return launch_standardize_f<128>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -40,6 +40,7 @@ struct ExtractArgs {
     int nslab;               // slabs of the X image
     const float* sa;         // standardisation: z = f * sa - sc
     const float* sc;
+    const float* x8_scale;   // E4M3 image (format 3): the first layer's activation scale (device)
 };
 // Launch shapes of the hot path that a plan's autotuner may vary.  Every
 // choice gives bit-identical results: rows, segments and tiles are processed
@@ -56,7 +57,8 @@ bool launch_config_valid(const LaunchConfig& c);
 
 cudaError_t launch_extract(const ExtractArgs& a, int F, int fmt, cudaStream_t s, int block = 128);
 cudaError_t launch_standardize(const int32_t* feat, const uint8_t* status, int64_t n, int64_t npad, uint8_t* x_img,
-                               int nslab, const float* sa, const float* sc, int F, int fmt, cudaStream_t s);
+                               int nslab, const float* sa, const float* sc, int F, int fmt, cudaStream_t s,
+                               const float* x8_scale = nullptr);
 cudaError_t launch_fit_standardizer(const int32_t* feat, const uint8_t* status, int64_t n, int F, double* mu,
                                     double* sigma, cudaStream_t s);
 
@@ -100,7 +102,9 @@ struct LayerArgs {
     uint8_t* out_img;         // mode 0: [tile][npad / 64][128 x 128 B]
     const float* w_out;       // mode 1: [npad]
     float* partial;           // mode 1: [n_chunks][2][n_tiles * 128]
-    int fmt;                  // instruction-descriptor operand format: 1 BF16, 0 F16
+    int fmt;                  // operands: 1 BF16, 0 F16 (kind::f16), 2 E4M3 (kind::f8f6f4)
+    const float* fp8;         // E4M3: the model's FP8 scale block (ADV_FP8_*)
+    int layer;                // E4M3: hidden-layer index (its scales)
     int* status_word;
     uint64_t timeout_ns;
 };

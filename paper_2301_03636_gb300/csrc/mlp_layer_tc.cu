@@ -1,5 +1,8 @@
 // Per-layer tensor-core scorer for MLPs whose hidden layers are too wide for
-// the fused kernel (a4-a5 of the large sweep, e.g. 128-1024-1024-1024-1):
+// the fused kernel (a4-a5 of the large sweep, e.g. 128-1024-1024-1024-1),
+// with 16-bit operands (BF16 / FP16, kind::f16) or E4M3 operands
+// (kind::f8f6f4, per-tensor scales: H = ReLU(s_x s_w acc + b), re-quantised
+// with the next layer's activation scale):
 // each hidden layer is one persistent launch computing
 //     H_out = ReLU(H_in W^T + b)        (Sec. 4.2 regression, Sec. 5 Exp. 3 network)
 // with H_in / H_out in the same tiled 16-bit image the extraction kernel
@@ -34,6 +37,7 @@ constexpr int LG_THREADS = 32 * (LG_STAGES + 1 + LG_EPI_WARPS);
 constexpr uint32_t LG_B_BYTES = LG_BN * ADV_SLAB_ROW_BYTES;                 // 32 KB
 constexpr uint32_t LG_STAGE_BYTES = ADV_X_SLAB_BYTES + LG_B_BYTES;          // 48 KB
 
+// KIND: 0 F16, 1 BF16 (kind::f16), 2 E4M3 (kind::f8f6f4).
 template <int FMT>
 __device__ __forceinline__ uint32_t lg_relu_pack(float lo, float hi) {
     uint32_t d;
@@ -42,8 +46,9 @@ __device__ __forceinline__ uint32_t lg_relu_pack(float lo, float hi) {
     return d;
 }
 
-template <int FMT>
+template <int KIND>
 __global__ void __launch_bounds__(LG_THREADS, 1) mlp_layer_tc_kernel(const __grid_constant__ LayerArgs a) {
+    constexpr int FMT = KIND == 1 ? 1 : 0;   // instruction-descriptor format code (E4M3 shares F16's 0)
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_addr(smem_raw);
     uint8_t* base = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
@@ -146,8 +151,12 @@ __global__ void __launch_bounds__(LG_THREADS, 1) mlp_layer_tc_kernel(const __gri
                     const uint64_t adesc = sw128_desc(smem_addr(st));
                     const uint64_t bdesc = sw128_desc(smem_addr(st + ADV_X_SLAB_BYTES));
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        umma_f16(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, (k | kk) != 0);
+                    for (int kk = 0; kk < 4; ++kk) {   // 32 bytes of K per instruction
+                        if constexpr (KIND == 2)
+                            umma_f8f6f4(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, (k | kk) != 0);
+                        else
+                            umma_f16(d_tmem, adesc + 2u * kk, bdesc + 2u * kk, idesc, (k | kk) != 0);
+                    }
                     umma_commit(&empty[stage]);
                     any = true;
                 }
@@ -165,7 +174,13 @@ __global__ void __launch_bounds__(LG_THREADS, 1) mlp_layer_tc_kernel(const __gri
         const int quad = warp & 3;                  // TMEM lane quadrant
         const int half = e >> 2;                    // column half of the item
         const uint32_t r = (uint32_t)(quad * 32 + lane);
-        const int out_slabs = a.npad / ADV_SLAB_K;
+        const int out_slabs = a.npad / (KIND == 2 ? ADV_SLAB_K8 : ADV_SLAB_K);
+        float acc_scale = 1.f, out_inv = 1.f;   // E4M3: dequantise the accumulator, quantise the output
+        if constexpr (KIND == 2) {
+            const float w_amax = __uint_as_float(reinterpret_cast<const unsigned*>(a.fp8)[ADV_FP8_W_AMAX + a.layer]);
+            acc_scale = __ldg(a.fp8 + ADV_FP8_X_SCALE + a.layer) * (w_amax > 0.f ? w_amax / ADV_E4M3_MAX : 1.f);
+            if (a.mode == 0) out_inv = 1.f / __ldg(a.fp8 + ADV_FP8_X_SCALE + a.layer + 1);
+        }
         for (int i = 0; i < n_my; ++i) {
             const int64_t item = b + (int64_t)i * G;
             const int tile = (int)(item / a.n_chunks), chunk = (int)(item % a.n_chunks);
@@ -189,7 +204,25 @@ __global__ void __launch_bounds__(LG_THREADS, 1) mlp_layer_tc_kernel(const __gri
                 for (int u = 0; u < 4; ++u) bq[u] = __ldg(reinterpret_cast<const float4*>(a.bias + n0 + c0) + u);
                 tmem_wait_ld();
                 const float* bf = reinterpret_cast<const float*>(bq);
-                if (a.mode == 0) {
+                if constexpr (KIND == 2) {
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) v[u] = __float_as_uint(__uint_as_float(v[u]) * acc_scale);
+                }
+                if (KIND == 2 && a.mode == 0) {
+                    const int c = n0 + c0;          // first output column of these 16: one 16-byte chunk
+                    uint8_t* slab = a.out_img + ((size_t)tile * out_slabs + (c >> 7)) * ADV_X_SLAB_BYTES;
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        float z[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            z[e] = fmaxf(__uint_as_float(v[4 * t + e]) + bf[4 * t + e], 0.f) * out_inv;
+                        pk[t] = e4m3x2(z[0], z[1]) | (e4m3x2(z[2], z[3]) << 16);
+                    }
+                    *reinterpret_cast<uint4*>(slab + sw128_offset(r, (uint32_t)((c & 127) >> 4))) =
+                        make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                } else if (a.mode == 0) {
                     const int c = n0 + c0;          // first output column of these 16
                     uint8_t* slab = a.out_img + ((size_t)tile * out_slabs + (c >> 6)) * ADV_X_SLAB_BYTES;
 #pragma unroll
@@ -252,7 +285,8 @@ cudaError_t launch_mlp_layer_tc(const LayerArgs& a, int num_sms, cudaStream_t s)
     if (a.npad <= 0 || a.npad % ADV_SLAB_K != 0 || a.a_slabs <= 0 || a.n_chunks != (a.npad + LG_BN - 1) / LG_BN)
         return cudaErrorInvalidValue;
     const size_t smem = mlp_layer_tc_smem_bytes();
-    auto kern = a.fmt == 1 ? mlp_layer_tc_kernel<1> : mlp_layer_tc_kernel<0>;
+    if (a.fmt == 2 && (!a.fp8 || a.npad % ADV_SLAB_K8 != 0)) return cudaErrorInvalidValue;
+    auto kern = a.fmt == 1 ? mlp_layer_tc_kernel<1> : (a.fmt == 2 ? mlp_layer_tc_kernel<2> : mlp_layer_tc_kernel<0>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t items = (int64_t)a.n_tiles * a.n_chunks;

@@ -37,6 +37,66 @@ __global__ void pack_w16_kernel(const float* __restrict__ W, int fo, int fi, int
     }
 }
 
+// max |x| over n values, folded into *amax_bits by atomicMax on the bit
+// pattern (non-negative floats order like their bit patterns).
+__global__ void amax_kernel(const float* __restrict__ x, int64_t n, unsigned* amax_bits) {
+    __shared__ float red[32];
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) atomicMax(amax_bits, __float_as_uint(m));
+    }
+}
+
+// E4M3 weight image of a hidden layer: slab k holds rows n = 0..npad8-1 of
+// W[n][128k .. 128k+127] / s as 8-bit values, 128 bytes per row, 16-byte
+// chunk c of row n at chunk position c ^ (n % 8); s = amax / 448 (per-tensor
+// scale, exact amax).  Padding is zero.
+__global__ void pack_w8_kernel(const float* __restrict__ W, int fo, int fi, int npad8, int nslab8,
+                               const unsigned* __restrict__ amax_bits, uint8_t* __restrict__ img) {
+    const float amax = __uint_as_float(*amax_bits);
+    const float inv = amax > 0.f ? ADV_E4M3_MAX / amax : 1.f;
+    const int kchunks = nslab8 * 8;                     // 16-element chunks per row
+    const int64_t total = (int64_t)npad8 * kchunks;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(c / kchunks);
+        const int kc = (int)(c % kchunks);
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = kc * 16 + 4 * i + e;
+                v[e] = (n < fo && k < fi) ? W[(size_t)n * fi + k] * inv : 0.f;
+            }
+            w[i] = e4m3x2(v[0], v[1]) | (e4m3x2(v[2], v[3]) << 16);
+        }
+        const size_t off = (size_t)(kc / 8) * npad8 * ADV_SLAB_ROW_BYTES + sw128_offset((uint32_t)n, (uint32_t)(kc % 8));
+        *reinterpret_cast<uint4*>(img + off) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Activation scales from the calibration amax values, in place: scale =
+// amax / 448 (1 when the amax is 0); then mark the model calibrated.
+__global__ void fp8_finalize_kernel(float* fp8, int n_hidden) {
+    if (threadIdx.x == 0) {
+        for (int l = 0; l < n_hidden; ++l) {
+            const float amax = __uint_as_float(reinterpret_cast<unsigned*>(fp8)[ADV_FP8_X_SCALE + l]);
+            fp8[ADV_FP8_X_SCALE + l] = amax > 0.f ? amax / ADV_E4M3_MAX : 1.f;
+        }
+        fp8[ADV_FP8_CALIBRATED] = 1.f;
+    }
+}
+
 // WT[k][n] = W[n][k], rows of ld >= fo floats, zero beyond fo.
 __global__ void transpose_kernel(const float* __restrict__ W, int fo, int fi, int ld, float* __restrict__ WT) {
     const int64_t total = (int64_t)ld * fi;
@@ -92,15 +152,24 @@ cudaError_t launch_repack(const ModelLayout& L, uint8_t* P, cudaStream_t s) {
             const int64_t chunks = (int64_t)L.npad[l] * L.kpad[l] / 8;
             pack_w16_kernel<<<grid_for(chunks), 256, 0, s>>>(W, fo, fi, L.npad[l], L.kpad[l], P + L.p_w16[0][l],
                                                             P + L.p_w16[1][l]);
-            pad_copy_kernel<<<grid_for(L.npad[l]), 256, 0, s>>>(master + L.layer_b_off[l], fo, L.npad[l],
-                                                               reinterpret_cast<float*>(P + L.p_bias_off[l]));
+            pad_copy_kernel<<<grid_for(L.npad8[l]), 256, 0, s>>>(master + L.layer_b_off[l], fo, L.npad8[l],
+                                                                reinterpret_cast<float*>(P + L.p_bias_off[l]));
             adv_count_launch(2);
+            if (!L.tc_ok) {   // E4M3 copy for the layer-by-layer path
+                unsigned* amax = reinterpret_cast<unsigned*>(P + L.p_fp8) + ADV_FP8_W_AMAX + l;
+                cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned), s);
+                if (e != cudaSuccess) return e;
+                amax_kernel<<<grid_for((int64_t)fo * fi), 256, 0, s>>>(W, (int64_t)fo * fi, amax);
+                pack_w8_kernel<<<grid_for((int64_t)L.npad8[l] * L.nslab8[l] * 8), 256, 0, s>>>(
+                    W, fo, fi, L.npad8[l], L.nslab8[l], amax, P + L.p_w8[l]);
+                adv_count_launch(2);
+            }
         }
         adv_count_launch(1);
     }
     const int last = L.n_layers - 1;
-    pad_copy_kernel<<<grid_for(L.npad[last - 1]), 256, 0, s>>>(master + L.layer_w_off[last], L.widths[last],
-                                                              L.npad[last - 1],
+    pad_copy_kernel<<<grid_for(L.npad8[last - 1]), 256, 0, s>>>(master + L.layer_w_off[last], L.widths[last],
+                                                               L.npad8[last - 1],
                                                               reinterpret_cast<float*>(P + L.p_wout_pad));
     adv_count_launch(1);
     return cudaGetLastError();
@@ -108,6 +177,9 @@ cudaError_t launch_repack(const ModelLayout& L, uint8_t* P, cudaStream_t s) {
 
 cudaError_t launch_set_params(const ModelLayout& L, uint8_t* P, const float* params, const double* mu,
                               const double* sigma, cudaStream_t s) {
+    // new parameters: the FP8 activation scales must be calibrated again
+    cudaError_t e0 = cudaMemsetAsync(P + L.p_fp8, 0, 32 * sizeof(float), s);
+    if (e0 != cudaSuccess) return e0;
     copy_f32_kernel<<<grid_for(L.n_params), 256, 0, s>>>(params, reinterpret_cast<float*>(P + L.p_master),
                                                          L.n_params);
     stdz_kernel<<<(L.F + 127) / 128, 128, 0, s>>>(mu, sigma, L.F, reinterpret_cast<float*>(P + L.p_stdz_a),
@@ -126,6 +198,21 @@ cudaError_t launch_set_params(const ModelLayout& L, uint8_t* P, const float* par
 
 cudaError_t launch_copy_f32(const float* src, float* dst, int64_t n, cudaStream_t s) {
     copy_f32_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, n);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp8_calibrate(const ModelLayout& L, uint8_t* P, const float* const* acts, int64_t n,
+                                 cudaStream_t s) {
+    float* fp8 = reinterpret_cast<float*>(P + L.p_fp8);
+    cudaError_t e = cudaMemsetAsync(fp8 + ADV_FP8_X_SCALE, 0, ADV_MAX_LAYERS * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    for (int l = 0; l < L.n_hidden; ++l) {
+        const int64_t cnt = n * L.widths[l];
+        amax_kernel<<<grid_for(cnt), 256, 0, s>>>(acts[l], cnt, reinterpret_cast<unsigned*>(fp8) + ADV_FP8_X_SCALE + l);
+        adv_count_launch(1);
+    }
+    fp8_finalize_kernel<<<1, 32, 0, s>>>(fp8, L.n_hidden);
     adv_count_launch(1);
     return cudaGetLastError();
 }

@@ -29,10 +29,11 @@ def wide():
     m = advisor.Model(WIDE, max_rows=max(n, 16384), max_kernels=192)
     m.set_params(p, mu, sigma)
     fcal, scal = advisor.advisor_extract_features(torch.from_numpy(cal).cuda(), 128)
+    m.calibrate_fp8(fcal)   # static E4M3 activation scales from the calibration sample
     return dict(off=off, d=d, n=n, m=m, best_ref=best_ref, y_ref=y_ref, fcal=fcal, scal=scal)
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("precision", ["bf16", "fp16", "fp8"])
 def test_wide_scores_within_calibrated_bound(gpu_lib, wide, precision):
     m = wide["m"]
     d = torch.from_numpy(wide["d"]).cuda()
@@ -48,7 +49,7 @@ def test_wide_scores_within_calibrated_bound(gpu_lib, wide, precision):
     assert err.max() <= eps / 2 * 1.5   # eps = 2 x the max on the calibration sample
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("precision", ["bf16", "fp16", "fp8"])
 def test_wide_rank_selection_identical(gpu_lib, wide, precision):
     m = wide["m"]
     eps = m.calibrate_eps(wide["fcal"], wide["scal"], precision)
@@ -57,7 +58,8 @@ def test_wide_rank_selection_identical(gpu_lib, wide, precision):
     o = torch.from_numpy(wide["off"]).cuda()
     best, _ = m.rank(d, o, precision, eps=eps, eps32=eps32)
     b = best.cpu().numpy()
-    print(f"{precision}: mismatches {(b != wide['best_ref']).sum()} of {len(b)}")
+    c32, c64 = m.rescore_counts()
+    print(f"{precision}: mismatches {(b != wide['best_ref']).sum()} of {len(b)}; re-scored {c32} FP32, {c64} FP64")
     assert np.array_equal(b, wide["best_ref"])
     assert m.device_status() == 0
 
@@ -104,3 +106,31 @@ def test_large_sweep_full_size_sampled_kernels(gpu_lib):
     ref = oracle.rank(np.concatenate(rows), sub_off, wl.widths, p, mu, sigma)[0]
     assert np.array_equal(b[ks], ref)
     assert m.device_status() == 0
+
+
+def test_fp8_needs_a_wide_model_and_a_calibration(gpu_lib, wide):
+    """E4M3 scoring: rejected for models that fit the fused 16-bit scorer,
+    before the activation scales are calibrated, and again after new
+    parameters are set."""
+    narrow = advisor.Model((64, 256, 256, 256, 1), max_rows=256, max_kernels=1)
+    narrow.set_params(W.make_weights((64, 256, 256, 256, 1), 1), np.zeros(64), np.ones(64))
+    f = torch.zeros((256, 64), dtype=torch.int32, device="cuda")
+    with pytest.raises(advisor.AdvisorError) as e:
+        narrow.calibrate_fp8(f)
+    assert e.value.code == 6   # ADVISOR_ERR_UNSUPPORTED
+    with pytest.raises(advisor.AdvisorError) as e:
+        narrow.score(f, None, "fp8")
+    assert e.value.code == 6
+    m = advisor.Model(WIDE, max_rows=16384, max_kernels=1)
+    p = W.make_weights(WIDE, 6)
+    m.set_params(p, np.zeros(128), np.ones(128))
+    f8 = wide["fcal"][:300]
+    with pytest.raises(advisor.AdvisorError) as e:
+        m.score(f8, None, "fp8")
+    assert e.value.code == 1   # ADVISOR_ERR_INVALID_ARGUMENT: not calibrated
+    m.calibrate_fp8(wide["fcal"])
+    y = m.score(f8, None, "fp8")
+    assert torch.isfinite(y).all()
+    m.set_params(p, np.zeros(128), np.ones(128))   # new parameters clear the scales
+    with pytest.raises(advisor.AdvisorError):
+        m.score(f8, None, "fp8")
