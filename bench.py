@@ -208,9 +208,26 @@ def training_leg(dev, steps=20):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
     flop = 3 * 65536 * FLOP_PER_ROW   # forward + two backward GEMMs per layer (first-layer dX skipped)
-    return {"workload": "batch 65,536, 64-256-256-256-1, FP32 SIMT forward/backward + Adam",
-            "ms_per_step": ms, "steps_per_s": 1000.0 / ms, "tflops": flop / (ms / 1000.0) / 1e12,
-            "loss_after": float(loss.item())}
+    out = {"workload": "batch 65,536, 64-256-256-256-1, forward / MSE / hand-written backward / Adam",
+           "fp32": {"ms_per_step": ms, "steps_per_s": 1000.0 / ms, "tflops": flop / (ms / 1000.0) / 1e12,
+                    "loss_after": float(loss.item()), "gemms": "FP32 SIMT"}}
+    _, tf, src = peaks()
+    for p in ("bf16", "fp16"):
+        m.set_params(wl.weights(), mu, sigma)
+        for _ in range(3):
+            m.train_step(f, t, p, loss=loss)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(steps):
+            m.train_step(f, t, p, loss=loss)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        ach = flop / (ms / 1000.0) / 1e12
+        out[p] = {"ms_per_step": ms, "steps_per_s": 1000.0 / ms, "tflops": ach, "frac_of_peak": ach / tf,
+                  "peak_source": src + " dense bf16", "loss_after": float(loss.item()),
+                  "gemms": p.upper() + " tensor cores (cuBLASLt), FP32 accumulation"}
+    return out
 
 
 def large_sweep_leg(dev, reps=5, rows=0):

@@ -405,17 +405,18 @@ class Plan:
 class MLPFunction(torch.autograd.Function):
     """y = MLP(features) with the library's hand-written backward.
 
-    apply(master, feat, model): `master` must be model.master() (the FP32
-    parameters the forward reads); its gradient comes from advisor_backward.
-    The features are integer inputs and get no gradient."""
+    apply(master, feat, model, precision="fp32"): `master` must be
+    model.master() (the FP32 parameters the forward reads); its gradient comes
+    from advisor_backward.  precision "bf16" / "fp16" runs the layer GEMMs on
+    the tensor cores.  The features are integer inputs and get no gradient."""
 
     @staticmethod
-    def forward(ctx, master, feat, model):
+    def forward(ctx, master, feat, model, precision="fp32"):
         ctx.model = model
         ctx.n = feat.shape[0]
-        return model.forward_saved(feat)
+        return model.forward_saved(feat, precision)
 
     @staticmethod
     def backward(ctx, dy):
         grad = ctx.model.backward(dy)
-        return grad, None, None
+        return grad, None, None, None

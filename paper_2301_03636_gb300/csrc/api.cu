@@ -46,6 +46,9 @@ struct advisor_model {
     int64_t saved_rows = 0;   // rows of the last advisor_forward_saved
     adv::LaunchConfig cfg{};  // launch shapes of the hot path (a plan may set them)
     bool fp8_calibrated = false;   // activation scales stored (advisor_model_calibrate_fp8)
+    int saved_fmt = 0;             // precision of the last advisor_forward_saved: 0 FP32, 1 BF16, 2 FP16
+    adv::LtContext* lt = nullptr;  // cuBLASLt handle of the 16-bit training GEMMs (created on first use)
+    ~advisor_model() { adv::lt_destroy(lt); }
 };
 
 namespace {
@@ -592,17 +595,30 @@ advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_des
                      d_best_local, d_best_score, stream);
 }
 
+// Training precision: 0 FP32 SIMT, 1 BF16 / 2 FP16 tensor-core GEMMs; -1 unsupported.
+int train_fmt(advisor_model* m, advisor_precision p) {
+    if (p == ADVISOR_FP32) return 0;
+    if (p != ADVISOR_BF16 && p != ADVISOR_FP16) return -1;
+    if (!m->lt) m->lt = adv::lt_create();
+    if (!m->lt) return -1;
+    return p == ADVISOR_BF16 ? 1 : 2;
+}
+
 advisor_status advisor_train_step(advisor_model_t m, const int32_t* d_feat_q16, const float* d_labels,
                                   int64_t n_rows, advisor_precision precision, const float* h_adam, float* d_loss,
                                   cudaStream_t stream) {
     if (!m || !d_feat_q16 || !d_labels || !h_adam || n_rows < 1) return ADVISOR_ERR_INVALID_ARGUMENT;
     advisor_status st = check_ready(m, n_rows);
     if (st != ADVISOR_OK) return st;
-    if (precision != ADVISOR_FP32) return ADVISOR_ERR_UNSUPPORTED;
+    const int fmt = train_fmt(m, precision);
+    if (fmt < 0) return ADVISOR_ERR_UNSUPPORTED;
     const adv::AdamHyper h{h_adam[0], h_adam[1], h_adam[2], h_adam[3], h_adam[4]};
     const int64_t step = m->adam_step + 1;
-    cudaError_t e = adv::launch_train_step(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), d_feat_q16, d_labels,
-                                           n_rows, &h, step, nullptr, d_loss, m->num_sms, stream);
+    cudaError_t e = fmt == 0 ? adv::launch_train_step(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), d_feat_q16,
+                                                      d_labels, n_rows, &h, step, nullptr, d_loss, m->num_sms, stream)
+                             : adv::launch_train_step_tc(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), m->lt,
+                                                         fmt, d_feat_q16, d_labels, n_rows, &h, step, nullptr, d_loss,
+                                                         stream);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     m->adam_step = step;
     return ADVISOR_OK;
@@ -614,7 +630,12 @@ advisor_status advisor_loss_grad(advisor_model_t m, const int32_t* d_feat_q16, c
     if (!m || !d_feat_q16 || !d_labels || !d_grad || n_rows < 1) return ADVISOR_ERR_INVALID_ARGUMENT;
     advisor_status st = check_ready(m, n_rows);
     if (st != ADVISOR_OK) return st;
-    if (precision != ADVISOR_FP32) return ADVISOR_ERR_UNSUPPORTED;
+    const int fmt = train_fmt(m, precision);
+    if (fmt < 0) return ADVISOR_ERR_UNSUPPORTED;
+    if (fmt != 0)
+        return cuda_status(adv::launch_train_step_tc(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), m->lt, fmt,
+                                                     d_feat_q16, d_labels, n_rows, nullptr, 0, d_grad, d_loss,
+                                                     stream));
     return cuda_status(adv::launch_train_step(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), d_feat_q16,
                                               d_labels, n_rows, nullptr, 0, d_grad, d_loss, m->num_sms, stream));
 }
@@ -631,11 +652,15 @@ advisor_status advisor_forward_saved(advisor_model_t m, const int32_t* d_feat_q1
     if (!m || !d_feat_q16 || n_rows < 1) return ADVISOR_ERR_INVALID_ARGUMENT;
     advisor_status st = check_ready(m, n_rows);
     if (st != ADVISOR_OK) return st;
-    if (precision != ADVISOR_FP32) return ADVISOR_ERR_UNSUPPORTED;
-    cudaError_t e = adv::launch_forward_saved(m->L, m->T, m->WS + m->W.train, mlp_desc(m), d_feat_q16, n_rows, d_y,
-                                              stream);
+    const int fmt = train_fmt(m, precision);
+    if (fmt < 0) return ADVISOR_ERR_UNSUPPORTED;
+    cudaError_t e = fmt == 0 ? adv::launch_forward_saved(m->L, m->T, m->WS + m->W.train, mlp_desc(m), d_feat_q16,
+                                                         n_rows, d_y, stream)
+                             : adv::launch_forward_saved_tc(m->L, m->T, m->WS + m->W.train, mlp_desc(m), m->lt, fmt,
+                                                            d_feat_q16, n_rows, d_y, stream);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     m->saved_rows = n_rows;
+    m->saved_fmt = fmt;
     return ADVISOR_OK;
 }
 
@@ -643,6 +668,9 @@ advisor_status advisor_backward(advisor_model_t m, const float* d_dy, int64_t n_
                                 cudaStream_t stream) {
     if (!m || !d_dy || !d_grad || n_rows < 1) return ADVISOR_ERR_INVALID_ARGUMENT;
     if (n_rows != m->saved_rows) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (m->saved_fmt != 0)
+        return cuda_status(adv::launch_backward_tc(m->L, m->T, m->WS + m->W.train, mlp_desc(m), m->lt, m->saved_fmt,
+                                                   d_dy, n_rows, d_grad, stream));
     return cuda_status(adv::launch_backward(m->L, m->T, m->WS + m->W.train, mlp_desc(m), d_dy, n_rows, d_grad, stream));
 }
 

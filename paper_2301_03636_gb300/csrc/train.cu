@@ -198,6 +198,18 @@ size_t train_layout(const ModelLayout& L, int64_t R, TrainLayout* t) {
     t->part = take((size_t)t->splits * lmax * 4);
     t->loss_part = take(1024 * 4);
     t->loss = take(64);
+    // 16-bit tensor-core training: 16-bit activations, weights and dZ
+    // ping-pong; the FP32 GEMM outputs reuse dB
+    t->x16 = take((size_t)R * L.F * 2);
+    for (int l = 0; l < L.n_hidden; ++l) {
+        t->h16[l] = take((size_t)R * L.widths[l + 1] * 2);
+        t->w16[l] = take((size_t)L.widths[l] * L.widths[l + 1] * 2);
+    }
+    t->dz16[0] = take((size_t)R * wmax * 2);
+    t->dz16[1] = take((size_t)R * wmax * 2);
+    t->c32 = t->dB;
+    t->lt_ws_bytes = (size_t)32 << 20;
+    t->lt_ws = take(t->lt_ws_bytes);
     t->rows = R;
     t->bytes = o;
     return o;
@@ -225,7 +237,7 @@ cudaError_t launch_forward_saved(const ModelLayout& L, const TrainLayout& T, uin
 }
 
 // dL/dy of loss = 0.5 mean (y - t)^2 into the gradient buffer, loss to d_loss.
-static cudaError_t launch_mse(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const float* labels,
+cudaError_t launch_mse_loss(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const float* labels,
                               int64_t n, float* d_loss, cudaStream_t s) {
     const int nb = 256;
     loss_kernel<<<nb, 256, 0, s>>>(reinterpret_cast<float*>(TW + T.act[L.n_layers]), labels, n,
@@ -294,18 +306,23 @@ cudaError_t launch_train_step(const ModelLayout& L, const TrainLayout& T, uint8_
     float* grad = d_grad_out ? d_grad_out : reinterpret_cast<float*>(TW + T.grad);
     cudaError_t e = launch_forward_saved(L, T, TW, md, feat, n, nullptr, s);
     if (e != cudaSuccess) return e;
-    e = launch_mse(L, T, TW, labels, n, d_loss, s);
+    e = launch_mse_loss(L, T, TW, labels, n, d_loss, s);
     if (e != cudaSuccess) return e;
     e = launch_backward_saved(L, T, TW, md, n, grad, s);
     if (e != cudaSuccess || !adam) return e;
-    const float c1 = (float)(1.0 - std::pow((double)adam->beta1, (double)step));
-    const float c2 = (float)(1.0 - std::pow((double)adam->beta2, (double)step));
+    return launch_adam_update(L, P, grad, *adam, step, s);
+}
+
+cudaError_t launch_adam_update(const ModelLayout& L, uint8_t* P, const float* grad, const AdamHyper& adam,
+                               int64_t step, cudaStream_t s) {
+    const float c1 = (float)(1.0 - std::pow((double)adam.beta1, (double)step));
+    const float c2 = (float)(1.0 - std::pow((double)adam.beta2, (double)step));
     adam_kernel<<<grid1(L.n_params), 256, 0, s>>>(reinterpret_cast<float*>(P + L.p_master), grad,
                                                   reinterpret_cast<float*>(P + L.p_adam_m),
-                                                  reinterpret_cast<float*>(P + L.p_adam_v), L.n_params, *adam, c1,
+                                                  reinterpret_cast<float*>(P + L.p_adam_v), L.n_params, adam, c1,
                                                   c2);
     adv_count_launch(1);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_repack(L, P, s);
 }

@@ -12,6 +12,13 @@ struct TrainLayout {
     size_t part;                      // split-K partial sums [splits][max(out*in + out)]
     size_t loss_part;                 // per-block loss partial sums
     size_t loss;                      // 1 float
+    // 16-bit tensor-core path (train_tc.cu)
+    size_t x16;                       // standardised input [R][F], 16-bit
+    size_t h16[ADV_MAX_LAYERS];       // hidden-layer outputs [R][w_{l+1}], 16-bit
+    size_t w16[ADV_MAX_LAYERS];       // row-major 16-bit copies of the hidden layers' weights
+    size_t dz16[2];                   // dZ ping-pong [R][wmax], 16-bit
+    size_t c32;                       // FP32 GEMM output [R][wmax] (aliases dB)
+    size_t lt_ws, lt_ws_bytes;        // cuBLASLt workspace
     int splits;
     int64_t rows;
     size_t bytes;
@@ -39,5 +46,26 @@ cudaError_t launch_forward_saved(const ModelLayout& L, const TrainLayout& T, uin
 // Backward of the last saved forward (same n) from dL/dy to d_grad.
 cudaError_t launch_backward(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
                             const float* d_dy, int64_t n, float* d_grad, cudaStream_t s);
+
+// dL/dy (into the dA buffer) and the loss of the saved forward output.
+cudaError_t launch_mse_loss(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const float* labels, int64_t n,
+                            float* d_loss, cudaStream_t s);
+// Adam update of the master weights (step counts from 1), then the repack.
+cudaError_t launch_adam_update(const ModelLayout& L, uint8_t* P, const float* grad, const AdamHyper& adam,
+                               int64_t step, cudaStream_t s);
+
+// 16-bit operands on the tensor cores (train_tc.cu); fmt 1 BF16, 2 FP16.
+struct LtContext;
+LtContext* lt_create();
+void lt_destroy(LtContext* c);
+cudaError_t launch_forward_saved_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
+                                    LtContext* lt, int fmt, const int32_t* feat, int64_t n, float* d_y,
+                                    cudaStream_t s);
+cudaError_t launch_backward_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
+                               LtContext* lt, int fmt, const float* d_dy, int64_t n, float* d_grad, cudaStream_t s);
+cudaError_t launch_train_step_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
+                                 const MlpDesc& md, LtContext* lt, int fmt, const int32_t* feat, const float* labels,
+                                 int64_t n, const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss,
+                                 cudaStream_t s);
 
 }  // namespace adv

@@ -1,0 +1,538 @@
+// Training mode with 16-bit operands on the tensor cores (Sec. 3 training
+// mode, Sec. 5 Exp. 3 network): the same forward, MSE loss on ln runtime,
+// hand-written backward and Adam update as the FP32 path in train.cu, with
+// every layer GEMM taking BF16 (or FP16) operands and accumulating in FP32:
+//   forward   C_l = H_{l-1} W_l^T (GEMM), H_l = 16-bit(ReLU(C_l + b_l)),
+//             y = H_L w_out + b_out (FP32 dot per row);
+//   backward  dZ_L = 16-bit(dy w_out^T masked by H_L > 0),
+//             dW_l = dZ_l^T H_{l-1}  (GEMM, K = rows, straight into the FP32 gradient),
+//             db_l = column sums of dZ_l (fixed split order),
+//             dZ_{l-1} = 16-bit(dZ_l W_l masked by H_{l-1} > 0);
+//   Adam on the FP32 master weights, then the derived copies are rebuilt.
+// The three GEMMs per layer are plain dense contractions and run through
+// cuBLASLt (tensor cores, FP32 accumulation, a workspace inside the caller's
+// buffer); every other step is a kernel of this file.  Activations are kept
+// in 16 bits between layers, so the masks use the stored 16-bit values
+// (positive iff the FP32 pre-activation rounded to a positive value).
+#include <algorithm>
+#include <new>
+
+#include <cublasLt.h>
+
+#include "pack.cuh"
+#include "train.cuh"
+
+namespace adv {
+
+namespace {
+
+constexpr int TC_SPLIT_ROWS = 1024;   // rows per partial sum of the column reductions
+
+int grid_n(int64_t n, int block = 256) {
+    const int64_t g = (n + block - 1) / block;
+    return (int)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
+}
+
+template <typename T>
+__device__ __forceinline__ T to16(float x);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ __half to16<__half>(float x) { return __float2half_rn(x); }
+template <typename T>
+__device__ __forceinline__ float from16(T x);
+template <>
+__device__ __forceinline__ float from16<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <>
+__device__ __forceinline__ float from16<__half>(__half x) { return __half2float(x); }
+
+template <typename T>
+__global__ void cvt16_kernel(const float* __restrict__ src, T* __restrict__ dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = to16<T>(src[i]);
+}
+
+// x[r][k] = 16-bit(f[r][k] * sa[k] - sc[k]), the standardisation of the scorers
+template <typename T>
+__global__ void stdz16_kernel(const int32_t* __restrict__ feat, int64_t n, int F, const float* __restrict__ sa,
+                              const float* __restrict__ sc, T* __restrict__ x) {
+    const int64_t total = n * F;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i % F);
+        x[i] = to16<T>(fmaf((float)feat[i], __ldg(sa + k), -__ldg(sc + k)));
+    }
+}
+
+template <typename T>
+__global__ void bias_relu16_kernel(const float* __restrict__ c, int64_t n, int w, const float* __restrict__ b,
+                                   T* __restrict__ h) {
+    const int64_t total = n * w;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        h[i] = to16<T>(fmaxf(c[i] + __ldg(b + (int)(i % w)), 0.f));
+}
+
+// y[r] = sum_j h[r][j] w_out[j] + b_out, one warp per row, fixed order
+template <typename T>
+__global__ void out_dot16_kernel(const T* __restrict__ h, int64_t n, int w, const float* __restrict__ wo,
+                                 const float* __restrict__ bo, float* __restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+        float s = 0.f;
+        for (int j = lane; j < w; j += 32) s = fmaf(from16<T>(h[r * w + j]), __ldg(wo + j), s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) y[r] = s + __ldg(bo);
+    }
+}
+
+// dz[r][j] = 16-bit(dy[r] w_out[j]) where h[r][j] > 0, else 0
+template <typename T>
+__global__ void dz_last16_kernel(const float* __restrict__ dy, const float* __restrict__ wo, const T* __restrict__ h,
+                                 int64_t n, int w, T* __restrict__ dz) {
+    const int64_t total = n * w;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        dz[i] = to16<T>(from16<T>(h[i]) > 0.f ? dy[i / w] * __ldg(wo + (int)(i % w)) : 0.f);
+}
+
+// dz[r][j] = 16-bit(c[r][j]) where h[r][j] > 0, else 0
+template <typename T>
+__global__ void mask16_kernel(const float* __restrict__ c, const T* __restrict__ h, int64_t n, int w,
+                              T* __restrict__ dz) {
+    const int64_t total = n * w;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        dz[i] = to16<T>(from16<T>(h[i]) > 0.f ? c[i] : 0.f);
+}
+
+// part[s][j] = sum over the rows of split s of wt[r] x[r][j] (wt null: 1), in row order
+template <typename T>
+__global__ void colsum16_kernel(const T* __restrict__ x, const float* __restrict__ wt, int64_t n, int w,
+                                float* __restrict__ part) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.y * TC_SPLIT_ROWS;
+    if (j >= w) return;
+    const int64_t r1 = r0 + TC_SPLIT_ROWS < n ? r0 + TC_SPLIT_ROWS : n;
+    float s = 0.f;
+    for (int64_t r = r0; r < r1; ++r) s = fmaf(wt ? wt[r] : 1.f, from16<T>(x[r * w + j]), s);
+    part[(size_t)blockIdx.y * w + j] = s;
+}
+
+// part[s] = sum of v over the rows of split s
+__global__ void rowsum_kernel(const float* __restrict__ v, int64_t n, float* __restrict__ part) {
+    __shared__ float red[32];
+    const int64_t r0 = (int64_t)blockIdx.x * TC_SPLIT_ROWS;
+    const int64_t r1 = r0 + TC_SPLIT_ROWS < n ? r0 + TC_SPLIT_ROWS : n;
+    float s = 0.f;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) s += v[r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        part[blockIdx.x] = t;
+    }
+}
+
+// out[j] = sum over s of part[s][j]: eight interleaved split sequences per
+// column (s = y, y + 8, ...) summed in split order, then combined in y order.
+// Block (32, 8), one block per 32 columns.
+__global__ void __launch_bounds__(256) splitsum16_kernel(const float* __restrict__ part, int splits, int w,
+                                                         float* __restrict__ out) {
+    __shared__ float red[8][33];
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    float s = 0.f;
+    if (j < w)
+        for (int i = threadIdx.y; i < splits; i += 8) s += part[(size_t)i * w + j];
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && j < w) {
+        float t = 0.f;
+#pragma unroll
+        for (int y = 0; y < 8; ++y) t += red[y][threadIdx.x];
+        out[j] = t;
+    }
+}
+
+void splitsum(const float* part, int splits, int w, float* out, cudaStream_t s) {
+    splitsum16_kernel<<<(w + 31) / 32, dim3(32, 8), 0, s>>>(part, splits, w, out);
+}
+
+// ---- vectorised forms: 8 consecutive columns (16 bytes of 16-bit values) per
+// thread, 32-bit indices; used when w % 8 == 0, 256 % (w / 8) == 0 and the
+// matrix has fewer than 2^31 elements.
+constexpr int VEC_ROWS = 256;   // rows per block of the fused column sums
+
+template <typename T>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi);
+template <>
+__device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+template <>
+__device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+template <typename T>
+__device__ __forceinline__ void unpack8(const uint4 u, float (&f)[8]) {
+    const T* h = reinterpret_cast<const T*>(&u);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) f[i] = from16<T>(h[i]);
+}
+__device__ __forceinline__ void load8f(const float* p, float (&f)[8]) {
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+    f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
+}
+template <typename T>
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+    return make_uint4(pack2<T>(f[0], f[1]), pack2<T>(f[2], f[3]), pack2<T>(f[4], f[5]), pack2<T>(f[6], f[7]));
+}
+
+bool vec_ok(int64_t n, int w) { return w % 8 == 0 && 256 % (w / 8) == 0 && n * w < ((int64_t)1 << 31); }
+
+template <typename T>
+__global__ void bias_relu16_vec_kernel(const float* __restrict__ c, int n, int w, const float* __restrict__ b,
+                                       T* __restrict__ h) {
+    const int w8 = w >> 3, total = n * w8;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < total; v += gridDim.x * blockDim.x) {
+        const int j = (v % w8) << 3;
+        float x[8], bb[8];
+        load8f(c + (size_t)v * 8, x);
+        load8f(b + j, bb);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fmaxf(x[i] + bb[i], 0.f);
+        reinterpret_cast<uint4*>(h)[v] = pack8<T>(x);
+    }
+}
+
+template <typename T>
+__global__ void stdz16_vec_kernel(const int32_t* __restrict__ feat, int n, int F, const float* __restrict__ sa,
+                                  const float* __restrict__ sc, T* __restrict__ x) {
+    const int f8 = F >> 3, total = n * f8;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < total; v += gridDim.x * blockDim.x) {
+        const int k = (v % f8) << 3;
+        const int4 a = reinterpret_cast<const int4*>(feat)[2 * v], bq = reinterpret_cast<const int4*>(feat)[2 * v + 1];
+        const int q[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
+        float z[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) z[i] = fmaf((float)q[i], __ldg(sa + k + i), -__ldg(sc + k + i));
+        reinterpret_cast<uint4*>(x)[v] = pack8<T>(z);
+    }
+}
+
+// dZ = 16-bit(g masked by h > 0) for a block of VEC_ROWS rows, with
+//   MODE 0: g[r][j] = c[r][j]                 (hidden layers)
+//   MODE 1: g[r][j] = dy[r] w_out[j]          (last hidden layer)
+// plus the block's column sums in row order: part0[block][j] = sum_r dZ[r][j]
+// (the bias gradient), and in MODE 1 part1[block][j] = sum_r dy[r] h[r][j]
+// (the output-row gradient).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) dz_colsum16_kernel(const float* __restrict__ c, const float* __restrict__ dy,
+                                                          const float* __restrict__ wo, const T* __restrict__ h,
+                                                          int n, int w, T* __restrict__ dz, float* __restrict__ part0,
+                                                          float* __restrict__ part1) {
+    __shared__ float red0[256 * 8], red1[MODE == 1 ? 256 * 8 : 1];
+    const int w8 = w >> 3;
+    const int cg = threadIdx.x % w8;            // column group: columns 8 cg .. 8 cg + 7
+    const int rl = threadIdx.x / w8;            // row lane
+    const int lanes = 256 / w8;                 // rows per pass
+    const int r0 = blockIdx.x * VEC_ROWS;
+    float s0[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, s1[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float wq[8];
+    if (MODE == 1) load8f(wo + 8 * cg, wq);
+    for (int r = r0 + rl; r < r0 + VEC_ROWS && r < n; r += lanes) {
+        const int v = r * w8 + cg;
+        float hv[8], g[8], o[8];
+        unpack8<T>(reinterpret_cast<const uint4*>(h)[v], hv);
+        if (MODE == 0) {
+            load8f(c + (size_t)v * 8, g);
+        } else {
+            const float d = dy[r];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) g[i] = d * wq[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) o[i] = hv[i] > 0.f ? g[i] : 0.f;
+        const uint4 pk = pack8<T>(o);
+        reinterpret_cast<uint4*>(dz)[v] = pk;
+        float q[8];
+        unpack8<T>(pk, q);   // the bias gradient sums the stored 16-bit dZ, as the GEMMs read it
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            s0[i] += q[i];
+            if (MODE == 1) s1[i] = fmaf(dy[r], hv[i], s1[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        red0[threadIdx.x * 8 + i] = s0[i];
+        if (MODE == 1) red1[threadIdx.x * 8 + i] = s1[i];
+    }
+    __syncthreads();
+    // row lanes of each column summed in lane order
+    for (int t = threadIdx.x; t < w; t += 256) {
+        const int g = t >> 3, i = t & 7;
+        float a0 = 0.f, a1 = 0.f;
+        for (int l = 0; l < lanes; ++l) {
+            a0 += red0[(l * w8 + g) * 8 + i];
+            if (MODE == 1) a1 += red1[(l * w8 + g) * 8 + i];
+        }
+        part0[(size_t)blockIdx.x * w + t] = a0;
+        if (MODE == 1) part1[(size_t)blockIdx.x * w + t] = a1;
+    }
+}
+
+}  // namespace
+
+// ---- cuBLASLt ------------------------------------------------------------------
+struct LtContext {
+    cublasLtHandle_t h = nullptr;
+    struct Entry {
+        int key[9];
+        cublasLtMatmulAlgo_t algo;
+        bool used = false;
+    };
+    Entry cache[64];
+};
+
+LtContext* lt_create() {
+    LtContext* c = new (std::nothrow) LtContext();
+    if (!c) return nullptr;
+    if (cublasLtCreate(&c->h) != CUBLAS_STATUS_SUCCESS) {
+        delete c;
+        return nullptr;
+    }
+    return c;
+}
+
+void lt_destroy(LtContext* c) {
+    if (!c) return;
+    if (c->h) cublasLtDestroy(c->h);
+    delete c;
+}
+
+// Column-major D[m x n] (FP32, ld ldd) = op(A) op(B) with 16-bit A (stored
+// ta ? k x m : m x k, ld lda) and B (stored tb ? n x k : k x n, ld ldb).
+static cudaError_t lt_gemm(LtContext* c, bool ta, bool tb, int m, int n, int k, const void* A, int lda, const void* B,
+                           int ldb, float* D, int ldd, cudaDataType_t ab, void* ws, size_t ws_bytes, cudaStream_t s) {
+    if (!c) return cudaErrorInvalidValue;
+    const int key[9] = {ta, tb, m, n, k, lda, ldb, ldd, (int)ab};
+    cublasLtMatmulDesc_t op = nullptr;
+    cublasLtMatrixLayout_t la = nullptr, lb = nullptr, ld = nullptr;
+    cublasStatus_t st = cublasLtMatmulDescCreate(&op, CUBLAS_COMPUTE_32F, CUDA_R_32F);
+    const cublasOperation_t opa = ta ? CUBLAS_OP_T : CUBLAS_OP_N, opb = tb ? CUBLAS_OP_T : CUBLAS_OP_N;
+    if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSA, &opa, sizeof(opa));
+    if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSB, &opb, sizeof(opb));
+    if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatrixLayoutCreate(&la, ab, ta ? k : m, ta ? m : k, lda);
+    if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatrixLayoutCreate(&lb, ab, tb ? n : k, tb ? k : n, ldb);
+    if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatrixLayoutCreate(&ld, CUDA_R_32F, m, n, ldd);
+    LtContext::Entry* hit = nullptr;
+    for (auto& e : c->cache)
+        if (e.used && std::equal(key, key + 9, e.key)) { hit = &e; break; }
+    if (st == CUBLAS_STATUS_SUCCESS && !hit) {
+        cublasLtMatmulPreference_t pref = nullptr;
+        st = cublasLtMatmulPreferenceCreate(&pref);
+        if (st == CUBLAS_STATUS_SUCCESS)
+            st = cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &ws_bytes,
+                                                      sizeof(ws_bytes));
+        cublasLtMatmulHeuristicResult_t res{};
+        int found = 0;
+        if (st == CUBLAS_STATUS_SUCCESS)
+            st = cublasLtMatmulAlgoGetHeuristic(c->h, op, la, lb, ld, ld, pref, 1, &res, &found);
+        if (pref) cublasLtMatmulPreferenceDestroy(pref);
+        if (st == CUBLAS_STATUS_SUCCESS && found > 0) {
+            for (auto& e : c->cache)
+                if (!e.used) { hit = &e; break; }
+            if (!hit) hit = &c->cache[0];   // full: replace the first entry
+            std::copy(key, key + 9, hit->key);
+            hit->algo = res.algo;
+            hit->used = true;
+        } else if (st == CUBLAS_STATUS_SUCCESS) {
+            st = CUBLAS_STATUS_NOT_SUPPORTED;
+        }
+    }
+    const float one = 1.f, zero = 0.f;
+    if (st == CUBLAS_STATUS_SUCCESS)
+        st = cublasLtMatmul(c->h, op, &one, A, la, B, lb, &zero, D, ld, D, ld, &hit->algo, ws, ws_bytes, s);
+    if (ld) cublasLtMatrixLayoutDestroy(ld);
+    if (lb) cublasLtMatrixLayoutDestroy(lb);
+    if (la) cublasLtMatrixLayoutDestroy(la);
+    if (op) cublasLtMatmulDescDestroy(op);
+    return st == CUBLAS_STATUS_SUCCESS ? cudaSuccess : cudaErrorUnknown;
+}
+
+// ---- the 16-bit training step -------------------------------------------------
+namespace {
+
+template <typename T>
+struct Tc {
+    const ModelLayout& L;
+    const TrainLayout& T_;
+    uint8_t* TW;
+    const MlpDesc& md;
+    LtContext* lt;
+    cudaDataType_t ab;
+
+    T* x16() const { return reinterpret_cast<T*>(TW + T_.x16); }
+    T* h16(int l) const { return reinterpret_cast<T*>(TW + T_.h16[l]); }
+    T* w16(int l) const { return reinterpret_cast<T*>(TW + T_.w16[l]); }
+    T* dz16(int i) const { return reinterpret_cast<T*>(TW + T_.dz16[i]); }
+    float* c32() const { return reinterpret_cast<float*>(TW + T_.c32); }
+    float* part() const { return reinterpret_cast<float*>(TW + T_.part); }
+    float* y() const { return reinterpret_cast<float*>(TW + T_.act[L.n_layers]); }
+    float* dy() const { return reinterpret_cast<float*>(TW + T_.dA); }
+    void* ws() const { return TW + T_.lt_ws; }
+    // input of hidden layer l: the standardised features or the previous layer's output
+    const T* in16(int l) const { return l == 0 ? x16() : h16(l - 1); }
+
+    cudaError_t forward(const int32_t* feat, int64_t n, cudaStream_t s) const {
+        for (int l = 0; l < L.n_hidden; ++l) {
+            const int64_t cnt = (int64_t)L.widths[l] * L.widths[l + 1];
+            cvt16_kernel<T><<<grid_n(cnt), 256, 0, s>>>(md.W[l], w16(l), cnt);
+        }
+        if (vec_ok(n, L.F) && L.F % 8 == 0)
+            stdz16_vec_kernel<T><<<grid_n(n * L.F / 8), 256, 0, s>>>(feat, (int)n, L.F, md.sa, md.sc, x16());
+        else
+            stdz16_kernel<T><<<grid_n(n * L.F), 256, 0, s>>>(feat, n, L.F, md.sa, md.sc, x16());
+        adv_count_launch(L.n_hidden + 1);
+        for (int l = 0; l < L.n_hidden; ++l) {
+            const int fi = L.widths[l], fo = L.widths[l + 1];
+            // row-major C[n][fo] = In[n][fi] W^T, i.e. column-major C^T = W In^T
+            cudaError_t e = lt_gemm(lt, true, false, fo, (int)n, fi, w16(l), fi, in16(l), fi, c32(), fo, ab, ws(),
+                                    T_.lt_ws_bytes, s);
+            if (e != cudaSuccess) return e;
+            if (vec_ok(n, fo))
+                bias_relu16_vec_kernel<T><<<grid_n(n * fo / 8), 256, 0, s>>>(c32(), (int)n, fo, md.b[l], h16(l));
+            else
+                bias_relu16_kernel<T><<<grid_n(n * fo), 256, 0, s>>>(c32(), n, fo, md.b[l], h16(l));
+            adv_count_launch(1);
+        }
+        const int wl = L.widths[L.n_hidden];
+        out_dot16_kernel<T><<<grid_n(n * 32), 256, 0, s>>>(h16(L.n_hidden - 1), n, wl, md.W[L.n_hidden],
+                                                           md.b[L.n_hidden], y());
+        adv_count_launch(1);
+        return cudaGetLastError();
+    }
+
+    // dL/dy in dy(); gradient (master layout) into grad
+    cudaError_t backward(int64_t n, float* grad, cudaStream_t s) const {
+        bool vec = true;
+        int64_t lmax = 0, wmax = 0;
+        for (int l = 0; l < L.n_layers; ++l) {
+            lmax = std::max<int64_t>(lmax, (int64_t)L.widths[l] * L.widths[l + 1]);
+            wmax = std::max<int64_t>(wmax, L.widths[l + 1]);
+        }
+        for (int l = 0; l < L.n_hidden; ++l) vec = vec && vec_ok(n, L.widths[l + 1]);
+        // the fused reductions keep two [blocks][w] partial arrays in the split-sum buffer
+        vec = vec && 2 * ((n + VEC_ROWS - 1) / VEC_ROWS) * wmax <= (int64_t)T_.splits * lmax;
+        if (vec) return backward_vec(n, grad, s);
+        const int splits = (int)((n + TC_SPLIT_ROWS - 1) / TC_SPLIT_ROWS);
+        const int H = L.n_hidden;
+        const int wl = L.widths[H];
+        // output layer: grad w_out = sum_r dy[r] H_L[r], grad b_out = sum_r dy[r]
+        dim3 cg((unsigned)((wl + 127) / 128), (unsigned)splits);
+        colsum16_kernel<T><<<cg, 128, 0, s>>>(h16(H - 1), dy(), n, wl, part());
+        splitsum(part(), splits, wl, grad + L.layer_w_off[H], s);
+        rowsum_kernel<<<splits, 256, 0, s>>>(dy(), n, part());
+        splitsum(part(), splits, 1, grad + L.layer_b_off[H], s);
+        dz_last16_kernel<T><<<grid_n(n * wl), 256, 0, s>>>(dy(), md.W[H], h16(H - 1), n, wl, dz16(0));
+        adv_count_launch(5);
+        int cur = 0;
+        for (int l = H - 1; l >= 0; --l) {
+            const int fi = L.widths[l], fo = L.widths[l + 1];
+            // dW[fo][fi] = dZ^T In: column-major dW^T[fi x fo] = In^T[fi x n] dZ[n x fo]
+            cudaError_t e = lt_gemm(lt, false, true, fi, fo, (int)n, in16(l), fi, dz16(cur), fo,
+                                    grad + L.layer_w_off[l], fi, ab, ws(), T_.lt_ws_bytes, s);
+            if (e != cudaSuccess) return e;
+            dim3 bg((unsigned)((fo + 127) / 128), (unsigned)splits);
+            colsum16_kernel<T><<<bg, 128, 0, s>>>(dz16(cur), nullptr, n, fo, part());
+            splitsum(part(), splits, fo, grad + L.layer_b_off[l], s);
+            adv_count_launch(2);
+            if (l == 0) break;
+            // dIn[n][fi] = dZ[n][fo] W[fo][fi]: column-major dIn^T = W^T dZ^T
+            e = lt_gemm(lt, false, false, fi, (int)n, fo, w16(l), fi, dz16(cur), fo, c32(), fi, ab, ws(),
+                        T_.lt_ws_bytes, s);
+            if (e != cudaSuccess) return e;
+            mask16_kernel<T><<<grid_n(n * fi), 256, 0, s>>>(c32(), h16(l - 1), n, fi, dz16(cur ^ 1));
+            adv_count_launch(1);
+            cur ^= 1;
+        }
+        return cudaGetLastError();
+    }
+
+    // The same backward with the dZ producers also reducing the bias (and
+    // output-row) gradients per 256-row block.
+    cudaError_t backward_vec(int64_t n, float* grad, cudaStream_t s) const {
+        const int blocks = (int)((n + VEC_ROWS - 1) / VEC_ROWS);
+        const int H = L.n_hidden;
+        const int wl = L.widths[H];
+        float* p0 = part();
+        float* p1 = part() + (size_t)blocks * wl;
+        dz_colsum16_kernel<T, 1><<<blocks, 256, 0, s>>>(nullptr, dy(), md.W[H], h16(H - 1), (int)n, wl, dz16(0), p0,
+                                                        p1);
+        splitsum(p1, blocks, wl, grad + L.layer_w_off[H], s);
+        rowsum_kernel<<<(int)((n + TC_SPLIT_ROWS - 1) / TC_SPLIT_ROWS), 256, 0, s>>>(dy(), n, p1);
+        splitsum(p1, (int)((n + TC_SPLIT_ROWS - 1) / TC_SPLIT_ROWS), 1,
+                                           grad + L.layer_b_off[H], s);
+        splitsum(p0, blocks, wl, grad + L.layer_b_off[H - 1], s);
+        adv_count_launch(5);
+        int cur = 0;
+        for (int l = H - 1; l >= 0; --l) {
+            const int fi = L.widths[l], fo = L.widths[l + 1];
+            cudaError_t e = lt_gemm(lt, false, true, fi, fo, (int)n, in16(l), fi, dz16(cur), fo,
+                                    grad + L.layer_w_off[l], fi, ab, ws(), T_.lt_ws_bytes, s);
+            if (e != cudaSuccess) return e;
+            if (l == 0) break;
+            e = lt_gemm(lt, false, false, fi, (int)n, fo, w16(l), fi, dz16(cur), fo, c32(), fi, ab, ws(),
+                        T_.lt_ws_bytes, s);
+            if (e != cudaSuccess) return e;
+            dz_colsum16_kernel<T, 0><<<blocks, 256, 0, s>>>(c32(), nullptr, nullptr, h16(l - 1), (int)n, fi,
+                                                            dz16(cur ^ 1), p0, nullptr);
+            splitsum(p0, blocks, fi, grad + L.layer_b_off[l - 1], s);
+            adv_count_launch(2);
+            cur ^= 1;
+        }
+        return cudaGetLastError();
+    }
+};
+
+}  // namespace
+
+cudaError_t launch_forward_saved_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
+                                    LtContext* lt, int fmt, const int32_t* feat, int64_t n, float* d_y,
+                                    cudaStream_t s) {
+    cudaError_t e;
+    if (fmt == 1) e = Tc<__nv_bfloat16>{L, T, TW, md, lt, CUDA_R_16BF}.forward(feat, n, s);
+    else e = Tc<__half>{L, T, TW, md, lt, CUDA_R_16F}.forward(feat, n, s);
+    if (e != cudaSuccess || !d_y) return e;
+    return launch_copy_f32(reinterpret_cast<const float*>(TW + T.act[L.n_layers]), d_y, n, s);
+}
+
+cudaError_t launch_backward_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
+                               LtContext* lt, int fmt, const float* d_dy, int64_t n, float* d_grad, cudaStream_t s) {
+    if (d_dy) {
+        cudaError_t e = launch_copy_f32(d_dy, reinterpret_cast<float*>(TW + T.dA), n, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (fmt == 1) return Tc<__nv_bfloat16>{L, T, TW, md, lt, CUDA_R_16BF}.backward(n, d_grad, s);
+    return Tc<__half>{L, T, TW, md, lt, CUDA_R_16F}.backward(n, d_grad, s);
+}
+
+cudaError_t launch_train_step_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
+                                 const MlpDesc& md, LtContext* lt, int fmt, const int32_t* feat, const float* labels,
+                                 int64_t n, const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss,
+                                 cudaStream_t s) {
+    float* grad = d_grad_out ? d_grad_out : reinterpret_cast<float*>(TW + T.grad);
+    cudaError_t e = launch_forward_saved_tc(L, T, TW, md, lt, fmt, feat, n, nullptr, s);
+    if (e != cudaSuccess) return e;
+    e = launch_mse_loss(L, T, TW, labels, n, d_loss, s);
+    if (e != cudaSuccess) return e;
+    e = launch_backward_tc(L, T, TW, md, lt, fmt, nullptr, n, grad, s);
+    if (e != cudaSuccess || !adam) return e;
+    return launch_adam_update(L, P, grad, *adam, step, s);
+}
+
+}  // namespace adv

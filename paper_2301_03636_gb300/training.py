@@ -26,9 +26,10 @@ def evaluate(model: advisor.Model, feat: torch.Tensor, labels: torch.Tensor, pre
 
 
 def train(model: advisor.Model, feat: torch.Tensor, labels: torch.Tensor, steps: int, batch: int,
-          lr: float = 1e-3, seed: int = 0, losses: list | None = None):
+          lr: float = 1e-3, seed: int = 0, losses: list | None = None, precision: str = "fp32"):
     """`steps` Adam steps on mini-batches of `batch` rows drawn without
-    replacement per epoch (a fixed permutation per epoch from `seed`)."""
+    replacement per epoch (a fixed permutation per epoch from `seed`);
+    precision "fp32" (SIMT) or "bf16" / "fp16" (tensor-core GEMMs)."""
     n = feat.shape[0]
     g = torch.Generator(device="cpu").manual_seed(seed)
     loss = torch.empty(1, dtype=torch.float32, device=feat.device)
@@ -44,7 +45,7 @@ def train(model: advisor.Model, feat: torch.Tensor, labels: torch.Tensor, steps:
             fb, lb = feat, labels
         else:
             fb, lb = feat.index_select(0, idx).contiguous(), labels.index_select(0, idx).contiguous()
-        model.train_step(fb, lb, "fp32", lr=lr, loss=loss)
+        model.train_step(fb, lb, precision, lr=lr, loss=loss)
         if losses is not None:
             losses.append(loss.clone())
     return model

@@ -129,3 +129,53 @@ def test_training_workload_meets_nrmse_criterion(gpu_lib):
     print(f"loss {first:.4f} -> {last:.4f}; validation RMSE {ev['rmse']:.4f} NRMSE {ev['nrmse']:.4f}")
     assert last < 0.25 * first
     assert ev["nrmse"] < metrics.SUCCESS_NRMSE
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_tensor_core_gradient_matches_oracle(gpu_lib, precision):
+    """16-bit operands on the tensor cores, FP32 accumulation: the gradient
+    within per-tensor relative L2 1e-2 and cosine 0.999 of the FP64 oracle."""
+    m, d, f, t, p, mu, sg = _setup(8192, 35)
+    loss_ref, g_ref = oracle.loss_grad(f, t, WIDTHS, p, mu, sg)
+    loss, g = m.loss_grad(torch.from_numpy(f).cuda(), torch.from_numpy(t).cuda(), precision)
+    g = g.cpu().numpy().astype(np.float64)
+    rel = _split_rel(g, g_ref, WIDTHS)
+    cos = float(g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref)))
+    print(precision, "loss", float(loss.item()), loss_ref, "per-tensor rel-L2:", np.array2string(rel, precision=4),
+          "cos", cos)
+    assert abs(float(loss.item()) - loss_ref) <= 1e-2 * abs(loss_ref)
+    assert rel.max() < 1e-2 and cos > 0.999
+
+
+def test_tensor_core_autograd_function(gpu_lib):
+    m, d, f, t, p, mu, sg = _setup(4096, 36)
+    _, g_ref = oracle.loss_grad(f, t, WIDTHS, p, mu, sg)
+    master = m.master().clone().requires_grad_(True)
+    ft, tt = torch.from_numpy(f).cuda(), torch.from_numpy(t).cuda()
+    y = advisor.MLPFunction.apply(master, ft, m, "bf16")
+    loss = 0.5 * ((y - tt) ** 2).mean()
+    loss.backward()
+    rel = _split_rel(master.grad.cpu().numpy().astype(np.float64), g_ref, WIDTHS)
+    assert rel.max() < 1e-2
+    y_ref = oracle.mlp_forward(f, WIDTHS, p, mu, sg)
+    assert np.abs(y.detach().cpu().numpy() - y_ref).max() < 0.1
+
+
+def test_tensor_core_training_meets_nrmse_criterion(gpu_lib):
+    wl = W.TRAINING
+    d_tr = W.make_descriptors(65536, W.SEEDS["c4"])
+    d_va = W.make_descriptors(16384, W.SEEDS["c4_val"])
+    t_tr, t_va = W.make_labels(d_tr, W.SEEDS["c4"]), W.make_labels(d_va, W.SEEDS["c4_val"])
+    f_tr, s_tr = advisor.advisor_extract_features(torch.from_numpy(d_tr).cuda(), 64)
+    f_va, _ = advisor.advisor_extract_features(torch.from_numpy(d_va).cuda(), 64)
+    mu, sigma = advisor.advisor_fit_standardizer(f_tr, s_tr)
+    m = advisor.Model(wl.widths, max_rows=65536, max_kernels=1)
+    m.set_params(wl.weights(), mu, sigma)
+    losses = []
+    training.train(m, f_tr, torch.from_numpy(t_tr).cuda(), steps=400, batch=65536, lr=1e-3, losses=losses,
+                   precision="bf16")
+    first, last = float(losses[0].item()), float(losses[-1].item())
+    ev = training.evaluate(m, f_va, torch.from_numpy(t_va).cuda())
+    print(f"bf16: loss {first:.4f} -> {last:.4f}; validation RMSE {ev['rmse']:.4f} NRMSE {ev['nrmse']:.4f}")
+    assert last < 0.25 * first
+    assert ev["nrmse"] < metrics.SUCCESS_NRMSE
