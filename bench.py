@@ -230,6 +230,47 @@ def training_leg(dev, steps=20):
     return out
 
 
+def plain_latency_leg(dev, reps=500):
+    """The small case: 64 kernels x 8 variants = 512 descriptors, F = 32, MLP
+    32-128-128-1 (He init).  One call = the whole path a1-a7 replayed as a
+    CUDA graph (advisor_plan_rank); FP32 SIMT scorer vs BF16 tensor cores (+
+    near-tie re-score).  Per-call device time (events around each replay, no
+    L2 flush: the inputs are 64 KB)."""
+    import torch
+
+    from paper_2301_03636_gb300 import advisor
+    wl = W.PLAIN_FP32_512
+    off = wl.offsets()
+    n, K = int(off[-1]), wl.n_kernels
+    d = torch.from_numpy(wl.descriptors()).to(dev)
+    o = torch.from_numpy(off).to(dev)
+    cal = torch.from_numpy(W.calibration_descriptors(16384)).to(dev)
+    fcal, scal = advisor.advisor_extract_features(cal, wl.n_features)
+    mu, sigma = advisor.advisor_fit_standardizer(fcal, scal)
+    m = advisor.Model(wl.widths, max_rows=16384, max_kernels=K, device=dev)
+    m.set_params(wl.weights(), mu, sigma)
+    eps32 = m.calibrate_eps(fcal, scal, "fp32")
+    out = {"workload": f"{K} kernels x 8 variants = {n} descriptors, F=32, MLP 32-128-128-1", "variants": n}
+    for p in ("fp32", "bf16"):
+        eps = m.calibrate_eps(fcal, scal, p)
+        plan = m.plan_rank(d, o, p, eps, eps32, autotune=False)
+        for _ in range(20):
+            plan.launch()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record()
+            plan.launch()
+            b.record()
+        torch.cuda.synchronize()
+        t = np.array([a.elapsed_time(b) * 1000.0 for a, b in ev])
+        out[p] = {"us_per_call_median": float(np.median(t)), "us_per_call_p99": float(np.quantile(t, 0.99)),
+                  "variants_per_s": n / (float(np.median(t)) * 1e-6),
+                  "kernels_per_call": plan.info()["kernels_per_replay"]}
+        plan.close()
+    return out
+
+
 def large_sweep_leg(dev, reps=5, rows=0):
     """The large sweep: 2^20 variants of 65,536 kernels (2..64 each), F = 128,
     MLP 128-1024-1024-1024-1, scored on the tensor cores one launch per hidden
@@ -532,6 +573,7 @@ def main():
         out["serving"] = serving_leg(dev)
         srv10 = [r for r in out["serving"]["runs"] if r["rate_per_s"] == 10000]
         out["p99_query_ms"] = srv10[0]["p99_ms"] if srv10 else None
+        out["plain_512"] = plain_latency_leg(dev)
         out["training"] = training_leg(dev)
         out["large_sweep"] = large_sweep_leg(dev)
         # the CPU oracle on the host cores (bounded sample)

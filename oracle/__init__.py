@@ -53,6 +53,11 @@ def lib():
         _lib.orc_mlp_loss_grad.argtypes = [P, P, i64, P, ctypes.c_int, P, P, P, P]
         _lib.orc_adam_step.argtypes = [P, P, P, P, i64, dbl, dbl, dbl, dbl, i64, P]
         _lib.orc_num_threads.restype = ctypes.c_int
+        _lib.orc_select_topn.argtypes = [P, P, i64, ctypes.c_int, P, P]
+        _lib.orc_variant_count.restype = i64
+        _lib.orc_variant_count.argtypes = [i64]
+        _lib.orc_enumerate_variants.restype = i64
+        _lib.orc_enumerate_variants.argtypes = [P, i64, P, P]
     return _lib
 
 
@@ -120,6 +125,41 @@ def select_best(y, offsets):
     score = np.empty(K, dtype=np.float64)
     lib().orc_select_best(_p(y), _p(off), K, _p(best), _p(score))
     return best, score
+
+
+def select_topn(y, offsets, N: int):
+    """Top N per kernel (Fig. 2): best [K][N] local indices, score [K][N]; -1 / +inf padding."""
+    y = _c(y, np.float64)
+    off = _c(offsets, np.int64)
+    K = len(off) - 1
+    best = np.empty((K, N), dtype=np.int32)
+    score = np.empty((K, N), dtype=np.float64)
+    lib().orc_select_topn(_p(y), _p(off), K, int(N), _p(best), _p(score))
+    return best, score
+
+
+def variant_count(depth: int) -> int:
+    """Variants generated for a loop nest of `depth` collapsible loops (Table 1)."""
+    return int(lib().orc_variant_count(int(depth)))
+
+
+def enumerate_variants(kernels):
+    """Every variant of every kernel (Sec. 4.1.3): (variants [n][16] int64, seg_off [K+1])."""
+    k = _c(kernels, np.int64).reshape(-1, 16)
+    total = sum(variant_count(d) for d in k[:, 0])
+    out = np.empty((total, 16), dtype=np.int64)
+    off = np.empty(len(k) + 1, dtype=np.int64)
+    n = lib().orc_enumerate_variants(_p(k), len(k), _p(out), _p(off))
+    assert n == total
+    return out, off
+
+
+def rank_topn(desc, offsets, widths, params, mu, sigma, N: int):
+    """Whole path with top-N selection: (best [K][N], score [K][N], y)."""
+    feat, status = extract_features(desc, widths[0])
+    y = mlp_forward(feat, widths, params, mu, sigma, status)
+    best, score = select_topn(y, offsets, N)
+    return best, score, y
 
 
 def loss_grad(feat, labels, widths, params, mu, sigma):

@@ -347,6 +347,90 @@ void orc_select_best(const double* y, const int64_t* off, int64_t n_kernels,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Top N per kernel (Fig. 2: "sort codes based on cost and select top N").    */
+/* best[k*N + t] = local index of the t-th smallest finite score of kernel k */
+/* (ties to the lower local index), score[k*N + t] its value; -1 / +inf     */
+/* where the kernel has fewer than t+1 finite scores.  Written as N passes   */
+/* of "smallest (score, index) pair after the previous one".                 */
+/* ------------------------------------------------------------------------ */
+void orc_select_topn(const double* y, const int64_t* off, int64_t n_kernels, int N,
+                     int32_t* best, double* score)
+{
+    for (int64_t k = 0; k < n_kernels; k++) {
+        double pv = -INFINITY;
+        int64_t pi = -1;
+        for (int t = 0; t < N; t++) {
+            int64_t bi = -1;
+            double bv = INFINITY;
+            for (int64_t r = off[k]; r < off[k + 1]; r++) {
+                const double v = y[r];
+                const int64_t i = r - off[k];
+                if (!(v < INFINITY)) continue;                    /* skips +inf and NaN */
+                if (!(v > pv || (v == pv && i > pi))) continue;   /* not after the previous pick */
+                if (bi < 0 || v < bv) { bi = i; bv = v; }
+            }
+            best[k * N + t] = (int32_t)bi;
+            score[k * N + t] = bi < 0 ? INFINITY : bv;
+            if (bi >= 0) { pv = bv; pi = bi; }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Variant generation (Sec. 4.1.3, Table 1).  A kernel whose loop nest has   */
+/* NUM = depth collapsible for loops (1..4) gets one variant for every       */
+/* combination of                                                            */
+/*   x    the loop of the 'parallel for' directive, 0 <= x < NUM;           */
+/*   dc   the collapse of 'teams distribute': none (0) when x = 0, where the */
+/*        two directives are combined, else 1..x;                            */
+/*   pc   the collapse of 'parallel for', 1..NUM-x;                          */
+/*   the schedule (static, dynamic, guided = 0, 1, 2) and the data transfer */
+/*   mode (0, 1);                                                            */
+/* emitted with x outermost and the data mode innermost (the library's      */
+/* canonical order).  A variant copies the kernel's loop nest and work       */
+/* fields (descriptor fields 0..10) and sets fields 11..15 = x, dc, pc,      */
+/* schedule, data mode.                                                      */
+/* ------------------------------------------------------------------------ */
+int64_t orc_variant_count(int64_t depth)
+{
+    if (depth < 1 || depth > 4) return 0;
+    int64_t combos = 0;
+    for (int64_t x = 0; x < depth; x++) combos += (x == 0 ? 1 : x) * (depth - x);
+    return combos * 3 * 2;
+}
+
+/* kernels[K][16] -> variants[n][16] (n = sum of the counts), seg_off[K+1]. */
+int64_t orc_enumerate_variants(const int64_t* kernels, int64_t n_kernels, int64_t* out, int64_t* seg_off)
+{
+    int64_t n = 0;
+    seg_off[0] = 0;
+    for (int64_t k = 0; k < n_kernels; k++) {
+        const int64_t* kd = kernels + 16 * k;
+        const int64_t depth = kd[0];
+        if (depth >= 1 && depth <= 4) {
+            for (int64_t x = 0; x < depth; x++) {
+                const int64_t dc_lo = x == 0 ? 0 : 1, dc_hi = x;
+                for (int64_t dc = dc_lo; dc <= dc_hi; dc++)
+                    for (int64_t pc = 1; pc <= depth - x; pc++)
+                        for (int64_t sched = 0; sched < 3; sched++)
+                            for (int64_t dm = 0; dm < 2; dm++) {
+                                int64_t* v = out + 16 * n;
+                                memcpy(v, kd, 11 * sizeof(int64_t));
+                                v[11] = x;
+                                v[12] = dc;
+                                v[13] = pc;
+                                v[14] = sched;
+                                v[15] = dm;
+                                n++;
+                            }
+            }
+        }
+        seg_off[k + 1] = n;
+    }
+    return n;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Training: loss = 0.5 * mean_r (y_r - t_r)^2 over the n rows (MSE on ln    */
 /* runtime), its FP64 gradient with respect to every parameter (same layout  */
 /* as params), and one Adam step (Kingma & Ba 2015) with decoupled weight     */

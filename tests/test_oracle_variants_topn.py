@@ -1,0 +1,105 @@
+"""Oracle pins for variant generation (Sec. 4.1.3, Table 1) and top-N
+selection (Fig. 2, "sort codes based on cost and select top N").
+
+Variant generation is pinned by the counts the paper prints (Table 1), by a
+brute-force filter over every parameter tuple through the oracle's own
+descriptor validation (the ranges of Sec. 4.1.3), and by the field layout.
+Top-N is pinned by a sort-based reference, the N = 1 case (the argmin), ties,
+padding and permutation invariance."""
+import os
+
+import numpy as np
+
+import oracle
+from paper_2301_03636_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1_variant_counts.txt")
+
+
+def _table1():
+    rows = [l.split() for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
+    return {int(a): int(b) for a, b in rows}
+
+
+def _kernels(n, seed):
+    """Loop nests: the kernel fields of valid descriptors (variant fields are overwritten)."""
+    return W.make_descriptors(n, seed, max_depth=4)
+
+
+def test_counts_match_table1():
+    for depth, count in _table1().items():
+        assert oracle.variant_count(depth) == count
+    assert oracle.variant_count(0) == 0 and oracle.variant_count(5) == 0
+
+
+def test_enumeration_equals_brute_force_filter():
+    """Every 5-tuple of variant parameters that the validation ranges accept,
+    and nothing else, once each."""
+    for depth in (1, 2, 3, 4):
+        k = _kernels(64, 100 + depth)
+        k = k[k[:, 0] == depth][:1]
+        if len(k) == 0:   # force the depth (trip counts of the unused loops are 1)
+            k = _kernels(1, 100 + depth)
+            k[0, 0] = depth
+            k[0, 1:5] = [4 if i < depth else 1 for i in range(4)]
+        v, off = oracle.enumerate_variants(k)
+        assert off.tolist() == [0, oracle.variant_count(depth)]
+        got = {tuple(r[11:16]) for r in v}
+        assert len(got) == len(v)                       # no duplicates
+        brute = set()
+        for x in range(5):
+            for dc in range(6):
+                for pc in range(6):
+                    for sched in range(4):
+                        for dm in range(3):
+                            d = k[0].copy()
+                            d[11:16] = [x, dc, pc, sched, dm]
+                            if oracle.validate(d[None, :])[0] == 0:
+                                brute.add((x, dc, pc, sched, dm))
+        assert got == brute
+
+
+def test_enumeration_layout_and_order():
+    k = _kernels(40, 7)
+    k[3, 0] = 0   # an invalid depth: no variants
+    v, off = oracle.enumerate_variants(k)
+    counts = np.diff(off)
+    assert counts[3] == 0
+    for i in range(len(k)):
+        seg = v[off[i]:off[i + 1]]
+        assert counts[i] == oracle.variant_count(k[i, 0])
+        assert (seg[:, :11] == k[i, :11]).all()        # the loop nest and work fields are copied
+        keys = [tuple(r[11:16]) for r in seg]
+        assert keys == sorted(keys) and len(set(keys)) == len(keys)   # canonical order, strictly increasing
+    assert (oracle.validate(v) == 0).all()
+
+
+def test_topn_equals_sort_reference():
+    rng = np.random.default_rng(3)
+    off = W.make_segments(50, 1, 30, seed=3)
+    y = rng.normal(size=off[-1]).round(1)            # many exact ties
+    y[rng.choice(len(y), 20, replace=False)] = np.inf
+    for N in (1, 3, 10, 40):
+        best, score = oracle.select_topn(y, off, N)
+        for k in range(len(off) - 1):
+            seg = y[off[k]:off[k + 1]]
+            idx = [i for i in np.lexsort((np.arange(len(seg)), seg)) if np.isfinite(seg[i])][:N]
+            assert best[k, :len(idx)].tolist() == idx
+            assert (best[k, len(idx):] == -1).all() and np.isinf(score[k, len(idx):]).all()
+            assert np.array_equal(score[k, :len(idx)], seg[idx])
+
+
+def test_topn_one_is_the_argmin_and_permutation_invariant():
+    rng = np.random.default_rng(4)
+    off = W.make_segments(30, 2, 20, seed=4)
+    y = rng.normal(size=off[-1])
+    b1, s1 = oracle.select_topn(y, off, 1)
+    b, s = oracle.select_best(y, off)
+    assert np.array_equal(b1[:, 0], b) and np.array_equal(s1[:, 0], s)
+    # permuting rows inside a kernel permutes the indices but keeps the selected values
+    yp = y.copy()
+    for k in range(len(off) - 1):
+        yp[off[k]:off[k + 1]] = rng.permutation(y[off[k]:off[k + 1]])
+    _, sa = oracle.select_topn(y, off, 5)
+    _, sb = oracle.select_topn(yp, off, 5)
+    assert np.array_equal(sa, sb)
