@@ -187,6 +187,25 @@ advisor_status advisor_score_variants_fp64(advisor_model_t m, const int32_t* d_f
                                            const uint8_t* d_row_status, int64_t n_rows,
                                            double* d_scores, cudaStream_t stream);
 
+/* Variant generation (Sec. 4.1.3; the counts are Table 1): every offload
+ * variant of each kernel's loop nest.  A kernel is given as a descriptor
+ * whose loop-nest and work fields (depth .. threads) are used and whose
+ * variant fields are ignored.  For NUM = depth collapsible loops the variants
+ * are all combinations of x = the loop of 'parallel for' (0..NUM-1), the
+ * 'teams distribute' collapse (0 = combined when x = 0, else 1..x), the
+ * 'parallel for' collapse (1..NUM-x), the schedule (0..2) and the data mode
+ * (0..1), in that order with the data mode fastest: 6, 18, 42, 84 variants
+ * for NUM = 1..4, none for any other depth.  Output: d_variants (device,
+ * capacity rows; rows beyond the capacity are not written), d_seg_off
+ * [n_kernels + 1] (device int64: kernel k owns rows d_seg_off[k] ..
+ * d_seg_off[k+1]-1, the layout advisor_rank takes) and d_total (device
+ * int64, nullable: the full count, which may exceed the capacity).
+ * Asynchronous on `stream`. */
+int64_t advisor_variant_count(int64_t depth);
+advisor_status advisor_enumerate_variants(const advisor_variant_desc* d_kernels, int64_t n_kernels,
+                                          advisor_variant_desc* d_variants, int64_t capacity,
+                                          int64_t* d_seg_off, int64_t* d_total, cudaStream_t stream);
+
 /* a6-a7: per-kernel selection (Fig. 2 "sort codes based on cost and select").
  * Kernel k owns rows d_seg_off[k] .. d_seg_off[k+1]-1 (int64, non-decreasing,
  * d_seg_off[0] >= 0, last <= n_rows).  d_best_local[k] = index of the selected
@@ -281,6 +300,23 @@ advisor_status advisor_plan_info(advisor_plan_t p, advisor_launch_config* cfg, f
 
 /* Release the graph (NULL is a no-op). */
 advisor_status advisor_plan_destroy(advisor_plan_t p);
+
+/* Top N per kernel (Fig. 2: "sort codes based on cost and select top N"):
+ * advisor_rank with d_best_local / d_best_score of shape [n_kernels][top_n]
+ * (row-major): entry t of kernel k is the local index and score of the
+ * kernel's (t+1)-th best variant, ties to the lower index; -1 / +inf where the
+ * kernel has fewer finite scores.  With eps_scores >= 0 the list equals the
+ * FP64 ordering whenever |score - fp64| <= eps_scores and |fp32 - fp64| <=
+ * eps_fp32: rows within 2*eps_scores of the N-th score are re-scored in FP32,
+ * and those within 2*eps_fp32 of another one near the N-th FP32 value in
+ * FP64; d_best_score then holds the deciding value of each entry.
+ * 1 <= top_n <= ADVISOR_MAX_TOP_N. */
+#define ADVISOR_MAX_TOP_N 128
+advisor_status advisor_rank_topn(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                                 const int64_t* d_seg_off, int64_t n_kernels, int32_t top_n,
+                                 advisor_precision precision, float eps_scores, float eps_fp32,
+                                 int32_t* d_best_local, double* d_best_score, float* d_scores,
+                                 uint8_t* d_row_status, cudaStream_t stream);
 
 /* a8: one training step (Sec. 3 training mode; Sec. 5 Exp. 3): forward,
  * loss = 0.5 * mean (y - label)^2 over the n_rows rows (labels: ln runtime),

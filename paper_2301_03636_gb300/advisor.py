@@ -76,6 +76,9 @@ def lib():
         "advisor_model_get_launch_config": (st, [P, P]),
         "advisor_get_rescore_counts": (st, [P, P, P]),
         "advisor_model_calibrate_fp8": (st, [P, P, i64, P]),
+        "advisor_variant_count": (i64, [i64]),
+        "advisor_rank_topn": (st, [P, P, i64, P, i64, i32, st, f32, f32, P, P, P, P, P]),
+        "advisor_enumerate_variants": (st, [P, i64, P, i64, P, P, P]),
         "advisor_model_set_launch_config": (st, [P, P]),
         "advisor_plan_rank": (st, [P, P, i64, P, i64, st, f32, f32, P, P, P, P, i32, P, ctypes.POINTER(P)]),
         "advisor_plan_launch": (st, [P, P]),
@@ -149,6 +152,24 @@ def advisor_extract_features(desc: torch.Tensor, n_features: int, stream=None):
     _check(lib().advisor_extract_features(_ptr(desc), n, n_features, _ptr(feat), _ptr(status), _stream(stream)),
            "advisor_extract_features")
     return feat, status
+
+
+def advisor_variant_count(depth: int) -> int:
+    return int(lib().advisor_variant_count(int(depth)))
+
+
+def advisor_enumerate_variants(kernels: torch.Tensor, stream=None):
+    """Every offload variant of each kernel's loop nest (Sec. 4.1.3): kernels
+    [K][16] int64 on the device -> (variants [n][16], seg_off [K+1])."""
+    K = kernels.shape[0]
+    cap = 84 * K   # the largest count per kernel (Table 1)
+    out = torch.empty((max(cap, 1), 16), dtype=torch.int64, device=kernels.device)
+    off = torch.empty(K + 1, dtype=torch.int64, device=kernels.device)
+    total = torch.empty(1, dtype=torch.int64, device=kernels.device)
+    _check(lib().advisor_enumerate_variants(_ptr(kernels), K, _ptr(out), cap, _ptr(off), _ptr(total),
+                                            _stream(stream)), "advisor_enumerate_variants")
+    n = int(total.item())
+    return out[:n], off
 
 
 def advisor_fit_standardizer(feat: torch.Tensor, status: torch.Tensor | None = None, stream=None):
@@ -280,6 +301,17 @@ class Model:
     def plan_rank(self, desc, offsets, precision="bf16", eps=-1.0, eps32=0.0, autotune=False, stream=None):
         """A Plan replaying rank() on these buffers (refill desc / offsets in place between launches)."""
         return Plan(self, desc, offsets, precision, eps, eps32, autotune, stream)
+
+    def rank_topn(self, desc, offsets, top_n, precision="bf16", eps=-1.0, eps32=0.0, scores=None, status=None,
+                  stream=None):
+        """The top_n best variants of every kernel: (best [K][top_n] int32, score [K][top_n] float64)."""
+        K = offsets.shape[0] - 1
+        best = torch.empty((K, top_n), dtype=torch.int32, device=self.device)
+        best_score = torch.empty((K, top_n), dtype=torch.float64, device=self.device)
+        _check(lib().advisor_rank_topn(self.handle, _ptr(desc), desc.shape[0], _ptr(offsets), K, int(top_n),
+                                       _prec(precision), float(eps), float(eps32), _ptr(best), _ptr(best_score),
+                                       _ptr(scores), _ptr(status), _stream(stream)), "advisor_rank_topn")
+        return best, best_score
 
     def train_step(self, feat, labels, precision="fp32", lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
                    weight_decay=0.0, loss=None, stream=None):

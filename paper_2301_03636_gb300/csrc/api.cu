@@ -21,7 +21,7 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 struct WsLayout {
     size_t x_img, h_img[2], partial, feat32, status, scores, counters, seg_state, seg_start, seg_cnt;
-    size_t cand_rows, y32, cand2_rows, y64;
+    size_t cand_rows, y32, cand2_rows, y64, pos64, seg_thr;
     size_t train;   // start of the training region
     size_t bytes;
 };
@@ -78,6 +78,8 @@ WsLayout ws_layout(const adv::ModelLayout& L, int64_t R, int64_t K, adv::TrainLa
     w.y32 = take((size_t)R * 4);
     w.cand2_rows = take((size_t)R * 8);
     w.y64 = take((size_t)R * 8);
+    w.pos64 = take((size_t)R * 4);
+    w.seg_thr = take((size_t)K * 8);
     w.train = o;
     const size_t tb = adv::train_layout(L, R, T);
     o = align256(o + tb);
@@ -282,6 +284,22 @@ const char* advisor_status_string(advisor_status s) {
 }
 
 int64_t advisor_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int64_t advisor_variant_count(int64_t depth) { return adv::variant_count(depth); }
+
+advisor_status advisor_enumerate_variants(const advisor_variant_desc* d_kernels, int64_t n_kernels,
+                                          advisor_variant_desc* d_variants, int64_t capacity, int64_t* d_seg_off,
+                                          int64_t* d_total, cudaStream_t stream) {
+    if (n_kernels < 0 || capacity < 0 || !d_seg_off || (n_kernels > 0 && !d_kernels) ||
+        (capacity > 0 && !d_variants))
+        return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (!aligned(d_kernels, 16) || !aligned(d_variants, 16)) return ADVISOR_ERR_INVALID_ARGUMENT;
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return ADVISOR_ERR_CUDA;
+    return cuda_status(adv::launch_enumerate(d_kernels, n_kernels, d_variants, capacity, d_seg_off, d_total, sms,
+                                             stream));
+}
 
 advisor_status advisor_model_calibrate_fp8(advisor_model_t m, const int32_t* d_feat_q16, int64_t n_rows,
                                            cudaStream_t stream) {
@@ -536,6 +554,112 @@ advisor_status advisor_select_best(advisor_model_t m, const float* d_scores, int
                      d_best_score, stream);
 }
 
+}  // extern "C"
+
+namespace {
+
+// a1-a5 of the ranking calls: descriptors -> scores and row status; *rs
+// receives where the re-score tiers read the rows from (the FP32 path keeps
+// the int32 features, the tensor-core paths re-extract from the descriptors).
+advisor_status rank_scores(advisor_model* m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                           advisor_precision precision, float* scores, uint8_t* status, adv::RowSrc* rs,
+                           cudaStream_t stream) {
+    *rs = adv::RowSrc{nullptr, d_desc, nullptr, nullptr, 0, nullptr};
+    if (n_rows == 0) return ADVISOR_OK;
+    const adv::ModelLayout& L = m->L;
+    adv::ExtractArgs a{};
+    a.desc = d_desc;
+    a.n_rows = n_rows;
+    a.status = status;
+    a.sa = reinterpret_cast<const float*>(m->P + L.p_stdz_a);
+    a.sc = reinterpret_cast<const float*>(m->P + L.p_stdz_c);
+    cudaError_t e;
+    if (precision == ADVISOR_FP32) {
+        a.n_rows_padded = n_rows;
+        a.feat = reinterpret_cast<int32_t*>(m->WS + m->W.feat32);
+        e = adv::launch_extract(a, L.F, 0, stream, m->cfg.extract_block);
+        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+        adv::RowSrc src{a.feat, nullptr, nullptr, nullptr, n_rows, status};
+        e = adv::launch_mlp_fp32(mlp_desc(m), src, scores, m->num_sms, false, stream);
+        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+        *rs = adv::RowSrc{a.feat, nullptr, nullptr, nullptr, 0, nullptr};
+        return ADVISOR_OK;
+    }
+    if (precision == ADVISOR_FP8_E4M3) {
+        if (!wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
+        if (!m->fp8_calibrated) return ADVISOR_ERR_INVALID_ARGUMENT;
+    } else if (precision != ADVISOR_BF16 && precision != ADVISOR_FP16) {
+        return ADVISOR_ERR_UNSUPPORTED;
+    }
+    const bool fused = tc_supported(m) && precision != ADVISOR_FP8_E4M3;
+    if (!fused && !wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
+    const int fi = precision == ADVISOR_BF16 ? 0 : (precision == ADVISOR_FP16 ? 1 : 2);
+    a.n_rows_padded = ((n_rows + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
+    a.x_img = m->WS + m->W.x_img;
+    a.nslab = fi == 2 ? L.nslab8[0] : L.nslab[0];
+    a.x8_scale = reinterpret_cast<const float*>(m->P + L.p_fp8) + ADV_FP8_X_SCALE;
+    e = adv::launch_extract(a, L.F, fi + 1, stream, m->cfg.extract_block);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    e = fused ? launch_tc_profiled(m, tc_args(m, a.x_img, n_rows, status, scores, fi), stream)
+              : launch_wide(m, a.x_img, n_rows, status, scores, fi, stream);
+    return e == cudaSuccess ? ADVISOR_OK : ADVISOR_ERR_CUDA;
+}
+
+// Top-N selection with the tiered re-score (select.cu, topn_*).
+advisor_status do_select_topn(advisor_model* m, const float* scores, int64_t n_rows, const int64_t* off, int64_t K,
+                              int N, adv::RowSrc src, bool rescore, float eps, float eps32, int32_t* best,
+                              double* best_score, cudaStream_t s) {
+    adv::SelectArgs a{};
+    a.scores = scores;
+    a.n_rows = n_rows;
+    a.off = off;
+    a.n_kernels = K;
+    a.best = best;
+    a.best_score = best_score;
+    a.eps = rescore ? eps : -1.f;
+    a.eps32 = eps32;
+    a.counters = reinterpret_cast<int*>(m->WS + m->W.counters);
+    a.seg_state = reinterpret_cast<int*>(m->WS + m->W.seg_state);
+    a.seg_start = reinterpret_cast<int*>(m->WS + m->W.seg_start);
+    a.seg_cnt = reinterpret_cast<int*>(m->WS + m->W.seg_cnt);
+    a.cand_rows = reinterpret_cast<int64_t*>(m->WS + m->W.cand_rows);
+    a.y32 = reinterpret_cast<float*>(m->WS + m->W.y32);
+    a.cand2_rows = reinterpret_cast<int64_t*>(m->WS + m->W.cand2_rows);
+    a.y64 = reinterpret_cast<double*>(m->WS + m->W.y64);
+    a.status_word = status_word(m);
+    a.top_n = N;
+    a.pos64 = reinterpret_cast<int*>(m->WS + m->W.pos64);
+    a.seg_thr = reinterpret_cast<double*>(m->WS + m->W.seg_thr);
+    cudaError_t e;
+    if (rescore) {
+        e = cudaMemsetAsync(a.counters, 0, 2 * sizeof(int), s);
+        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    }
+    e = adv::launch_topn_tier1(a, s, m->cfg.select_block);
+    if (e != cudaSuccess || !rescore) return cuda_status(e);
+    const adv::MlpDesc md = mlp_desc(m);
+    adv::RowSrc r1 = src;
+    r1.rows = a.cand_rows;
+    r1.count_dev = &a.counters[0];
+    r1.count = 0;
+    e = adv::launch_mlp_fp32(md, r1, a.y32, m->num_sms, true, s, a.status_word, m->cfg.list_blocks_per_sm,
+                             m->cfg.list_chunk_kb);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    e = adv::launch_topn_tier2(a, s, m->cfg.select_block);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    adv::RowSrc r2 = src;
+    r2.rows = a.cand2_rows;
+    r2.count_dev = &a.counters[1];
+    r2.count = 0;
+    e = adv::launch_mlp_fp64(md, r2, a.y64, m->num_sms, s);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    return cuda_status(adv::launch_topn_final(a, s, m->cfg.select_block));
+}
+
+}  // namespace
+
+extern "C" {
+
 advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
                             const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
                             float eps_scores, float eps_fp32, int32_t* d_best_local, double* d_best_score,
@@ -550,49 +674,34 @@ advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_des
     if (rescore && eps_fp32 < 0.f) return ADVISOR_ERR_INVALID_ARGUMENT;
     float* scores = d_scores ? d_scores : reinterpret_cast<float*>(m->WS + m->W.scores);
     uint8_t* status = d_row_status ? d_row_status : m->WS + m->W.status;
-    const adv::ModelLayout& L = m->L;
-    if (n_rows > 0) {
-        adv::ExtractArgs a{};
-        a.desc = d_desc;
-        a.n_rows = n_rows;
-        a.status = status;
-        a.sa = reinterpret_cast<const float*>(m->P + L.p_stdz_a);
-        a.sc = reinterpret_cast<const float*>(m->P + L.p_stdz_c);
-        cudaError_t e;
-        if (precision == ADVISOR_FP32) {
-            a.n_rows_padded = n_rows;
-            a.feat = reinterpret_cast<int32_t*>(m->WS + m->W.feat32);
-            e = adv::launch_extract(a, L.F, 0, stream, m->cfg.extract_block);
-            if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
-            adv::RowSrc src{a.feat, nullptr, nullptr, nullptr, n_rows, status};
-            e = adv::launch_mlp_fp32(mlp_desc(m), src, scores, m->num_sms, false, stream);
-            if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
-            adv::RowSrc rs{a.feat, nullptr, nullptr, nullptr, 0, nullptr};
-            return do_select(m, scores, n_rows, d_seg_off, n_kernels, rs, rescore, eps_scores, eps_fp32,
-                             d_best_local, d_best_score, stream);
-        }
-        if (precision == ADVISOR_FP8_E4M3) {
-            if (!wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
-            if (!m->fp8_calibrated) return ADVISOR_ERR_INVALID_ARGUMENT;
-        } else if (precision != ADVISOR_BF16 && precision != ADVISOR_FP16) {
-            return ADVISOR_ERR_UNSUPPORTED;
-        }
-        const bool fused = tc_supported(m) && precision != ADVISOR_FP8_E4M3;
-        if (!fused && !wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
-        const int fi = precision == ADVISOR_BF16 ? 0 : (precision == ADVISOR_FP16 ? 1 : 2);
-        a.n_rows_padded = ((n_rows + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
-        a.x_img = m->WS + m->W.x_img;
-        a.nslab = fi == 2 ? L.nslab8[0] : L.nslab[0];
-        a.x8_scale = reinterpret_cast<const float*>(m->P + L.p_fp8) + ADV_FP8_X_SCALE;
-        e = adv::launch_extract(a, L.F, fi + 1, stream, m->cfg.extract_block);
-        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
-        e = fused ? launch_tc_profiled(m, tc_args(m, a.x_img, n_rows, status, scores, fi), stream)
-                  : launch_wide(m, a.x_img, n_rows, status, scores, fi, stream);
-        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
-    }
-    adv::RowSrc rs{nullptr, d_desc, nullptr, nullptr, 0, nullptr};
+    adv::RowSrc rs{};
+    st = rank_scores(m, d_desc, n_rows, precision, scores, status, &rs, stream);
+    if (st != ADVISOR_OK) return st;
     return do_select(m, scores, n_rows, d_seg_off, n_kernels, rs, rescore && n_rows > 0, eps_scores, eps_fp32,
                      d_best_local, d_best_score, stream);
+}
+
+advisor_status advisor_rank_topn(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                                 const int64_t* d_seg_off, int64_t n_kernels, int32_t top_n,
+                                 advisor_precision precision, float eps_scores, float eps_fp32,
+                                 int32_t* d_best_local, double* d_best_score, float* d_scores,
+                                 uint8_t* d_row_status, cudaStream_t stream) {
+    if (!m || n_rows < 0 || n_kernels < 0 || !d_best_local || !d_best_score) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (top_n < 1 || top_n > ADVISOR_MAX_TOP_N) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (n_kernels == 0) return ADVISOR_OK;
+    if (!d_seg_off || (n_rows > 0 && (!d_desc || !aligned(d_desc, 16)))) return ADVISOR_ERR_INVALID_ARGUMENT;
+    advisor_status st = check_ready(m, n_rows);
+    if (st != ADVISOR_OK) return st;
+    if (n_kernels > m->max_kernels) return ADVISOR_ERR_OUT_OF_MEMORY;
+    const bool rescore = eps_scores >= 0.f;
+    if (rescore && eps_fp32 < 0.f) return ADVISOR_ERR_INVALID_ARGUMENT;
+    float* scores = d_scores ? d_scores : reinterpret_cast<float*>(m->WS + m->W.scores);
+    uint8_t* status = d_row_status ? d_row_status : m->WS + m->W.status;
+    adv::RowSrc rs{};
+    st = rank_scores(m, d_desc, n_rows, precision, scores, status, &rs, stream);
+    if (st != ADVISOR_OK) return st;
+    return do_select_topn(m, scores, n_rows, d_seg_off, n_kernels, top_n, rs, rescore && n_rows > 0, eps_scores,
+                          eps_fp32, d_best_local, d_best_score, stream);
 }
 
 // Training precision: 0 FP32 SIMT, 1 BF16 / 2 FP16 tensor-core GEMMs; -1 unsupported.

@@ -133,9 +133,21 @@ struct SelectArgs {
     int64_t* cand2_rows;
     double* y64;
     int* status_word;
+    // top-N selection
+    int top_n;                 // N (best / best_score are [n_kernels][N])
+    int* pos64;                // per FP32 candidate: its position in the FP64 list, or -1
+    double* seg_thr;           // per kernel: the FP32 window bound
 };
 cudaError_t launch_select_tier1(const SelectArgs& a, cudaStream_t s, int block = 256);
+cudaError_t launch_topn_tier1(const SelectArgs& a, cudaStream_t s, int block = 256);
+cudaError_t launch_topn_tier2(const SelectArgs& a, cudaStream_t s, int block = 256);
+cudaError_t launch_topn_final(const SelectArgs& a, cudaStream_t s, int block = 256);
 cudaError_t launch_select_tier2(const SelectArgs& a, cudaStream_t s, int block = 256);
 cudaError_t launch_select_final(const SelectArgs& a, cudaStream_t s, int block = 256);
+
+// Variant generation (enumerate.cu).
+int64_t variant_count(int64_t depth);
+cudaError_t launch_enumerate(const advisor_variant_desc* kernels, int64_t K, advisor_variant_desc* out,
+                             int64_t capacity, int64_t* seg_off, int64_t* total, int num_sms, cudaStream_t s);
 
 }  // namespace adv

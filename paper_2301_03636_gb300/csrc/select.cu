@@ -180,6 +180,199 @@ __global__ void __launch_bounds__(256) select_final_kernel(SelectArgs a) {
     }
 }
 
+// ---- top N per kernel (Fig. 2: "sort codes based on cost and select top N") ----
+//
+// Exact against the FP64 ordering under the same error bounds as the argmin:
+//   tier 1: t = the N-th smallest (score, row) of the kernel; every finite
+//           row with score <= t + 2 eps is a candidate (no other row can be in
+//           the FP64 top N); candidates are re-scored in FP32;
+//   tier 2: t32 = the N-th smallest (FP32, row) among the candidates; those
+//           with FP32 <= t32 + 2 eps32 that have another such candidate within
+//           2 eps32 are re-scored in FP64 (only they can be ordered wrongly);
+//   final:  the N smallest (key, row) among the candidates with FP32 <=
+//           t32 + 2 eps32, key = the FP64 value where there is one, else the
+//           FP32 value: two keys of different kinds belong to rows more than
+//           2 eps32 apart in FP32, whose FP32 and FP64 orders agree.
+// Without re-score (eps < 0) tier 1 writes the N smallest scores directly.
+
+// The smallest finite (v, r) pair after (pv, pr) over rows lo + lane, +32, ...
+__device__ __forceinline__ void next_after(const float* __restrict__ v, int64_t lo, int64_t hi, float pv, int64_t pr,
+                                           float& bv, int64_t& br) {
+    const int lane = threadIdx.x & 31;
+    bv = INFINITY;
+    br = -1;
+    for (int64_t r = lo + lane; r < hi; r += 32) {
+        const float x = v[r];
+        if (finite_score(x) && (x > pv || (x == pv && r > pr))) lex_min(bv, br, x, r);
+    }
+    warp_lex_min(bv, br);
+}
+
+__global__ void __launch_bounds__(256) topn_tier1_kernel(SelectArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int N = a.top_n;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < a.n_kernels; k += nwarps) {
+        const int64_t lo = a.off[k], hi = a.off[k + 1];
+        if (lo < 0 || hi < lo || hi > a.n_rows) {
+            if (lane == 0) {
+                atomicOr(a.status_word, ADV_DEV_BAD_SEGMENTS);
+                for (int t = 0; t < N; ++t) {
+                    a.best[k * N + t] = -1;
+                    a.best_score[k * N + t] = INFINITY;
+                }
+                a.seg_state[k] = 0;
+            }
+            continue;
+        }
+        float pv = -INFINITY;
+        int64_t pr = -1;
+        int found = 0;
+        for (int t = 0; t < N; ++t) {
+            float bv;
+            int64_t br;
+            next_after(a.scores, lo, hi, pv, pr, bv, br);
+            if (br < 0) break;
+            if (lane == 0 && a.eps < 0.f) {
+                a.best[k * N + t] = (int32_t)(br - lo);
+                a.best_score[k * N + t] = (double)bv;
+            }
+            pv = bv;
+            pr = br;
+            ++found;
+        }
+        if (a.eps < 0.f || found == 0) {
+            if (lane == 0) {
+                for (int t = found; t < N; ++t) {
+                    a.best[k * N + t] = -1;
+                    a.best_score[k * N + t] = INFINITY;
+                }
+                a.seg_state[k] = 0;
+            }
+            continue;
+        }
+        const double thr = (double)pv + 2.0 * (double)a.eps;
+        int cnt = 0;
+        for (int64_t r0 = lo; r0 < hi; r0 += 32) {
+            const int64_t r = r0 + lane;
+            const bool take = r < hi && finite_score(a.scores[r]) && (double)a.scores[r] <= thr;
+            cnt += __popc(__ballot_sync(0xffffffffu, take));
+        }
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&a.counters[0], cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        int done = 0;
+        for (int64_t r0 = lo; r0 < hi; r0 += 32) {
+            const int64_t r = r0 + lane;
+            const bool take = r < hi && finite_score(a.scores[r]) && (double)a.scores[r] <= thr;
+            done += append_ordered(take, r, a.cand_rows, base, done);
+        }
+        if (lane == 0) {
+            a.seg_start[k] = base;
+            a.seg_cnt[k] = cnt;
+            a.seg_state[k] = 1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) topn_tier2_kernel(SelectArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int N = a.top_n;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < a.n_kernels; k += nwarps) {
+        if (a.seg_state[k] != 1) continue;
+        const int start = a.seg_start[k], cnt = a.seg_cnt[k];
+        const float* y = a.y32 + start;
+        // the N-th smallest (FP32, position) among the candidates (positions follow row order)
+        float pv = -INFINITY;
+        int64_t pr = -1;
+        for (int t = 0; t < N; ++t) {
+            float bv;
+            int64_t br;
+            next_after(y, 0, cnt, pv, pr, bv, br);
+            if (br < 0) break;
+            pv = bv;
+            pr = br;
+        }
+        const double thr = pr >= 0 ? (double)pv + 2.0 * (double)a.eps32 : -(double)INFINITY;
+        const double win = 2.0 * (double)a.eps32;
+        int cnt2 = 0;
+        for (int i0 = 0; i0 < cnt; i0 += 32) {
+            const int i = i0 + lane;
+            bool take = false;
+            if (i < cnt && finite_score(y[i]) && (double)y[i] <= thr) {
+                for (int j = 0; j < cnt && !take; ++j)
+                    take = j != i && finite_score(y[j]) && (double)y[j] <= thr &&
+                           fabs((double)y[j] - (double)y[i]) <= win;
+            }
+            cnt2 += __popc(__ballot_sync(0xffffffffu, take));
+        }
+        int base = 0;
+        if (lane == 0 && cnt2 > 0) base = atomicAdd(&a.counters[1], cnt2);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        int done = 0;
+        for (int i0 = 0; i0 < cnt; i0 += 32) {
+            const int i = i0 + lane;
+            bool take = false;
+            if (i < cnt && finite_score(y[i]) && (double)y[i] <= thr) {
+                for (int j = 0; j < cnt && !take; ++j)
+                    take = j != i && finite_score(y[j]) && (double)y[j] <= thr &&
+                           fabs((double)y[j] - (double)y[i]) <= win;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, take);
+            if (i < cnt) a.pos64[start + i] = take ? base + done + __popc(m & ((1u << lane) - 1u)) : -1;
+            if (take) a.cand2_rows[base + done + __popc(m & ((1u << lane) - 1u))] = a.cand_rows[start + i];
+            done += __popc(m);
+        }
+        if (lane == 0) {
+            a.seg_thr[k] = thr;
+            a.seg_state[k] = 2;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) topn_final_kernel(SelectArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int N = a.top_n;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < a.n_kernels; k += nwarps) {
+        if (a.seg_state[k] != 2) continue;
+        const int64_t lo = a.off[k];
+        const int start = a.seg_start[k], cnt = a.seg_cnt[k];
+        const double thr = a.seg_thr[k];
+        double pv = -(double)INFINITY;
+        int64_t pr = -1;
+        int t = 0;
+        for (; t < N; ++t) {
+            double bv = INFINITY;
+            int64_t br = -1;
+            for (int i = lane; i < cnt; i += 32) {
+                const float y = a.y32[start + i];
+                if (!finite_score(y) || (double)y > thr) continue;
+                const int p = a.pos64[start + i];
+                const double key = p >= 0 ? a.y64[p] : (double)y;
+                const int64_t r = a.cand_rows[start + i];
+                if (key < (double)INFINITY && (key > pv || (key == pv && r > pr))) lex_min_d(bv, br, key, r);
+            }
+            warp_lex_min_d(bv, br);
+            if (br < 0) break;
+            if (lane == 0) {
+                a.best[k * N + t] = (int32_t)(br - lo);
+                a.best_score[k * N + t] = bv;
+            }
+            pv = bv;
+            pr = br;
+        }
+        if (lane == 0) {
+            for (; t < N; ++t) {
+                a.best[k * N + t] = -1;
+                a.best_score[k * N + t] = INFINITY;
+            }
+            a.seg_state[k] = 0;
+        }
+    }
+}
+
 // One warp per segment; the kernels stride over segments, so any grid and
 // any whole number of warps per block covers them.
 static int select_grid(int64_t n_kernels, int block) {
@@ -205,6 +398,25 @@ cudaError_t launch_select_tier2(const SelectArgs& a, cudaStream_t s, int block) 
 cudaError_t launch_select_final(const SelectArgs& a, cudaStream_t s, int block) {
     if (!select_block_ok(block)) return cudaErrorInvalidValue;
     select_final_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_topn_tier1(const SelectArgs& a, cudaStream_t s, int block) {
+    if (!select_block_ok(block)) return cudaErrorInvalidValue;
+    topn_tier1_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+cudaError_t launch_topn_tier2(const SelectArgs& a, cudaStream_t s, int block) {
+    if (!select_block_ok(block)) return cudaErrorInvalidValue;
+    topn_tier2_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+cudaError_t launch_topn_final(const SelectArgs& a, cudaStream_t s, int block) {
+    if (!select_block_ok(block)) return cudaErrorInvalidValue;
+    topn_final_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
     adv_count_launch(1);
     return cudaGetLastError();
 }

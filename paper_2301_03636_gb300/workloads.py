@@ -208,6 +208,36 @@ LARGE_SWEEP = Workload("sweep_1m_f128_1024x3", (128, 1024, 1024, 1024, 1), 65536
 WORKLOADS = {w.name: w for w in (PLAIN_FP32_512, BATCHED_4096, SERVING, TRAINING, LARGE_SWEEP)}
 
 
+def make_dslash_kernels(n_kernels: int, seed: int) -> np.ndarray:
+    """Loop nests shaped like the paper's flagship kernel, the Wilson Dslash
+    operator (Sec. 5, four nested site loops; Fig. plot_variants_summit runs
+    L_X,L_Y,L_Z,L_T = 32,32,32,16): depth 4, trip counts a lattice L^3 x T
+    drawn from a few sizes, 1,320 flops and 1,440 bytes per site (single
+    precision: 8 gauge links x 72 B + 9 spinors x 96 B), the gauge field and
+    source spinor mapped to the device (384 B per site) and the result spinor
+    back (96 B per site), teams uniform in 1..1024, threads a multiple of 32
+    in 32..1024.  Variant fields are left at their first valid value (the
+    enumerator fills them).  Returns [n_kernels][16] int64."""
+    rng = np.random.Generator(np.random.PCG64(seed + 4049))
+    lattices = np.array([[8, 8, 8, 16], [16, 16, 16, 16], [16, 16, 16, 32], [24, 24, 24, 48], [32, 32, 32, 16],
+                         [32, 32, 32, 64]], dtype=np.int64)
+    d = np.zeros((n_kernels, DESC_FIELDS), dtype=np.int64)
+    lat = lattices[rng.integers(0, len(lattices), size=n_kernels)]
+    sites = lat.prod(axis=1)
+    d[:, 0] = 4
+    d[:, 1:5] = lat
+    d[:, 5] = 1320
+    d[:, 6] = 1440
+    d[:, 7] = sites * 384
+    d[:, 8] = sites * 96
+    d[:, 9] = rng.integers(1, 1025, size=n_kernels)
+    d[:, 10] = 32 * rng.integers(1, 33, size=n_kernels)
+    d[:, 11] = 0   # combined 'teams distribute parallel for'
+    d[:, 12] = 0
+    d[:, 13] = 1
+    return d
+
+
 def calibration_descriptors(n: int = 65536) -> np.ndarray:
     """The fixed sample the z-score standardiser is fitted on (Sec. 5, Experiment 3)."""
     return make_descriptors(n, CALIBRATION_SEED)

@@ -1,0 +1,65 @@
+"""Variant generation on the GPU (Sec. 4.1.3, Table 1) against the oracle's
+enumeration (bit-exact, same order), the capacity limit, and the whole
+advisor path on Dslash-shaped kernels (Sec. 5's flagship kernel: four nested
+loops, 84 variants each): enumerate on the GPU, rank, compare the selected
+variant of every kernel with the oracle's."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2301_03636_gb300 import advisor
+from paper_2301_03636_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_enumeration_bit_exact_with_oracle(gpu_lib):
+    k = W.make_descriptors(3000, 91, max_depth=4)
+    k[::97, 0] = 0        # invalid depths: no variants
+    k[5::131, 0] = 5
+    ref, ref_off = oracle.enumerate_variants(k)
+    v, off = advisor.advisor_enumerate_variants(torch.from_numpy(k).cuda())
+    assert np.array_equal(off.cpu().numpy(), ref_off)
+    assert np.array_equal(v.cpu().numpy(), ref)
+
+
+def test_capacity_and_empty_input(gpu_lib):
+    L = gpu_lib
+    import ctypes
+    k = torch.from_numpy(W.make_dslash_kernels(10, 3)).cuda()
+    out = torch.full((500, 16), -7, dtype=torch.int64, device="cuda")
+    off = torch.empty(11, dtype=torch.int64, device="cuda")
+    total = torch.empty(1, dtype=torch.int64, device="cuda")
+    assert L.advisor_enumerate_variants(ctypes.c_void_p(k.data_ptr()), 10, ctypes.c_void_p(out.data_ptr()), 400,
+                                        ctypes.c_void_p(off.data_ptr()), ctypes.c_void_p(total.data_ptr()),
+                                        None) == advisor.OK
+    torch.cuda.synchronize()
+    ref, ref_off = oracle.enumerate_variants(k.cpu().numpy())
+    assert int(total.item()) == 840 and np.array_equal(off.cpu().numpy(), ref_off)
+    o = out.cpu().numpy()
+    assert np.array_equal(o[:400], ref[:400]) and (o[400:] == -7).all()   # nothing past the capacity
+    v, off0 = advisor.advisor_enumerate_variants(torch.zeros((0, 16), dtype=torch.int64, device="cuda"))
+    assert v.shape[0] == 0 and off0.cpu().tolist() == [0]
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_dslash_enumerate_and_rank(gpu_lib, precision):
+    wl = W.BATCHED_4096   # the batched model (F = 64, 64-256-256-256-1) covers depth-4 nests
+    kernels = W.make_dslash_kernels(256, 17)
+    d_k = torch.from_numpy(kernels).cuda()
+    v, off = advisor.advisor_enumerate_variants(d_k)
+    assert v.shape[0] == 256 * 84
+    cal = W.calibration_descriptors(16384)
+    fc, sc = oracle.extract_features(cal, 64)
+    mu, sigma = oracle.fit_standardizer(fc, sc)
+    p = wl.weights()
+    m = advisor.Model(wl.widths, max_rows=max(v.shape[0], 16384), max_kernels=256)
+    m.set_params(p, mu, sigma)
+    fcal, scal = advisor.advisor_extract_features(torch.from_numpy(cal).cuda(), 64)
+    eps, eps32 = m.calibrate_eps(fcal, scal, precision), m.calibrate_eps(fcal, scal, "fp32")
+    best, _ = m.rank(v.contiguous(), off, precision, eps=eps, eps32=eps32)
+    ref_v, ref_off = oracle.enumerate_variants(kernels)
+    ref_best = oracle.rank(ref_v, ref_off, wl.widths, p, mu, sigma)[0]
+    assert np.array_equal(best.cpu().numpy(), ref_best)
+    assert m.device_status() == 0

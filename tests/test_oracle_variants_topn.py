@@ -103,3 +103,12 @@ def test_topn_one_is_the_argmin_and_permutation_invariant():
     _, sa = oracle.select_topn(y, off, 5)
     _, sb = oracle.select_topn(yp, off, 5)
     assert np.array_equal(sa, sb)
+
+
+def test_library_variant_count_matches_table1():
+    """The C ABI's host-side count (no GPU needed) against the printed table."""
+    from paper_2301_03636_gb300 import advisor, build
+    build.build()
+    for depth, count in _table1().items():
+        assert advisor.advisor_variant_count(depth) == count
+    assert advisor.advisor_variant_count(0) == 0 and advisor.advisor_variant_count(5) == 0
