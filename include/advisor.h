@@ -250,18 +250,22 @@ advisor_status advisor_model_calibrate_fp8(advisor_model_t m, const int32_t* d_f
                                            cudaStream_t stream);
 
 /* Launch shapes of the hot path (the batching of many kernels' variants
- * into persistent launches).  Every setting gives bit-identical results:
- * rows, tiles and segments run the same per-row / per-segment code whatever
- * the grid or block, and no summation order depends on them. */
+ * into persistent launches).  Every setting but layer_path gives
+ * bit-identical results: rows, tiles and segments run the same per-row /
+ * per-segment code whatever the grid or block, and no summation order
+ * depends on them. */
 typedef struct {
     int32_t extract_block;      /* threads per block of the extraction kernel: 64, 128 or 256 */
     int32_t tc_ctas;            /* CTAs of the persistent tensor-core scorer (at most one per SM; 0 = one per SM) */
     int32_t list_blocks_per_sm; /* FP32 near-tie scorer: persistent 16-row blocks per SM, 1 or 2 */
     int32_t list_chunk_kb;      /* FP32 near-tie scorer: weight chunk per bulk copy, 16 or 32 (KB) */
     int32_t select_block;       /* threads per block of the selection kernels (a warp per kernel): 128 or 256 */
+    int32_t layer_path;         /* 1: score models that fit the fused tensor-core kernel (hidden widths <= 256)
+                                   with one launch per layer instead (0 or 1); the two paths agree within the
+                                   16-bit error bound (different accumulation order), not bit for bit */
 } advisor_launch_config;
 
-/* The model's launch shapes (defaults 128, 0, 1, 32, 256), used by every
+/* The model's launch shapes (defaults 128, 0, 1, 32, 256, 0), used by every
  * later call.  set returns ADVISOR_ERR_INVALID_ARGUMENT for a value outside
  * the lists above and leaves the configuration unchanged. */
 advisor_status advisor_model_get_launch_config(advisor_model_t m, advisor_launch_config* out);

@@ -97,7 +97,7 @@ class LaunchConfig(ctypes.Structure):
     """advisor_launch_config: launch shapes of the hot path (results do not depend on them)."""
     _fields_ = [("extract_block", ctypes.c_int32), ("tc_ctas", ctypes.c_int32),
                 ("list_blocks_per_sm", ctypes.c_int32), ("list_chunk_kb", ctypes.c_int32),
-                ("select_block", ctypes.c_int32)]
+                ("select_block", ctypes.c_int32), ("layer_path", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -63,10 +63,11 @@ WsLayout ws_layout(const adv::ModelLayout& L, int64_t R, int64_t K, adv::TrainLa
     w.x_img = take((size_t)tiles * L.nslab[0] * ADV_X_SLAB_BYTES);
     // models too wide for the fused scorer run layer by layer through two
     // activation images and per-chunk partial sums of the output layer
-    const bool wide = !L.tc_ok && L.n_hidden >= 1;
-    for (int i = 0; i < 2; ++i) w.h_img[i] = take(wide ? (size_t)tiles * (L.nmax / 64) * ADV_X_SLAB_BYTES : 0);
-    const int last_chunks = (L.npad[L.n_hidden > 0 ? L.n_hidden - 1 : 0] + 255) / 256;
-    w.partial = take(wide ? (size_t)2 * last_chunks * tiles * ADV_TILE_M * 4 : 0);
+    // (every model may run layer by layer: the path a launch configuration can choose)
+    const bool layered = L.n_hidden >= 1;
+    for (int i = 0; i < 2; ++i) w.h_img[i] = take(layered ? (size_t)tiles * (L.nmax / 64) * ADV_X_SLAB_BYTES : 0);
+    const int last_chunks = (L.npad8[L.n_hidden > 0 ? L.n_hidden - 1 : 0] + 255) / 256;
+    w.partial = take(layered ? (size_t)2 * last_chunks * tiles * ADV_TILE_M * 4 : 0);
     w.feat32 = take((size_t)R * L.F * 4);
     w.status = take((size_t)R);
     w.scores = take((size_t)R * 4);
@@ -143,6 +144,11 @@ bool tc_supported(const advisor_model* m) {
 
 // Models whose hidden layers exceed the fused scorer: one launch per layer.
 bool wide_supported(const advisor_model* m) { return !m->L.tc_ok && m->L.n_hidden >= 1; }
+// The fused scorer for this call: the model fits it, the precision is 16-bit
+// and the launch configuration does not ask for the layer-by-layer path.
+bool use_fused(const advisor_model* m, advisor_precision p) {
+    return tc_supported(m) && p != ADVISOR_FP8_E4M3 && !m->cfg.layer_path;
+}
 
 cudaError_t launch_wide(advisor_model* m, const uint8_t* x_img, int64_t n_rows, const uint8_t* status, float* scores,
                         int fi, cudaStream_t s);
@@ -336,6 +342,7 @@ advisor_status advisor_model_get_launch_config(advisor_model_t m, advisor_launch
     out->list_blocks_per_sm = m->cfg.list_blocks_per_sm;
     out->list_chunk_kb = m->cfg.list_chunk_kb;
     out->select_block = m->cfg.select_block;
+    out->layer_path = m->cfg.layer_path;
     return ADVISOR_OK;
 }
 
@@ -347,6 +354,7 @@ advisor_status advisor_model_set_launch_config(advisor_model_t m, const advisor_
     n.list_blocks_per_sm = c->list_blocks_per_sm;
     n.list_chunk_kb = c->list_chunk_kb;
     n.select_block = c->select_block;
+    n.layer_path = c->layer_path;
     if (!adv::launch_config_valid(n)) return ADVISOR_ERR_INVALID_ARGUMENT;
     m->cfg = n;
     return ADVISOR_OK;
@@ -512,8 +520,8 @@ advisor_status advisor_score_variants(advisor_model_t m, const int32_t* d_feat_q
     } else if (precision != ADVISOR_BF16 && precision != ADVISOR_FP16) {
         return ADVISOR_ERR_UNSUPPORTED;
     }
-    const bool fused = tc_supported(m) && precision != ADVISOR_FP8_E4M3;
-    if (!fused && !wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
+    const bool fused = use_fused(m, precision);
+    if (!fused && m->L.n_hidden < 1) return ADVISOR_ERR_UNSUPPORTED;
     const int fi = precision == ADVISOR_BF16 ? 0 : (precision == ADVISOR_FP16 ? 1 : 2);
     const int64_t npad = ((n_rows + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
     uint8_t* x = m->WS + m->W.x_img;
@@ -591,8 +599,8 @@ advisor_status rank_scores(advisor_model* m, const advisor_variant_desc* d_desc,
     } else if (precision != ADVISOR_BF16 && precision != ADVISOR_FP16) {
         return ADVISOR_ERR_UNSUPPORTED;
     }
-    const bool fused = tc_supported(m) && precision != ADVISOR_FP8_E4M3;
-    if (!fused && !wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
+    const bool fused = use_fused(m, precision);
+    if (!fused && m->L.n_hidden < 1) return ADVISOR_ERR_UNSUPPORTED;
     const int fi = precision == ADVISOR_BF16 ? 0 : (precision == ADVISOR_FP16 ? 1 : 2);
     a.n_rows_padded = ((n_rows + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
     a.x_img = m->WS + m->W.x_img;

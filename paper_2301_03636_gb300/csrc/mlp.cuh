@@ -43,15 +43,18 @@ struct ExtractArgs {
     const float* x8_scale;   // E4M3 image (format 3): the first layer's activation scale (device)
 };
 // Launch shapes of the hot path that a plan's autotuner may vary.  Every
-// choice gives bit-identical results: rows, segments and tiles are processed
-// by the same per-row / per-segment code whatever the grid or block shape,
-// and no summation order depends on them.
+// choice but layer_path gives bit-identical results: rows, segments and tiles
+// are processed by the same per-row / per-segment code whatever the grid or
+// block shape, and no summation order depends on them; layer_path changes
+// the tensor-core accumulation order (results agree within the 16-bit error
+// bound, and the tiered re-score keeps the selections exact).
 struct LaunchConfig {
     int extract_block = 128;       // threads per block of the extraction kernel: 64, 128 or 256
     int tc_ctas = 0;               // CTAs of the persistent tensor-core scorer: 0 = one per SM
     int list_blocks_per_sm = 1;    // FP32 near-tie scorer: blocks per SM, 1 or 2
     int list_chunk_kb = 32;        // FP32 near-tie scorer: weight chunk per bulk copy, 16 or 32 KB
     int select_block = 256;        // threads per block of the selection kernels: 128 or 256
+    int layer_path = 0;            // 1: run models that fit the fused scorer layer by layer instead
 };
 bool launch_config_valid(const LaunchConfig& c);
 

@@ -8,7 +8,8 @@
 // the sequence as one graph removes the per-launch host overhead and the
 // gaps between kernels.  The autotuner measures a small set of launch shapes
 // (advisor_launch_config) on the caller's own data and keeps the fastest;
-// the shapes never change results, so the choice is a pure speed decision.
+// the shapes never change the selections (the layer-by-layer path changes
+// the last bits of the 16-bit scores, within their error bound).
 //
 // Only public entry points of the library are used here.
 #include <algorithm>
@@ -48,7 +49,7 @@ struct RankCall {
 bool same(const advisor_launch_config& a, const advisor_launch_config& b) {
     return a.extract_block == b.extract_block && a.tc_ctas == b.tc_ctas &&
            a.list_blocks_per_sm == b.list_blocks_per_sm && a.list_chunk_kb == b.list_chunk_kb &&
-           a.select_block == b.select_block;
+           a.select_block == b.select_block && a.layer_path == b.layer_path;
 }
 
 void release(cudaGraph_t g, cudaGraphExec_t x) {
@@ -173,7 +174,7 @@ advisor_status advisor_plan_rank(advisor_model_t m, const advisor_variant_desc* 
             return ADVISOR_ERR_CUDA;
         }
         // one setting at a time, in the order the kernels run
-        for (int knob = 0; knob < 4; ++knob) {
+        for (int knob = 0; knob < 5; ++knob) {
             std::vector<advisor_launch_config> cands;
             advisor_launch_config c = best;
             if (knob == 0) {
@@ -184,8 +185,10 @@ advisor_status advisor_plan_rank(advisor_model_t m, const advisor_variant_desc* 
                 c.list_blocks_per_sm = 1; c.list_chunk_kb = 32; cands.push_back(c);
                 c.list_blocks_per_sm = 2; c.list_chunk_kb = 16; cands.push_back(c);
                 c.list_blocks_per_sm = 1; c.list_chunk_kb = 16; cands.push_back(c);
-            } else {
+            } else if (knob == 3) {
                 for (int b : {128, 256}) { c.select_block = b; cands.push_back(c); }
+            } else {
+                for (int lp : {0, 1}) { c.layer_path = lp; cands.push_back(c); }
             }
             for (const auto& cand : cands) {
                 if (same(cand, best)) continue;

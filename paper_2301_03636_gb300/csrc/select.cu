@@ -424,7 +424,8 @@ cudaError_t launch_topn_final(const SelectArgs& a, cudaStream_t s, int block) {
 bool launch_config_valid(const LaunchConfig& c) {
     return (c.extract_block == 64 || c.extract_block == 128 || c.extract_block == 256) && c.tc_ctas >= 0 &&
            (c.list_blocks_per_sm == 1 || c.list_blocks_per_sm == 2) &&
-           (c.list_chunk_kb == 16 || c.list_chunk_kb == 32) && select_block_ok(c.select_block);
+           (c.list_chunk_kb == 16 || c.list_chunk_kb == 32) && select_block_ok(c.select_block) &&
+           (c.layer_path == 0 || c.layer_path == 1);
 }
 
 }  // namespace adv

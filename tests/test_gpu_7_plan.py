@@ -47,7 +47,7 @@ def _direct(m, d, o, precision, eps, eps32):
 
 
 CONFIGS = [
-    dict(extract_block=128, tc_ctas=0, list_blocks_per_sm=1, list_chunk_kb=32, select_block=256),   # default
+    dict(extract_block=128, tc_ctas=0, list_blocks_per_sm=1, list_chunk_kb=32, select_block=256, layer_path=0),  # default
     dict(extract_block=64, tc_ctas=0, list_blocks_per_sm=1, list_chunk_kb=32, select_block=256),
     dict(extract_block=256, tc_ctas=37, list_blocks_per_sm=2, list_chunk_kb=16, select_block=128),
     dict(extract_block=128, tc_ctas=1, list_blocks_per_sm=1, list_chunk_kb=16, select_block=128),
@@ -88,7 +88,7 @@ def test_invalid_launch_config_rejected(gpu_lib, setup):
     m = setup["m"]
     before = m.launch_config.as_dict()
     for bad in (dict(extract_block=96), dict(list_blocks_per_sm=3), dict(list_chunk_kb=64), dict(select_block=64),
-                dict(tc_ctas=-1)):
+                dict(tc_ctas=-1), dict(layer_path=2)):
         kw = dict(CONFIGS[0])
         kw.update(bad)
         with pytest.raises(advisor.AdvisorError):
@@ -138,14 +138,38 @@ def test_autotuned_plan(gpu_lib, setup):
     assert m.launch_config.as_dict() == before          # the model's own shapes are untouched
     assert info["replay_us"] > 0.0
     c = info["config"]
-    assert c["extract_block"] in (64, 128, 256) and c["select_block"] in (128, 256)
+    assert c["extract_block"] in (64, 128, 256) and c["select_block"] in (128, 256) and c["layer_path"] in (0, 1)
     assert (c["list_blocks_per_sm"], c["list_chunk_kb"]) in ((1, 32), (2, 16), (1, 16))
     plan.launch()
     torch.cuda.synchronize()
-    for a, b in zip((plan.best, plan.best_score, plan.scores, plan.status), direct):
-        assert torch.equal(a, b)
     assert np.array_equal(plan.best.cpu().numpy(), setup["ref_a"])
+    assert torch.equal(plan.status, direct[3])
+    if c["layer_path"] == 0:   # the same kernels as the direct call: identical bits
+        for a, b in zip((plan.best, plan.best_score, plan.scores), direct):
+            assert torch.equal(a, b)
+    else:                      # another accumulation order: within the calibrated bound
+        assert float((plan.scores - direct[2]).abs().max()) <= eps
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_layer_path_on_a_fused_model(gpu_lib, setup, precision):
+    """The layer-by-layer scorer run on a model the fused kernel also covers:
+    selections identical to the oracle, scores within the calibrated bound of
+    the fused kernel's."""
+    m = setup["m"]
+    eps, eps32 = setup["eps"][precision], setup["eps"]["fp32"]
+    d = torch.from_numpy(setup["d_a"]).cuda()
+    o = torch.from_numpy(setup["off"]).cuda()
+    fused = _direct(m, d, o, precision, eps, eps32)
+    try:
+        m.launch_config = _cfg(**dict(CONFIGS[0], layer_path=1))
+        layered = _direct(m, d, o, precision, eps, eps32)
+    finally:
+        m.launch_config = _cfg(**CONFIGS[0])
+    assert np.array_equal(layered[0].cpu().numpy(), setup["ref_a"])
+    assert float((layered[2] - fused[2]).abs().max()) <= eps
+    assert m.device_status() == 0
 
 
 def test_plan_rejects_what_rank_rejects(gpu_lib, setup):
