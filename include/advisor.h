@@ -112,9 +112,10 @@ const char* advisor_status_string(advisor_status s);
 
 /* Create the host object of an MLP with layer widths widths[0..n_widths-1]
  * (Sec. 5, Exp. 3: fully connected, ReLU hidden layers, one output neuron).
- * widths[0] = number of features F (32, 64 or 128), widths[n_widths-1] must be
- * 1, 3 <= n_widths <= 8, hidden widths 1..1024.  The tensor-core precisions
- * additionally need every hidden width <= 256 (checked when scoring). */
+ * widths[0] = number of features F (32, 33, 64 or 128), widths[n_widths-1]
+ * must be 1, 3 <= n_widths <= 8, hidden widths 1..1024 (any width: the
+ * tensor-core images pad to multiples of 64 with zero weights).  Hidden widths
+ * up to 256 run in the fused tensor-core scorer, wider ones layer by layer. */
 advisor_status advisor_model_create(const int32_t* h_widths, int32_t n_widths, advisor_model_t* out);
 advisor_status advisor_model_destroy(advisor_model_t m);
 
@@ -165,7 +166,11 @@ advisor_status advisor_fit_standardizer(const int32_t* d_feat_q16, const uint8_t
  * base-2 logarithm by repeated squaring), signed differences of those,
  * one-hot and small-integer variant parameters.  d_feat_q16 [n_rows][F]
  * row-major int32; invalid rows get all-zero features.  d_row_status [n_rows]
- * (nullable) receives the ADVISOR_ROW_* bits.  F in {32, 64, 128}. */
+ * (nullable) receives the ADVISOR_ROW_* bits.  F in {32, 33, 64, 128}: 32
+ * base features; 33 = the base features and the number of collapsed loops
+ * (dist_collapse + pf_collapse), the input width of the paper's network
+ * (Sec. 5 Exp. 3, whose 33 features the paper does not list); 64 adds eight
+ * features per loop level; 128 adds 64 signed differences of base features. */
 advisor_status advisor_extract_features(const advisor_variant_desc* d_desc, int64_t n_rows,
                                         int32_t n_features, int32_t* d_feat_q16,
                                         uint8_t* d_row_status, cudaStream_t stream);

@@ -54,6 +54,9 @@ def lib():
         _lib.orc_adam_step.argtypes = [P, P, P, P, i64, dbl, dbl, dbl, dbl, i64, P]
         _lib.orc_num_threads.restype = ctypes.c_int
         _lib.orc_select_topn.argtypes = [P, P, i64, ctypes.c_int, P, P]
+        _lib.orc_rmsprop_step.argtypes = [P, P, P, i64, dbl, dbl, dbl, dbl, P]
+        _lib.orc_mlp_rmse_grad.restype = dbl
+        _lib.orc_mlp_rmse_grad.argtypes = [P, P, i64, P, ctypes.c_int, P, P, P, P]
         _lib.orc_variant_count.restype = i64
         _lib.orc_variant_count.argtypes = [i64]
         _lib.orc_enumerate_variants.restype = i64
@@ -172,6 +175,28 @@ def loss_grad(feat, labels, widths, params, mu, sigma):
     loss = lib().orc_mlp_loss_grad(_p(feat), _p(labels), len(feat), _p(w), len(w), _p(params),
                                    _p(mu), _p(sigma), _p(grad))
     return float(loss), grad
+
+
+def rmse_grad(feat, labels, widths, params, mu, sigma):
+    """RMSE loss (Sec. 5 Exp. 3) and its FP64 gradient."""
+    feat = _c(feat, np.int32)
+    labels = _c(labels, np.float32)
+    w = _c(widths, np.int32)
+    params = _c(params, np.float32)
+    mu, sigma = _c(mu, np.float64), _c(sigma, np.float64)
+    grad = np.empty(len(params), dtype=np.float64)
+    loss = lib().orc_mlp_rmse_grad(_p(feat), _p(labels), len(feat), _p(w), len(w), _p(params),
+                                   _p(mu), _p(sigma), _p(grad))
+    return float(loss), grad
+
+
+def rmsprop_step(params, grad, v, lr, alpha, eps, weight_decay):
+    params = _c(params, np.float64)
+    grad = _c(grad, np.float64)
+    v = _c(v, np.float64).copy()
+    out = np.empty_like(params)
+    lib().orc_rmsprop_step(_p(params), _p(grad), _p(v), len(params), lr, alpha, eps, weight_decay, _p(out))
+    return out, v
 
 
 def adam_step(params, grad, m, v, lr, beta1, beta2, eps, step):

@@ -126,7 +126,7 @@ uint8_t orc_validate(const int64_t* d)
 
 static int32_t imax0(int32_t a) { return a > 0 ? a : 0; }
 
-/* Features of one valid descriptor.  F is 32, 64 or 128. */
+/* Features of one valid descriptor.  F is 32, 33, 64 or 128. */
 static void features_one(const int64_t* d, int F, int32_t* f)
 {
     const int64_t depth = d[0];
@@ -189,6 +189,10 @@ static void features_one(const int64_t* d, int F, int32_t* f)
     b[31] = orc_log2_q16((uint64_t)(T < P ? T : P));
     for (int j = 0; j < 32 && j < F; j++) f[j] = b[j];
     if (F <= 32) return;
+    if (F == 33) {   /* the paper-shaped input: the base features and the number of collapsed loops */
+        f[32] = (int32_t)(dc + pc) * Q1;
+        return;
+    }
 
     /* 8 features per loop level; all zero for levels >= depth */
     for (int i = 0; i < 4; i++) {
@@ -510,6 +514,33 @@ void orc_adam_step(const double* params, const double* grad, double* m, double* 
         double mh = m[i] / c1, vh = v[i] / c2;
         out_params[i] = params[i] - lr * mh / (sqrt(vh) + eps);
     }
+}
+
+/* RMSprop (Tieleman & Hinton 2012, the optimizer of Sec. 5 Exp. 3) with the */
+/* weight decay added to the gradient:                                        */
+/*   g' = g + wd * w;  v = alpha v + (1 - alpha) g'^2;  w -= lr g' / (sqrt(v) + eps). */
+void orc_rmsprop_step(const double* params, const double* grad, double* v, int64_t np_, double lr,
+                      double alpha, double eps, double wd, double* out_params)
+{
+    for (int64_t i = 0; i < np_; i++) {
+        const double g = grad[i] + wd * params[i];
+        v[i] = alpha * v[i] + (1.0 - alpha) * g * g;
+        out_params[i] = params[i] - lr * g / (sqrt(v[i]) + eps);
+    }
+}
+
+/* The RMSE loss of Sec. 5 Exp. 3, RMSE = sqrt(mean_r (y_r - t_r)^2), and its */
+/* gradient: with m = mean (y - t)^2 = 2 * (the MSE loss above),              */
+/* dRMSE = dm / (2 sqrt(m)) = (gradient of the MSE loss) / RMSE (0 if RMSE = 0). */
+double orc_mlp_rmse_grad(const int32_t* feat, const float* labels, int64_t n, const int32_t* widths,
+                         int nw, const float* params, const double* mu, const double* sigma, double* grad)
+{
+    const double half_ms = orc_mlp_loss_grad(feat, labels, n, widths, nw, params, mu, sigma, grad);
+    const double rmse = sqrt(2.0 * half_ms);
+    int64_t np_ = 0;
+    for (int l = 0; l + 1 < nw; l++) np_ += (int64_t)widths[l + 1] * widths[l] + widths[l + 1];
+    for (int64_t i = 0; i < np_; i++) grad[i] = rmse > 0.0 ? grad[i] / rmse : 0.0;
+    return rmse;
 }
 
 int orc_num_threads(void)

@@ -363,7 +363,7 @@ advisor_status advisor_model_set_launch_config(advisor_model_t m, const advisor_
 advisor_status advisor_model_create(const int32_t* h_widths, int32_t n_widths, advisor_model_t* out) {
     if (!h_widths || !out || n_widths < 3 || n_widths > ADV_MAX_LAYERS) return ADVISOR_ERR_INVALID_ARGUMENT;
     const int F = h_widths[0];
-    if (F != 32 && F != 64 && F != 128) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (F != 32 && F != 33 && F != 64 && F != 128) return ADVISOR_ERR_INVALID_ARGUMENT;
     if (h_widths[n_widths - 1] != 1) return ADVISOR_ERR_INVALID_ARGUMENT;
     for (int i = 1; i + 1 < n_widths; ++i)
         if (h_widths[i] < 1 || h_widths[i] > 1024) return ADVISOR_ERR_INVALID_ARGUMENT;
@@ -488,7 +488,7 @@ advisor_status advisor_fit_standardizer(const int32_t* d_feat_q16, const uint8_t
 
 advisor_status advisor_extract_features(const advisor_variant_desc* d_desc, int64_t n_rows, int32_t n_features,
                                         int32_t* d_feat_q16, uint8_t* d_row_status, cudaStream_t stream) {
-    if (n_rows < 0 || (n_features != 32 && n_features != 64 && n_features != 128))
+    if (n_rows < 0 || (n_features != 32 && n_features != 33 && n_features != 64 && n_features != 128))
         return ADVISOR_ERR_INVALID_ARGUMENT;
     if (n_rows == 0) return ADVISOR_OK;
     if (!d_desc || !d_feat_q16 || !aligned(d_desc, 16) || !aligned(d_feat_q16, 16))

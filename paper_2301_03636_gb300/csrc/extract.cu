@@ -119,9 +119,14 @@ __global__ void __launch_bounds__(256) extract_kernel(ExtractArgs a) {
         }
         if (a.status) a.status[row] = (uint8_t)st;
         if (a.feat) {
-            int4* dst = reinterpret_cast<int4*>(a.feat + (size_t)row * F);
+            if constexpr (F % 4 == 0) {
+                int4* dst = reinterpret_cast<int4*>(a.feat + (size_t)row * F);
 #pragma unroll
-            for (int j = 0; j < F / 4; ++j) dst[j] = make_int4(f[4 * j], f[4 * j + 1], f[4 * j + 2], f[4 * j + 3]);
+                for (int j = 0; j < F / 4; ++j) dst[j] = make_int4(f[4 * j], f[4 * j + 1], f[4 * j + 2], f[4 * j + 3]);
+            } else {   // rows not 16-byte aligned (F = 33)
+#pragma unroll
+                for (int j = 0; j < F; ++j) a.feat[(size_t)row * F + j] = f[j];
+            }
         }
     } else {
 #pragma unroll
@@ -147,11 +152,16 @@ __global__ void __launch_bounds__(128) standardize_kernel(const int32_t* __restr
     int32_t f[F];
     const bool valid = row < n_rows;
     if (valid) {
-        const int4* src = reinterpret_cast<const int4*>(feat + (size_t)row * F);
+        if constexpr (F % 4 == 0) {
+            const int4* src = reinterpret_cast<const int4*>(feat + (size_t)row * F);
 #pragma unroll
-        for (int j = 0; j < F / 4; ++j) {
-            const int4 v = __ldg(src + j);
-            f[4 * j] = v.x; f[4 * j + 1] = v.y; f[4 * j + 2] = v.z; f[4 * j + 3] = v.w;
+            for (int j = 0; j < F / 4; ++j) {
+                const int4 v = __ldg(src + j);
+                f[4 * j] = v.x; f[4 * j + 1] = v.y; f[4 * j + 2] = v.z; f[4 * j + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < F; ++j) f[j] = __ldg(feat + (size_t)row * F + j);
         }
     } else {
 #pragma unroll
@@ -228,6 +238,7 @@ cudaError_t launch_extract(const ExtractArgs& a, int F, int fmt, cudaStream_t s,
     if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;
     switch (F) {
         case 32: return launch_extract_f<32>(a, fmt, s, block);
+        case 33: return launch_extract_f<33>(a, fmt, s, block);
         case 64: return launch_extract_f<64>(a, fmt, s, block);
         case 128: return launch_extract_f<128>(a, fmt, s, block);
         default: return cudaErrorInvalidValue;
@@ -253,6 +264,7 @@ cudaError_t launch_standardize(const int32_t* feat, const uint8_t* status, int64
                                const float* x8_scale) {
     switch (F) {
         case 32: return launch_standardize_f<32>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, s);
+        case 33: return launch_standardize_f<33>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, s);
         case 64: return launch_standardize_f<64>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, s);
         case 128: return launch_standardize_f<128>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, s);
         default: return cudaErrorInvalidValue;

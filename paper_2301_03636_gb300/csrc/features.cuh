@@ -223,6 +223,10 @@ __device__ __forceinline__ void row_features_from_logs(const int64_t (&d)[16], c
     base[31] = L[A_MIN];
 #pragma unroll
     for (int j = 0; j < 32; ++j) f[j] = base[j];
+    if constexpr (F == 33) {
+        // the paper-shaped input (33 features): the number of collapsed loops
+        f[32] = (r.dc + r.pc) * ONE;
+    }
     if constexpr (F >= 64) {
         // per loop level: log trip, distributed?, parallel-for?, in a collapse
         // group of >= 2 loops?, log prefix product, log suffix product,
@@ -256,7 +260,7 @@ __device__ __forceinline__ void row_features_from_logs(const int64_t (&d)[16], c
     }
 }
 
-// The F features of a valid row (F = 32, 64 or 128), one thread.
+// The F features of a valid row (F = 32, 33, 64 or 128), one thread.
 template <int F>
 __device__ __forceinline__ void row_features(const int64_t (&d)[16], int32_t (&f)[F]) {
     constexpr int N = FeatureLogs<F>::N;
@@ -274,7 +278,7 @@ __device__ __forceinline__ void row_features(const int64_t (&d)[16], int32_t (&f
 // group assembles the (identical) feature vector, keeping features g + G q
 // in mine[q].
 template <int F, int G>
-__device__ __forceinline__ void row_features_lanes(const int64_t (&d)[16], int g, int32_t (&mine)[F / G]) {
+__device__ __forceinline__ void row_features_lanes(const int64_t (&d)[16], int g, int32_t (&mine)[(F + G - 1) / G]) {
     static_assert(G == 8 || G == 16 || G == 32, "lane group size");
     constexpr int N = FeatureLogs<F>::N;
     constexpr int NL = (N + G - 1) / G;   // logarithms per lane
@@ -294,7 +298,7 @@ __device__ __forceinline__ void row_features_lanes(const int64_t (&d)[16], int g
     int32_t f[F];
     row_features_from_logs<F>(d, L, f);
 #pragma unroll
-    for (int q = 0; q < F / G; ++q) mine[q] = 0;
+    for (int q = 0; q < (F + G - 1) / G; ++q) mine[q] = 0;
 #pragma unroll
     for (int j = 0; j < F; ++j)
         if (j % G == g) mine[j / G] = f[j];

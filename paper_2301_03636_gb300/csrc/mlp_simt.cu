@@ -26,11 +26,16 @@ __device__ __forceinline__ bool fetch_row_features(const RowSrc& src, int64_t ro
         }
         return st == 0 && !(src.status && src.status[row]);
     } else {
-        const int4* p = reinterpret_cast<const int4*>(src.feat + (size_t)row * F);
+        if constexpr (F % 4 == 0) {
+            const int4* p = reinterpret_cast<const int4*>(src.feat + (size_t)row * F);
 #pragma unroll
-        for (int j = 0; j < F / 4; ++j) {
-            const int4 v = __ldg(p + j);
-            f[4 * j] = v.x; f[4 * j + 1] = v.y; f[4 * j + 2] = v.z; f[4 * j + 3] = v.w;
+            for (int j = 0; j < F / 4; ++j) {
+                const int4 v = __ldg(p + j);
+                f[4 * j] = v.x; f[4 * j + 1] = v.y; f[4 * j + 2] = v.z; f[4 * j + 3] = v.w;
+            }
+        } else {   // rows not 16-byte aligned (F = 33)
+#pragma unroll
+            for (int j = 0; j < F; ++j) f[j] = __ldg(src.feat + (size_t)row * F + j);
         }
         return !(src.status && src.status[row]);
     }
@@ -41,7 +46,7 @@ __device__ __forceinline__ bool fetch_row_features(const RowSrc& src, int64_t ro
 // Returns the row's validity; every lane of the warp must call it.
 template <int F, int G, bool FROM_DESC>
 __device__ __forceinline__ bool fetch_row_features_lanes(const RowSrc& src, int64_t row, int g,
-                                                         int32_t (&mine)[F / G]) {
+                                                         int32_t (&mine)[(F + G - 1) / G]) {
     bool ok = false;
     if constexpr (FROM_DESC) {
         int64_t d[16];
@@ -53,17 +58,17 @@ __device__ __forceinline__ bool fetch_row_features_lanes(const RowSrc& src, int6
         row_features_lanes<F, G>(d, g, mine);
         if (!ok) {
 #pragma unroll
-            for (int q = 0; q < F / G; ++q) mine[q] = 0;
+            for (int q = 0; q < (F + G - 1) / G; ++q) mine[q] = 0;
         }
     } else {
         if (row >= 0) {
             const int32_t* p = src.feat + (size_t)row * F;
 #pragma unroll
-            for (int q = 0; q < F / G; ++q) mine[q] = __ldg(p + G * q + g);
+            for (int q = 0; q < (F + G - 1) / G; ++q) mine[q] = G * q + g < F ? __ldg(p + G * q + g) : 0;
             ok = true;
         } else {
 #pragma unroll
-            for (int q = 0; q < F / G; ++q) mine[q] = 0;
+            for (int q = 0; q < (F + G - 1) / G; ++q) mine[q] = 0;
         }
     }
     return ok && !(src.status && src.status[row]);
@@ -241,12 +246,12 @@ __global__ void __launch_bounds__(256, 1) mlp_fp32_list_kernel(MlpDesc m, RowSrc
             const int lane = tid & 31, r = 2 * (tid >> 5) + (lane >> 4), g = lane & 15;
             const int64_t pos = tile * RB + r;
             const int64_t row = pos < count ? (src.rows ? src.rows[pos] : pos) : -1;
-            int32_t mine[F / 16];
+            int32_t mine[(F + 15) / 16];
             const bool ok = fetch_row_features_lanes<F, 16, FROM_DESC>(src, row, g, mine);
 #pragma unroll
-            for (int q = 0; q < F / 16; ++q) {
+            for (int q = 0; q < (F + 15) / 16; ++q) {
                 const int k = 16 * q + g;
-                h0[k * RB + r] = fmaf((float)mine[q], __ldg(m.sa + k), -__ldg(m.sc + k));
+                if (k < F) h0[k * RB + r] = fmaf((float)mine[q], __ldg(m.sa + k), -__ldg(m.sc + k));
             }
             if (g == 0) row_ok[r] = ok ? 1 : 0;
         }
@@ -343,10 +348,11 @@ __global__ void __launch_bounds__(256) mlp_fp64_kernel(MlpDesc m, RowSrc src, do
         const int64_t row = src.rows ? src.rows[pos] : pos;
         if (threadIdx.x < 32) {   // warp 0 fetches the row, its lanes sharing the logarithms
             const int lane = threadIdx.x;
-            int32_t mine[F / 32];
+            int32_t mine[(F + 31) / 32];
             const bool ok = fetch_row_features_lanes<F, 32, FROM_DESC>(src, row, lane, mine);
 #pragma unroll
-            for (int q = 0; q < F / 32; ++q) fs[32 * q + lane] = mine[q];
+            for (int q = 0; q < (F + 31) / 32; ++q)
+                if (32 * q + lane < F) fs[32 * q + lane] = mine[q];
             if (lane == 0) okf = ok ? 1 : 0;
         }
         __syncthreads();
@@ -400,6 +406,7 @@ template <int TM, int RPT, bool FD>
 static cudaError_t launch_fp32_f(const MlpDesc& m, const RowSrc& src, float* out, int grid, cudaStream_t s) {
     switch (m.widths[0]) {
         case 32: return launch_fp32_t<TM, RPT, 32, FD>(m, src, out, grid, s);
+        case 33: return launch_fp32_t<TM, RPT, 33, FD>(m, src, out, grid, s);
         case 64: return launch_fp32_t<TM, RPT, 64, FD>(m, src, out, grid, s);
         case 128: return launch_fp32_t<TM, RPT, 128, FD>(m, src, out, grid, s);
         default: return cudaErrorInvalidValue;
@@ -441,6 +448,7 @@ static cudaError_t launch_fp32_list(const MlpDesc& m, const RowSrc& src, float* 
     }
     switch (m.widths[0]) {
         case 32: return fd ? launch_fp32_list_t<32, true>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s) : launch_fp32_list_t<32, false>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s);
+        case 33: return fd ? launch_fp32_list_t<33, true>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s) : launch_fp32_list_t<33, false>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s);
         case 64: return fd ? launch_fp32_list_t<64, true>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s) : launch_fp32_list_t<64, false>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s);
         case 128: return fd ? launch_fp32_list_t<128, true>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s) : launch_fp32_list_t<128, false>(m, src, out, grid, wmax4, status_word, blocks_per_sm, chunk_kb, s);
         default: return cudaErrorInvalidValue;
@@ -486,6 +494,7 @@ cudaError_t launch_mlp_fp64(const MlpDesc& m, const RowSrc& src, double* out, in
     const bool fd = (src.feat == nullptr);
     switch (m.widths[0]) {
         case 32: return fd ? launch_fp64_t<32, true>(m, src, out, grid, s) : launch_fp64_t<32, false>(m, src, out, grid, s);
+        case 33: return fd ? launch_fp64_t<33, true>(m, src, out, grid, s) : launch_fp64_t<33, false>(m, src, out, grid, s);
         case 64: return fd ? launch_fp64_t<64, true>(m, src, out, grid, s) : launch_fp64_t<64, false>(m, src, out, grid, s);
         case 128: return fd ? launch_fp64_t<128, true>(m, src, out, grid, s) : launch_fp64_t<128, false>(m, src, out, grid, s);
         default: return cudaErrorInvalidValue;

@@ -199,3 +199,64 @@ def test_adam_first_step_closed_form():
     out, m, v = oracle.adam_step(p, g, np.zeros(4), np.zeros(4), 1e-3, 0.9, 0.999, 1e-8, 1)
     assert np.allclose(out, p - 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_rmse_gradient_against_finite_differences():
+    """RMSE loss of Sec. 5 Exp. 3 (sqrt of the mean squared error), checked
+    against its definition on the forward values and by central differences."""
+    widths = (33, 10, 6, 1)
+    rng = np.random.Generator(np.random.PCG64(9))
+    p = (np.round(rng.normal(0, 0.4, size=W.param_count(widths)) * 4096) / 4096).astype(np.float32)
+    d = W.make_descriptors(48, 19)
+    f, st = oracle.extract_features(d, 33)
+    mu, sigma = oracle.fit_standardizer(f, st)
+    t = rng.normal(0, 1, size=48).astype(np.float32)
+    loss, g = oracle.rmse_grad(f, t, widths, p, mu, sigma)
+    y = oracle.mlp_forward(f, widths, p, mu, sigma)
+    assert abs(loss - np.sqrt(np.mean((y - t.astype(np.float64)) ** 2))) < 1e-12
+    h = 2.0 ** -12
+    errs = []
+    for i in rng.choice(len(p), size=50, replace=False):
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (oracle.rmse_grad(f, t, widths, pp, mu, sigma)[0] - oracle.rmse_grad(f, t, widths, pm, mu, sigma)[0]) / (2 * h)
+        errs.append(abs(fd - g[i]) / max(1e-6, abs(g[i]), abs(fd)))
+    errs = np.array(errs)
+    assert np.median(errs) < 1e-6 and np.quantile(errs, 0.9) < 1e-4
+
+
+def test_rmsprop_first_steps_closed_form():
+    """From v = 0: v1 = (1 - a) g'^2 and the update is lr g' / (sqrt(1 - a) |g'| + eps),
+    with g' = g + wd w; a second step follows the recursion by hand."""
+    p = np.array([1.0, -2.0, 0.5, 0.0])
+    g = np.array([0.1, -3.0, 0.0, 1e-3])
+    lr, a, eps, wd = 0.01, 0.99, 1e-8, 1e-4
+    out, v = oracle.rmsprop_step(p, g, np.zeros(4), lr, a, eps, wd)
+    gp = g + wd * p
+    assert np.allclose(v, (1 - a) * gp * gp, rtol=1e-14, atol=0)
+    assert np.allclose(out, p - lr * gp / (np.sqrt(1 - a) * np.abs(gp) + eps), rtol=1e-13, atol=1e-16)
+    out2, v2 = oracle.rmsprop_step(out, g, v, lr, a, eps, wd)
+    gp2 = g + wd * out
+    vv = a * v + (1 - a) * gp2 * gp2
+    assert np.allclose(v2, vv, rtol=1e-14, atol=0)
+    assert np.allclose(out2, out - lr * gp2 / (np.sqrt(vv) + eps), rtol=1e-13, atol=1e-16)
+
+
+def test_features_33_are_the_base_features_and_the_collapse_count():
+    """F = 33 (the paper's input width): the 32 base features and
+    (dist_collapse + pf_collapse) * 2^16, hand-checked on fixed variants."""
+    d = np.ones((3, 16), dtype=np.int64)
+    d[:, 0] = 3
+    d[:, 1:4] = [[16, 8, 4], [16, 8, 4], [16, 8, 4]]
+    d[:, 5], d[:, 6], d[:, 7], d[:, 8] = 2, 8, 1024, 512
+    d[:, 9], d[:, 10] = 64, 128
+    d[:, 11:14] = [[0, 0, 3], [1, 1, 2], [2, 2, 1]]   # (pf_pos, dist_collapse, pf_collapse)
+    d[:, 14:16] = [[0, 0], [1, 1], [2, 0]]
+    f33, st = oracle.extract_features(d, 33)
+    f32, _ = oracle.extract_features(d, 32)
+    assert (st == 0).all()
+    assert np.array_equal(f33[:, :32], f32)
+    assert f33[:, 32].tolist() == [3 * 65536, 3 * 65536, 3 * 65536]
+    d[1, 13] = 1
+    assert oracle.extract_features(d, 33)[0][1, 32] == 2 * 65536
