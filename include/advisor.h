@@ -340,6 +340,27 @@ advisor_status advisor_train_step(advisor_model_t m, const int32_t* d_feat_q16, 
                                   int64_t n_rows, advisor_precision precision, const float* h_adam,
                                   float* d_loss, cudaStream_t stream);
 
+/* A training step with a choice of optimizer and loss (Sec. 5 Exp. 3 trains
+ * with RMSprop and the RMSE loss): optimizer ADVISOR_OPT_ADAM (lr, beta1,
+ * beta2, eps, decoupled weight_decay: the update of advisor_train_step) or
+ * ADVISOR_OPT_RMSPROP (g' = g + weight_decay w; v = alpha v + (1 - alpha)
+ * g'^2; w -= lr g' / (sqrt(v) + eps), v kept with the model); loss
+ * ADVISOR_LOSS_MSE (0.5 mean (y - t)^2) or ADVISOR_LOSS_RMSE (sqrt(mean
+ * (y - t)^2)).  d_loss (nullable) receives the loss before the update.
+ * Precisions as advisor_train_step. */
+#define ADVISOR_OPT_ADAM 0
+#define ADVISOR_OPT_RMSPROP 1
+#define ADVISOR_LOSS_MSE 0
+#define ADVISOR_LOSS_RMSE 1
+typedef struct {
+    int32_t optimizer;
+    int32_t loss;
+    float lr, beta1, beta2, alpha, eps, weight_decay;
+} advisor_train_options;
+advisor_status advisor_train_step_ex(advisor_model_t m, const int32_t* d_feat_q16, const float* d_labels,
+                                     int64_t n_rows, advisor_precision precision, const advisor_train_options* opt,
+                                     float* d_loss, cudaStream_t stream);
+
 /* Gradient only (no update): d_grad [param_count] FP32 of the same loss,
  * same layout as the master parameters.  For gradient checks. */
 advisor_status advisor_loss_grad(advisor_model_t m, const int32_t* d_feat_q16, const float* d_labels,

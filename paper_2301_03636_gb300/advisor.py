@@ -78,6 +78,7 @@ def lib():
         "advisor_model_calibrate_fp8": (st, [P, P, i64, P]),
         "advisor_variant_count": (i64, [i64]),
         "advisor_rank_topn": (st, [P, P, i64, P, i64, i32, st, f32, f32, P, P, P, P, P]),
+        "advisor_train_step_ex": (st, [P, P, P, i64, st, P, P, P]),
         "advisor_enumerate_variants": (st, [P, i64, P, i64, P, P, P]),
         "advisor_model_set_launch_config": (st, [P, P]),
         "advisor_plan_rank": (st, [P, P, i64, P, i64, st, f32, f32, P, P, P, P, i32, P, ctypes.POINTER(P)]),
@@ -101,6 +102,13 @@ class LaunchConfig(ctypes.Structure):
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class TrainOptions(ctypes.Structure):
+    """advisor_train_options: optimizer 0 Adam / 1 RMSprop, loss 0 MSE / 1 RMSE."""
+    _fields_ = [("optimizer", ctypes.c_int32), ("loss", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("alpha", ctypes.c_float),
+                ("eps", ctypes.c_float), ("weight_decay", ctypes.c_float)]
 
 
 def header_functions() -> list[str]:
@@ -319,6 +327,15 @@ class Model:
         _check(lib().advisor_train_step(self.handle, _ptr(feat), _ptr(labels), feat.shape[0], _prec(precision),
                                         ctypes.cast(h, ctypes.c_void_p), _ptr(loss), _stream(stream)),
                "advisor_train_step")
+        return loss
+
+    def train_step_ex(self, feat, labels, precision="fp32", optimizer="rmsprop", loss_fn="rmse", lr=0.01,
+                      alpha=0.99, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, loss=None, stream=None):
+        """One step with a choice of optimizer ("adam" / "rmsprop") and loss ("mse" / "rmse")."""
+        o = TrainOptions(optimizer={"adam": 0, "rmsprop": 1}[optimizer], loss={"mse": 0, "rmse": 1}[loss_fn],
+                         lr=lr, beta1=beta1, beta2=beta2, alpha=alpha, eps=eps, weight_decay=weight_decay)
+        _check(lib().advisor_train_step_ex(self.handle, _ptr(feat), _ptr(labels), feat.shape[0], _prec(precision),
+                                           ctypes.byref(o), _ptr(loss), _stream(stream)), "advisor_train_step_ex")
         return loss
 
     def loss_grad(self, feat, labels, precision="fp32", stream=None):

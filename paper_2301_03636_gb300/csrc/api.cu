@@ -741,6 +741,30 @@ advisor_status advisor_train_step(advisor_model_t m, const int32_t* d_feat_q16, 
     return ADVISOR_OK;
 }
 
+advisor_status advisor_train_step_ex(advisor_model_t m, const int32_t* d_feat_q16, const float* d_labels,
+                                     int64_t n_rows, advisor_precision precision, const advisor_train_options* opt,
+                                     float* d_loss, cudaStream_t stream) {
+    if (!m || !d_feat_q16 || !d_labels || !opt || n_rows < 1) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if ((opt->optimizer != ADVISOR_OPT_ADAM && opt->optimizer != ADVISOR_OPT_RMSPROP) ||
+        (opt->loss != ADVISOR_LOSS_MSE && opt->loss != ADVISOR_LOSS_RMSE))
+        return ADVISOR_ERR_INVALID_ARGUMENT;
+    advisor_status st = check_ready(m, n_rows);
+    if (st != ADVISOR_OK) return st;
+    const int fmt = train_fmt(m, precision);
+    if (fmt < 0) return ADVISOR_ERR_UNSUPPORTED;
+    adv::TrainOptions o{};
+    o.optimizer = opt->optimizer;
+    o.loss = opt->loss;
+    o.h = adv::AdamHyper{opt->lr, opt->beta1, opt->beta2, opt->eps, opt->weight_decay};
+    o.alpha = opt->alpha;
+    const int64_t step = m->adam_step + 1;
+    cudaError_t e = adv::launch_train_step_ex(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), m->lt, fmt,
+                                              d_feat_q16, d_labels, n_rows, o, step, d_loss, stream);
+    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    m->adam_step = step;
+    return ADVISOR_OK;
+}
+
 advisor_status advisor_loss_grad(advisor_model_t m, const int32_t* d_feat_q16, const float* d_labels,
                                  int64_t n_rows, advisor_precision precision, float* d_grad, float* d_loss,
                                  cudaStream_t stream) {

@@ -139,6 +139,33 @@ __global__ void loss_final_kernel(const float* __restrict__ part, int nb, int64_
     }
 }
 
+// RMSE loss (Sec. 5 Exp. 3) from the MSE path's values: loss[0] holds
+// 0.5 mean e^2 and dy the MSE gradient e / n; RMSE = sqrt(2 loss[0]) goes to
+// loss[1] (and loss_out) and dy becomes e / (n RMSE), in place.
+__global__ void rmse_scale_kernel(float* __restrict__ dy, int64_t n, float* __restrict__ loss,
+                                  float* __restrict__ loss_out) {
+    const float rmse = sqrtf(2.f * loss[0]);
+    const float inv = rmse > 0.f ? 1.f / rmse : 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dy[i] *= inv;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        loss[1] = rmse;
+        if (loss_out) *loss_out = rmse;
+    }
+}
+
+// RMSprop (Tieleman & Hinton 2012) with the weight decay added to the
+// gradient: g' = g + wd w; v = alpha v + (1 - alpha) g'^2; w -= lr g' / (sqrt(v) + eps).
+__global__ void rmsprop_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ v, int64_t n,
+                               float lr, float alpha, float eps, float wd) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i] + wd * p[i];
+        const float vi = alpha * v[i] + (1.f - alpha) * gi * gi;
+        v[i] = vi;
+        p[i] -= lr * gi / (sqrtf(vi) + eps);
+    }
+}
+
 // Column sums of dZ [n][w] per split of SPLIT_ROWS rows.
 __global__ void colsum_kernel(const float* __restrict__ dz, int64_t n, int w, float* __restrict__ part,
                               int64_t split_stride) {
@@ -250,7 +277,7 @@ cudaError_t launch_mse_loss(const ModelLayout& L, const TrainLayout& T, uint8_t*
 
 // Backward of the saved forward from dL/dy (already in the dA buffer) to the
 // parameter gradient.
-static cudaError_t launch_backward_saved(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
+cudaError_t launch_backward_saved(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
                                         int64_t n, float* grad, cudaStream_t s) {
     cudaError_t e;
     auto act = [&](int l) { return reinterpret_cast<float*>(TW + T.act[l]); };
@@ -323,6 +350,32 @@ cudaError_t launch_adam_update(const ModelLayout& L, uint8_t* P, const float* gr
                                                   c2);
     adv_count_launch(1);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_repack(L, P, s);
+}
+
+cudaError_t launch_train_step_ex(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
+                                 const MlpDesc& md, LtContext* lt, int fmt, const int32_t* feat, const float* labels,
+                                 int64_t n, const TrainOptions& o, int64_t step, float* d_loss, cudaStream_t s) {
+    float* grad = reinterpret_cast<float*>(TW + T.grad);
+    float* loss = reinterpret_cast<float*>(TW + T.loss);
+    cudaError_t e = fmt == 0 ? launch_forward_saved(L, T, TW, md, feat, n, nullptr, s)
+                             : launch_forward_saved_tc(L, T, TW, md, lt, fmt, feat, n, nullptr, s);
+    if (e != cudaSuccess) return e;
+    e = launch_mse_loss(L, T, TW, labels, n, o.loss == 1 ? nullptr : d_loss, s);
+    if (e != cudaSuccess) return e;
+    if (o.loss == 1) {
+        rmse_scale_kernel<<<grid1(n), 256, 0, s>>>(reinterpret_cast<float*>(TW + T.dA), n, loss, d_loss);
+        adv_count_launch(1);
+    }
+    e = fmt == 0 ? launch_backward_saved(L, T, TW, md, n, grad, s) : launch_backward_tc(L, T, TW, md, lt, fmt, nullptr, n, grad, s);
+    if (e != cudaSuccess) return e;
+    if (o.optimizer == 0) return launch_adam_update(L, P, grad, o.h, step, s);
+    rmsprop_kernel<<<grid1(L.n_params), 256, 0, s>>>(reinterpret_cast<float*>(P + L.p_master), grad,
+                                                     reinterpret_cast<float*>(P + L.p_adam_v), L.n_params, o.h.lr,
+                                                     o.alpha, o.h.eps, o.h.weight_decay);
+    adv_count_launch(1);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_repack(L, P, s);
 }

@@ -54,6 +54,25 @@ cudaError_t launch_mse_loss(const ModelLayout& L, const TrainLayout& T, uint8_t*
 cudaError_t launch_adam_update(const ModelLayout& L, uint8_t* P, const float* grad, const AdamHyper& adam,
                                int64_t step, cudaStream_t s);
 
+// Backward of the saved forward from dL/dy already in the dA buffer.
+cudaError_t launch_backward_saved(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
+                                  int64_t n, float* grad, cudaStream_t s);
+
+// Optimizer and loss of a training step: optimizer 0 Adam (h), 1 RMSprop
+// (h.lr, alpha, h.eps, h.weight_decay added to the gradient); loss 0 MSE
+// (0.5 mean (y - t)^2), 1 RMSE (sqrt(mean (y - t)^2)).
+struct TrainOptions {
+    int optimizer;
+    int loss;
+    AdamHyper h;
+    float alpha;
+};
+struct LtContext;
+// One training step with these options; fmt 0 FP32 SIMT, 1 BF16, 2 FP16.
+cudaError_t launch_train_step_ex(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
+                                 const MlpDesc& md, LtContext* lt, int fmt, const int32_t* feat, const float* labels,
+                                 int64_t n, const TrainOptions& o, int64_t step, float* d_loss, cudaStream_t s);
+
 // 16-bit operands on the tensor cores (train_tc.cu); fmt 1 BF16, 2 FP16.
 struct LtContext;
 LtContext* lt_create();

@@ -51,6 +51,34 @@ def train(model: advisor.Model, feat: torch.Tensor, labels: torch.Tensor, steps:
     return model
 
 
+def train_paper_recipe(model: advisor.Model, feat: torch.Tensor, labels: torch.Tensor, epochs: int = 150,
+                       batch: int = 16, lr: float = 0.01, step_epochs: int = 30, gamma: float = 0.1,
+                       weight_decay: float = 1e-4, seed: int = 0, precision: str = "fp32",
+                       epoch_losses: list | None = None):
+    """The training recipe of Sec. 5 Exp. 3: RMSprop with an initial learning
+    rate of 0.01 multiplied by 0.1 every 30 epochs, weight decay 1e-4, the
+    RMSE loss, mini-batches of 16 rows (a fresh permutation per epoch; the
+    last partial batch of an epoch is dropped), 150 epochs.  `epoch_losses`
+    (optional) receives the mean batch RMSE of every epoch."""
+    n = feat.shape[0]
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+    steps_per_epoch = n // batch
+    for ep in range(epochs):
+        rate = lr * gamma ** (ep // step_epochs)
+        perm = torch.randperm(n, generator=g).to(feat.device)
+        acc = torch.zeros(1, dtype=torch.float32, device=feat.device)
+        for i in range(steps_per_epoch):
+            idx = perm[i * batch:(i + 1) * batch]
+            model.train_step_ex(feat.index_select(0, idx).contiguous(), labels.index_select(0, idx).contiguous(),
+                                precision, optimizer="rmsprop", loss_fn="rmse", lr=rate,
+                                weight_decay=weight_decay, loss=loss)
+            acc += loss
+        if epoch_losses is not None:
+            epoch_losses.append(float(acc.item()) / max(steps_per_epoch, 1))
+    return model
+
+
 def save_checkpoint(model: advisor.Model, path: str):
     torch.cuda.synchronize()
     blob = {"widths": model.widths, "param_block": model.param_block.cpu(), "adam_step": model.adam_step}
