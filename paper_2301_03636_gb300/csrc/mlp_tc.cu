@@ -4,14 +4,15 @@
 // layer (one neuron, Sec. 5 Exp. 3) fused into the last hidden layer's
 // epilogue in FP32.
 //
-// Persistent kernel, one CTA per SM, 640 threads:
-//   warps 0, 18, 19  weight producers: stream 64-column K slabs of each
-//                hidden layer's weights (pre-packed in the shared-memory image
-//                order, one 1-D bulk copy of up to 32 KB per slab) through a
-//                3-stage ring, producer q owning stage q.  Bulk copies issued
-//                by one thread complete one after another (~450-800 cycles
-//                each whatever their size), so one issuing thread per stage
-//                keeps three copies in flight;
+// Persistent kernel, one CTA per SM, 608 threads:
+//   warps 0, 18  weight producers: stream 64-column K slabs of each hidden
+//                layer's weights (pre-packed in the shared-memory image order,
+//                one 1-D bulk copy of up to 32 KB per slab) through a 2-stage
+//                ring, producer q owning stage q (bulk copies issued by one
+//                thread complete one after another, ~450-800 cycles each).
+//                Two stages leave room for the biases and the output row in
+//                shared memory, which shortens the epilogue more than a third
+//                stage would shorten the MMA waits;
 //   warp 1       MMA issuer (one thread) and tensor-memory owner;
 //   warps 2-17   sixteen epilogue warps.  Warp w reads TMEM lanes
 //                32*(w%4) .. 32*(w%4)+31 (one row per thread); the four warps
@@ -30,7 +31,7 @@
 
 namespace adv {
 
-constexpr int TC_STAGES = 3;
+constexpr int TC_STAGES = 2;
 constexpr int TC_THREADS = 32 * (2 + 16 + (TC_STAGES - 1));   // producer 0, MMA, 16 epilogue, producers 1..
 
 // Diagnostic timeline of CTA 0 (clock64 stamps), compiled in only with
@@ -66,7 +67,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
     uint8_t* act[2] = {base, base + act_bytes};
     uint8_t* wst = base + 2 * act_bytes;
     const uint32_t stage_bytes = (uint32_t)a.nmax * ADV_SLAB_ROW_BYTES;   // one K slab of all N rows
-    uint64_t* bars = reinterpret_cast<uint64_t*>(wst + TC_STAGES * stage_bytes);
+    // biases of the hidden layers and the output row, staged once per CTA: the
+    // epilogue reads them with broadcast shared loads instead of global loads
+    float* bias_s = reinterpret_cast<float*>(wst + TC_STAGES * stage_bytes);   // [n_hidden + 1][nmax]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(bias_s + (a.n_hidden + 1) * a.nmax);
     uint64_t* w_full = bars;
     uint64_t* w_empty = bars + TC_STAGES;
     uint64_t* x_full = bars + 2 * TC_STAGES;
@@ -96,6 +100,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
         *abort_flag = 0;
         fence_mbar_init();
         fence_proxy_async_smem();
+    }
+    for (int i = threadIdx.x; i < (a.n_hidden + 1) * a.nmax; i += blockDim.x) {
+        const int l = i / a.nmax, c = i % a.nmax;
+        bias_s[i] = l < a.n_hidden ? (c < a.npad[l] ? a.bias[l][c] : 0.f)
+                                   : (c < a.npad[a.n_hidden - 1] ? a.w_out[c] : 0.f);
     }
     if (warp == 1) {
         tmem_alloc(tmem_holder, tmem_cols);
@@ -223,7 +232,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
             const int ns = (2 * p + 1 < n_my) ? 2 : 1;
             for (int l = 0; l < a.n_hidden && ok; ++l) {
                 const bool last = (l + 1 == a.n_hidden);
-                const float* __restrict__ bias = a.bias[l];
+                const float* bias = bias_s + l * a.nmax;
                 const int cw = a.npad[l] >> 2;              // this warp's columns: [cb, cb + cw), cw % 16 == 0
                 const int cb = j * cw;
                 for (int s = 0; s < ns; ++s) {
@@ -249,7 +258,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                         float4 bq[8];
 #pragma unroll
                         for (int q = 0; q < 8; ++q)
-                            bq[q] = (q < 4 || two) ? __ldg(reinterpret_cast<const float4*>(bias + c0) + q)
+                            bq[q] = (q < 4 || two) ? reinterpret_cast<const float4*>(bias + c0)[q]
                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
                         tmem_wait_ld();
                         const float* bf = reinterpret_cast<const float*>(bq);
@@ -274,10 +283,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                                         make_uint4(pk[0], pk[1], pk[2], pk[3]);
                                 }
                             } else {
-                                const float4* w4 = reinterpret_cast<const float4*>(a.w_out + c);
+                                const float4* w4 = reinterpret_cast<const float4*>(bias_s + a.n_hidden * a.nmax + c);
 #pragma unroll
                                 for (int u = 0; u < 4; ++u) {
-                                    const float4 wq = __ldg(w4 + u);
+                                    const float4 wq = w4[u];   // staged in shared memory
                                     const float* bb = bf + 16 * h + 4 * u;
                                     y4[0] = fmaf(fmaxf(__uint_as_float(v[4 * u + 0]) + bb[0], 0.f), wq.x, y4[0]);
                                     y4[1] = fmaf(fmaxf(__uint_as_float(v[4 * u + 1]) + bb[1], 0.f), wq.y, y4[1]);
@@ -335,9 +344,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
 }
 
 size_t mlp_tc_smem_bytes(int nslab_max, int nmax, int n_hidden) {
-    (void)n_hidden;
     return (size_t)2 * nslab_max * ADV_X_SLAB_BYTES + (size_t)TC_STAGES * nmax * ADV_SLAB_ROW_BYTES +
-           (2 * TC_STAGES + 9) * sizeof(uint64_t) + 16 + 1024;
+           (size_t)(n_hidden + 1) * nmax * sizeof(float) + (2 * TC_STAGES + 9) * sizeof(uint64_t) + 16 + 1024;
 }
 
 cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s, int ctas) {
