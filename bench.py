@@ -396,24 +396,35 @@ def large_sweep_leg(dev, reps=5, rows=0):
     out["fp32"] = {"ms": ms, "variants_per_s": n / (ms / 1000.0), "tflops": n * flop_row / (ms / 1000.0) / 1e12,
                    "max_abs_err_vs_fp64": float((y[:sample].double() - y64).abs().max().item())}
     eps32 = m.calibrate_eps(fcal, scal, "fp32")
+    eps16 = m.calibrate_eps(fcal, scal, "fp16")
     best = torch.empty(K, dtype=torch.int32, device=dev)
     bsc = torch.empty(K, dtype=torch.float64, device=dev)
-    for p in ("bf16", "fp8"):
+    ref_best = None
+    # the tiered ranking: first tier (BF16 or E4M3 layers) -> [FP16 tensor-core
+    # tier on the gathered candidates] -> FP32 -> FP64; every variant selects
+    # the same rows
+    for p, mid in (("bf16", False), ("bf16", True), ("fp8", False), ("fp8", True)):
         eps = m.calibrate_eps(fcal, scal, p)
-        m.rank(d, o, p, eps, eps32, best=best, best_score=bsc)
+        e16 = eps16 if mid else None
+        m.rank(d, o, p, eps, eps32, best=best, best_score=bsc, eps16=e16)
         torch.cuda.synchronize()
         tt = []
         for _ in range(3):
             a.record()
-            m.rank(d, o, p, eps, eps32, best=best, best_score=bsc)
+            m.rank(d, o, p, eps, eps32, best=best, best_score=bsc, eps16=e16)
             b.record()
             torch.cuda.synchronize()
             tt.append(a.elapsed_time(b))
-        c32, c64 = m.rescore_counts()
+        c16, c32, c64 = m.rescore_counts_ex()
+        if ref_best is None:
+            ref_best = best.clone()
         ms = float(np.median(tt))
-        out["rank_" + p] = {"ms": ms, "variants_per_s": n / (ms / 1000.0), "eps": eps, "eps32": eps32,
-                            "near_tie_fp32_rows": c32, "near_tie_fp64_rows": c64,
-                            "near_tie_fraction": c32 / n}
+        r = {"ms": ms, "variants_per_s": n / (ms / 1000.0), "eps": eps, "eps32": eps32,
+             "near_tie_fp32_rows": c32, "near_tie_fp64_rows": c64, "near_tie_fraction": c32 / n,
+             "same_selection_as_rank_bf16": bool(torch.equal(best, ref_best))}
+        if mid:
+            r.update({"eps16": eps16, "near_tie_fp16_rows": c16, "fp16_fraction": c16 / n})
+        out["rank_" + p + ("_fp16tier" if mid else "")] = r
     return out
 
 

@@ -240,6 +240,23 @@ advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_des
                             int32_t* d_best_local, double* d_best_score, float* d_scores,
                             uint8_t* d_row_status, cudaStream_t stream);
 
+/* advisor_rank with an FP16 tensor-core tier between the first scores and
+ * the FP32 re-score (a7 of Fig. 2's selection, made cheaper for wide models
+ * and coarse first tiers).  eps_fp16 >= 0 enables it: the tier-1 candidates
+ * are re-extracted from their descriptors into a compact FP16 image, scored
+ * on the tensor cores, and only those within 2*eps_fp16 of their kernel's
+ * FP16 minimum (and any whose FP16 value is not finite) go on to FP32.  The
+ * selection equals the FP64 argmin whenever |score - fp64| <= eps_scores,
+ * |fp16 - fp64| <= eps_fp16 and |fp32 - fp64| <= eps_fp32 hold.  Needs
+ * eps_scores >= 0 (else ADVISOR_ERR_INVALID_ARGUMENT), a 16-bit or E4M3
+ * first tier and a model the tensor-core scorers run (else
+ * ADVISOR_ERR_UNSUPPORTED).  eps_fp16 < 0: identical to advisor_rank. */
+advisor_status advisor_rank_ex(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                               const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
+                               float eps_scores, float eps_fp16, float eps_fp32, int32_t* d_best_local,
+                               double* d_best_score, float* d_scores, uint8_t* d_row_status,
+                               cudaStream_t stream);
+
 /* FP8 (E4M3) operands for models whose hidden layers run one launch per
  * layer (a hidden width above 256): per-tensor scales, scale = amax / 448.
  * Weight scales come from the exact amax of each weight matrix (computed by
@@ -327,6 +344,16 @@ advisor_status advisor_rank_topn(advisor_model_t m, const advisor_variant_desc* 
                                  int32_t* d_best_local, double* d_best_score, float* d_scores,
                                  uint8_t* d_row_status, cudaStream_t stream);
 
+/* advisor_rank_topn with the FP16 middle tier of advisor_rank_ex: t16 = the
+ * N-th smallest finite FP16 value among a kernel's tier-1 candidates (+inf
+ * if fewer than N are finite); candidates above t16 + 2*eps_fp16 are dropped
+ * before the FP32 tier.  Same argument rules as advisor_rank_ex. */
+advisor_status advisor_rank_topn_ex(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                                    const int64_t* d_seg_off, int64_t n_kernels, int32_t top_n,
+                                    advisor_precision precision, float eps_scores, float eps_fp16,
+                                    float eps_fp32, int32_t* d_best_local, double* d_best_score,
+                                    float* d_scores, uint8_t* d_row_status, cudaStream_t stream);
+
 /* a8: one training step (Sec. 3 training mode; Sec. 5 Exp. 3): forward,
  * loss = 0.5 * mean (y - label)^2 over the n_rows rows (labels: ln runtime),
  * hand-written backward, Adam update of the FP32 master weights followed by
@@ -404,6 +431,11 @@ advisor_status advisor_get_device_status(advisor_model_t m, cudaStream_t stream)
  * int64[2]).  Synchronises `stream`.  Values are undefined before the first
  * such call. */
 advisor_status advisor_get_rescore_counts(advisor_model_t m, int64_t* h_counts, cudaStream_t stream);
+
+/* As advisor_get_rescore_counts with the FP16 middle tier (host int64[3]):
+ * h_counts[0] = rows re-scored in FP16 (0 when the last selection ran
+ * without that tier), [1] = rows re-scored in FP32, [2] = in FP64. */
+advisor_status advisor_get_rescore_counts_ex(advisor_model_t m, int64_t* h_counts, cudaStream_t stream);
 
 /* Tensor-core scoring that allocates nothing: the same computation and
  * result as advisor_score_variants with ADVISOR_BF16 or ADVISOR_FP16, for

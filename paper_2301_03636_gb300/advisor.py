@@ -62,6 +62,9 @@ def lib():
         "advisor_score_variants_fp64": (st, [P, P, P, i64, P, P]),
         "advisor_select_best": (st, [P, P, i64, P, i64, P, f32, f32, P, P, P]),
         "advisor_rank": (st, [P, P, i64, P, i64, st, f32, f32, P, P, P, P, P]),
+        "advisor_rank_ex": (st, [P, P, i64, P, i64, st, f32, f32, f32, P, P, P, P, P]),
+        "advisor_rank_topn_ex": (st, [P, P, i64, P, i64, i32, st, f32, f32, f32, P, P, P, P, P]),
+        "advisor_get_rescore_counts_ex": (st, [P, P, P]),
         "advisor_train_step": (st, [P, P, P, i64, st, P, P, P]),
         "advisor_loss_grad": (st, [P, P, P, i64, st, P, P, P]),
         "advisor_get_device_status": (st, [P, P]),
@@ -280,13 +283,19 @@ class Model:
         return best, best_score
 
     def rank(self, desc, offsets, precision="bf16", eps=-1.0, eps32=0.0, scores=None, status=None, best=None,
-             best_score=None, stream=None):
+             best_score=None, stream=None, eps16=None):
+        """Best variant of every kernel (advisor_rank; with eps16, advisor_rank_ex's FP16 middle tier)."""
         K = offsets.shape[0] - 1
         best = torch.empty(K, dtype=torch.int32, device=self.device) if best is None else best
         best_score = torch.empty(K, dtype=torch.float64, device=self.device) if best_score is None else best_score
-        _check(lib().advisor_rank(self.handle, _ptr(desc), desc.shape[0], _ptr(offsets), K, _prec(precision),
-                                  float(eps), float(eps32), _ptr(best), _ptr(best_score), _ptr(scores), _ptr(status),
-                                  _stream(stream)), "advisor_rank")
+        if eps16 is None:
+            _check(lib().advisor_rank(self.handle, _ptr(desc), desc.shape[0], _ptr(offsets), K, _prec(precision),
+                                      float(eps), float(eps32), _ptr(best), _ptr(best_score), _ptr(scores),
+                                      _ptr(status), _stream(stream)), "advisor_rank")
+        else:
+            _check(lib().advisor_rank_ex(self.handle, _ptr(desc), desc.shape[0], _ptr(offsets), K, _prec(precision),
+                                         float(eps), float(eps16), float(eps32), _ptr(best), _ptr(best_score),
+                                         _ptr(scores), _ptr(status), _stream(stream)), "advisor_rank_ex")
         return best, best_score
 
     def rescore_counts(self, stream=None):
@@ -295,6 +304,13 @@ class Model:
         _check(lib().advisor_get_rescore_counts(self.handle, ctypes.cast(c, ctypes.c_void_p), _stream(stream)),
                "advisor_get_rescore_counts")
         return int(c[0]), int(c[1])
+
+    def rescore_counts_ex(self, stream=None):
+        """(rows re-scored in FP16, in FP32, in FP64) by the last selection with re-score."""
+        c = (ctypes.c_int64 * 3)()
+        _check(lib().advisor_get_rescore_counts_ex(self.handle, ctypes.cast(c, ctypes.c_void_p), _stream(stream)),
+               "advisor_get_rescore_counts_ex")
+        return int(c[0]), int(c[1]), int(c[2])
 
     @property
     def launch_config(self) -> LaunchConfig:
@@ -311,14 +327,20 @@ class Model:
         return Plan(self, desc, offsets, precision, eps, eps32, autotune, stream)
 
     def rank_topn(self, desc, offsets, top_n, precision="bf16", eps=-1.0, eps32=0.0, scores=None, status=None,
-                  stream=None):
+                  stream=None, eps16=None):
         """The top_n best variants of every kernel: (best [K][top_n] int32, score [K][top_n] float64)."""
         K = offsets.shape[0] - 1
         best = torch.empty((K, top_n), dtype=torch.int32, device=self.device)
         best_score = torch.empty((K, top_n), dtype=torch.float64, device=self.device)
-        _check(lib().advisor_rank_topn(self.handle, _ptr(desc), desc.shape[0], _ptr(offsets), K, int(top_n),
-                                       _prec(precision), float(eps), float(eps32), _ptr(best), _ptr(best_score),
-                                       _ptr(scores), _ptr(status), _stream(stream)), "advisor_rank_topn")
+        if eps16 is None:
+            _check(lib().advisor_rank_topn(self.handle, _ptr(desc), desc.shape[0], _ptr(offsets), K, int(top_n),
+                                           _prec(precision), float(eps), float(eps32), _ptr(best), _ptr(best_score),
+                                           _ptr(scores), _ptr(status), _stream(stream)), "advisor_rank_topn")
+        else:
+            _check(lib().advisor_rank_topn_ex(self.handle, _ptr(desc), desc.shape[0], _ptr(offsets), K, int(top_n),
+                                              _prec(precision), float(eps), float(eps16), float(eps32), _ptr(best),
+                                              _ptr(best_score), _ptr(scores), _ptr(status), _stream(stream)),
+                   "advisor_rank_topn_ex")
         return best, best_score
 
     def train_step(self, feat, labels, precision="fp32", lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,

@@ -21,7 +21,7 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 struct WsLayout {
     size_t x_img, h_img[2], partial, feat32, status, scores, counters, seg_state, seg_start, seg_cnt;
-    size_t cand_rows, y32, cand2_rows, y64, pos64, seg_thr;
+    size_t cand_rows, y32, cand2_rows, y64, pos64, seg_thr, y16, cand_mid_rows;
     size_t train;   // start of the training region
     size_t bytes;
 };
@@ -48,6 +48,7 @@ struct advisor_model {
     bool fp8_calibrated = false;   // activation scales stored (advisor_model_calibrate_fp8)
     int saved_fmt = 0;             // precision of the last advisor_forward_saved: 0 FP32, 1 BF16, 2 FP16
     adv::LtContext* lt = nullptr;  // cuBLASLt handle of the 16-bit training GEMMs (created on first use)
+    bool last_mid = false;         // the last re-scoring selection ran the FP16 middle tier
     ~advisor_model() { adv::lt_destroy(lt); }
 };
 
@@ -81,6 +82,8 @@ WsLayout ws_layout(const adv::ModelLayout& L, int64_t R, int64_t K, adv::TrainLa
     w.y64 = take((size_t)R * 8);
     w.pos64 = take((size_t)R * 4);
     w.seg_thr = take((size_t)K * 8);
+    w.y16 = take((size_t)R * 4);
+    w.cand_mid_rows = take((size_t)R * 8);
     w.train = o;
     const size_t tb = adv::train_layout(L, R, T);
     o = align256(o + tb);
@@ -151,7 +154,7 @@ bool use_fused(const advisor_model* m, advisor_precision p) {
 }
 
 cudaError_t launch_wide(advisor_model* m, const uint8_t* x_img, int64_t n_rows, const uint8_t* status, float* scores,
-                        int fi, cudaStream_t s);
+                        int fi, cudaStream_t s, const int* n_rows_dev = nullptr);
 
 advisor_status check_ready(const advisor_model* m, int64_t n_rows) {
     if (!m || !m->P || !m->WS || !m->params_set) return ADVISOR_ERR_INVALID_ARGUMENT;
@@ -180,10 +183,11 @@ cudaError_t launch_tc_profiled(advisor_model* m, const adv::TcArgs& a, cudaStrea
 }
 
 cudaError_t launch_wide(advisor_model* m, const uint8_t* x_img, int64_t n_rows, const uint8_t* status, float* scores,
-                        int fi, cudaStream_t s) {
+                        int fi, cudaStream_t s, const int* n_rows_dev) {
     const adv::ModelLayout& L = m->L;
     const int tiles = (int)((n_rows + ADV_TILE_M - 1) / ADV_TILE_M);
-    if (m->prof_start) {
+    const bool profiled = !n_rows_dev;   // the events bracket the first-tier scorer only
+    if (profiled && m->prof_start) {
         cudaError_t e = record_event(m->prof_start, s);
         if (e != cudaSuccess) return e;
     }
@@ -198,6 +202,7 @@ cudaError_t launch_wide(advisor_model* m, const uint8_t* x_img, int64_t n_rows, 
         a.npad = f8 ? L.npad8[l] : L.npad[l];
         a.n_chunks = (a.npad + 255) / 256;
         a.n_tiles = tiles;
+        a.n_rows_dev = n_rows_dev;
         a.bias = reinterpret_cast<const float*>(m->P + L.p_bias_off[l]);
         a.mode = l + 1 == L.n_hidden ? 1 : 0;
         a.out_img = m->WS + m->W.h_img[l & 1];
@@ -217,15 +222,52 @@ cudaError_t launch_wide(advisor_model* m, const uint8_t* x_img, int64_t n_rows, 
                                              (int64_t)tiles * ADV_TILE_M, n_rows,
                                              reinterpret_cast<const float*>(m->P + L.p_master) +
                                                  L.layer_b_off[L.n_layers - 1],
-                                             status, scores, m->num_sms, s);
-    if (e == cudaSuccess && m->prof_stop) e = record_event(m->prof_stop, s);
+                                             status, scores, m->num_sms, s, n_rows_dev);
+    if (e == cudaSuccess && profiled && m->prof_stop) e = record_event(m->prof_stop, s);
     return e;
 }
+
+// FP16 middle tier of the re-score: the tier-1 candidates (a.cand_rows,
+// count counters[0]) are re-extracted from their descriptors into a compact
+// FP16 image, scored on the tensor cores (y16, row counts read on the device)
+// and filtered by select_mid / topn_mid into a.cand_mid_rows (counters[2]).
+cudaError_t run_mid_tier(advisor_model* m, const advisor_variant_desc* desc, int64_t n_rows, adv::SelectArgs& a,
+                         bool topn, cudaStream_t s) {
+    const adv::ModelLayout& L = m->L;
+    adv::ExtractArgs x{};
+    x.desc = desc;
+    x.n_rows = n_rows;
+    x.n_rows_padded = ((n_rows + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
+    x.x_img = m->WS + m->W.x_img;
+    x.nslab = L.nslab[0];
+    x.sa = reinterpret_cast<const float*>(m->P + L.p_stdz_a);
+    x.sc = reinterpret_cast<const float*>(m->P + L.p_stdz_c);
+    x.rows = a.cand_rows;
+    x.count_dev = &a.counters[0];
+    cudaError_t e = adv::launch_extract_list(x, L.F, 2 /* FP16 image */, m->num_sms, s);
+    if (e != cudaSuccess) return e;
+    float* y16 = reinterpret_cast<float*>(m->WS + m->W.y16);
+    if (use_fused(m, ADVISOR_FP16)) {
+        adv::TcArgs t = tc_args(m, x.x_img, n_rows, nullptr, y16, 1);
+        t.n_rows_dev = &a.counters[0];
+        e = adv::launch_mlp_tc(t, m->num_sms, s, m->cfg.tc_ctas);
+    } else {
+        e = launch_wide(m, x.x_img, n_rows, nullptr, y16, 1, s, &a.counters[0]);
+    }
+    if (e != cudaSuccess) return e;
+    a.y16 = y16;
+    a.cand_mid_rows = reinterpret_cast<int64_t*>(m->WS + m->W.cand_mid_rows);
+    return topn ? adv::launch_topn_mid(a, s, m->cfg.select_block) : adv::launch_select_mid(a, s, m->cfg.select_block);
+}
+
+// The middle tier needs the descriptors (the 16-bit image is rebuilt from
+// them) and a model the tensor-core scorers run.
+bool mid_supported(const advisor_model* m) { return tc_supported(m) || wide_supported(m); }
 
 // Tiered selection; `src` supplies the rows for the re-score (features or descriptors).
 advisor_status do_select(advisor_model* m, const float* scores, int64_t n_rows, const int64_t* off, int64_t K,
                          adv::RowSrc src, bool rescore, float eps, float eps32, int32_t* best, double* best_score,
-                         cudaStream_t s) {
+                         cudaStream_t s, float eps16 = -1.f) {
     if (K > m->max_kernels) return ADVISOR_ERR_OUT_OF_MEMORY;
     adv::SelectArgs a{};
     a.scores = scores;
@@ -245,17 +287,25 @@ advisor_status do_select(advisor_model* m, const float* scores, int64_t n_rows, 
     a.cand2_rows = reinterpret_cast<int64_t*>(m->WS + m->W.cand2_rows);
     a.y64 = reinterpret_cast<double*>(m->WS + m->W.y64);
     a.status_word = status_word(m);
+    a.eps16 = eps16;
+    const bool mid = rescore && eps16 >= 0.f;
     cudaError_t e;
     if (rescore) {
-        e = cudaMemsetAsync(a.counters, 0, 2 * sizeof(int), s);
+        e = cudaMemsetAsync(a.counters, 0, 4 * sizeof(int), s);
         if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+        m->last_mid = mid;
     }
     e = adv::launch_select_tier1(a, s, m->cfg.select_block);
     if (e != cudaSuccess || !rescore) return cuda_status(e);
+    if (mid) {
+        e = run_mid_tier(m, src.desc, n_rows, a, false, s);
+        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+        a.cand_rows = a.cand_mid_rows;   // the FP32 tier takes the survivors
+    }
     const adv::MlpDesc md = mlp_desc(m);
     adv::RowSrc r1 = src;
     r1.rows = a.cand_rows;
-    r1.count_dev = &a.counters[0];
+    r1.count_dev = &a.counters[mid ? 2 : 0];
     r1.count = 0;
     e = adv::launch_mlp_fp32(md, r1, a.y32, m->num_sms, true, s, a.status_word, m->cfg.list_blocks_per_sm,
                              m->cfg.list_chunk_kb);
@@ -324,14 +374,25 @@ advisor_status advisor_model_calibrate_fp8(advisor_model_t m, const int32_t* d_f
     return ADVISOR_OK;
 }
 
-advisor_status advisor_get_rescore_counts(advisor_model_t m, int64_t* h_counts, cudaStream_t stream) {
+advisor_status advisor_get_rescore_counts_ex(advisor_model_t m, int64_t* h_counts, cudaStream_t stream) {
     if (!m || !h_counts || !m->WS) return ADVISOR_ERR_INVALID_ARGUMENT;
-    int c[2] = {0, 0};
+    int c[4] = {0, 0, 0, 0};
     if (cudaMemcpyAsync(c, m->WS + m->W.counters, sizeof(c), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
         cudaStreamSynchronize(stream) != cudaSuccess)
         return ADVISOR_ERR_CUDA;
-    h_counts[0] = c[0];
-    h_counts[1] = c[1];
+    h_counts[0] = m->last_mid ? c[0] : 0;   // FP16 tier
+    h_counts[1] = m->last_mid ? c[2] : c[0];   // FP32 tier
+    h_counts[2] = c[1];                        // FP64 tier
+    return ADVISOR_OK;
+}
+
+advisor_status advisor_get_rescore_counts(advisor_model_t m, int64_t* h_counts, cudaStream_t stream) {
+    if (!h_counts) return ADVISOR_ERR_INVALID_ARGUMENT;
+    int64_t c[3];
+    const advisor_status st = advisor_get_rescore_counts_ex(m, c, stream);
+    if (st != ADVISOR_OK) return st;
+    h_counts[0] = c[1];
+    h_counts[1] = c[2];
     return ADVISOR_OK;
 }
 
@@ -616,7 +677,7 @@ advisor_status rank_scores(advisor_model* m, const advisor_variant_desc* d_desc,
 // Top-N selection with the tiered re-score (select.cu, topn_*).
 advisor_status do_select_topn(advisor_model* m, const float* scores, int64_t n_rows, const int64_t* off, int64_t K,
                               int N, adv::RowSrc src, bool rescore, float eps, float eps32, int32_t* best,
-                              double* best_score, cudaStream_t s) {
+                              double* best_score, cudaStream_t s, float eps16 = -1.f) {
     adv::SelectArgs a{};
     a.scores = scores;
     a.n_rows = n_rows;
@@ -638,17 +699,25 @@ advisor_status do_select_topn(advisor_model* m, const float* scores, int64_t n_r
     a.top_n = N;
     a.pos64 = reinterpret_cast<int*>(m->WS + m->W.pos64);
     a.seg_thr = reinterpret_cast<double*>(m->WS + m->W.seg_thr);
+    a.eps16 = eps16;
+    const bool mid = rescore && eps16 >= 0.f;
     cudaError_t e;
     if (rescore) {
-        e = cudaMemsetAsync(a.counters, 0, 2 * sizeof(int), s);
+        e = cudaMemsetAsync(a.counters, 0, 4 * sizeof(int), s);
         if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+        m->last_mid = mid;
     }
     e = adv::launch_topn_tier1(a, s, m->cfg.select_block);
     if (e != cudaSuccess || !rescore) return cuda_status(e);
+    if (mid) {
+        e = run_mid_tier(m, src.desc, n_rows, a, true, s);
+        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+        a.cand_rows = a.cand_mid_rows;   // the FP32 tier takes the survivors
+    }
     const adv::MlpDesc md = mlp_desc(m);
     adv::RowSrc r1 = src;
     r1.rows = a.cand_rows;
-    r1.count_dev = &a.counters[0];
+    r1.count_dev = &a.counters[mid ? 2 : 0];
     r1.count = 0;
     e = adv::launch_mlp_fp32(md, r1, a.y32, m->num_sms, true, s, a.status_word, m->cfg.list_blocks_per_sm,
                              m->cfg.list_chunk_kb);
@@ -664,14 +733,11 @@ advisor_status do_select_topn(advisor_model* m, const float* scores, int64_t n_r
     return cuda_status(adv::launch_topn_final(a, s, m->cfg.select_block));
 }
 
-}  // namespace
-
-extern "C" {
-
-advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
-                            const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
-                            float eps_scores, float eps_fp32, int32_t* d_best_local, double* d_best_score,
-                            float* d_scores, uint8_t* d_row_status, cudaStream_t stream) {
+// Shared checks of the ranking calls.
+advisor_status rank_checks(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                           const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
+                           float eps_scores, float eps_fp16, float eps_fp32, const int32_t* d_best_local,
+                           const double* d_best_score) {
     if (!m || n_rows < 0 || n_kernels < 0 || !d_best_local || !d_best_score) return ADVISOR_ERR_INVALID_ARGUMENT;
     if (n_kernels == 0) return ADVISOR_OK;
     if (!d_seg_off || (n_rows > 0 && (!d_desc || !aligned(d_desc, 16)))) return ADVISOR_ERR_INVALID_ARGUMENT;
@@ -680,13 +746,59 @@ advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_des
     if (n_kernels > m->max_kernels) return ADVISOR_ERR_OUT_OF_MEMORY;
     const bool rescore = eps_scores >= 0.f;
     if (rescore && eps_fp32 < 0.f) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (eps_fp16 >= 0.f) {
+        if (!rescore) return ADVISOR_ERR_INVALID_ARGUMENT;
+        if (precision == ADVISOR_FP32 || !mid_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
+    }
+    return ADVISOR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+advisor_status advisor_rank_ex(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                               const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
+                               float eps_scores, float eps_fp16, float eps_fp32, int32_t* d_best_local,
+                               double* d_best_score, float* d_scores, uint8_t* d_row_status, cudaStream_t stream) {
+    advisor_status st = rank_checks(m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, eps_fp16,
+                                    eps_fp32, d_best_local, d_best_score);
+    if (st != ADVISOR_OK || n_kernels == 0) return st;
+    const bool rescore = eps_scores >= 0.f;
     float* scores = d_scores ? d_scores : reinterpret_cast<float*>(m->WS + m->W.scores);
     uint8_t* status = d_row_status ? d_row_status : m->WS + m->W.status;
     adv::RowSrc rs{};
     st = rank_scores(m, d_desc, n_rows, precision, scores, status, &rs, stream);
     if (st != ADVISOR_OK) return st;
     return do_select(m, scores, n_rows, d_seg_off, n_kernels, rs, rescore && n_rows > 0, eps_scores, eps_fp32,
-                     d_best_local, d_best_score, stream);
+                     d_best_local, d_best_score, stream, eps_fp16 >= 0.f ? eps_fp16 : -1.f);
+}
+
+advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                            const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
+                            float eps_scores, float eps_fp32, int32_t* d_best_local, double* d_best_score,
+                            float* d_scores, uint8_t* d_row_status, cudaStream_t stream) {
+    return advisor_rank_ex(m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, -1.f, eps_fp32,
+                           d_best_local, d_best_score, d_scores, d_row_status, stream);
+}
+
+advisor_status advisor_rank_topn_ex(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                                    const int64_t* d_seg_off, int64_t n_kernels, int32_t top_n,
+                                    advisor_precision precision, float eps_scores, float eps_fp16, float eps_fp32,
+                                    int32_t* d_best_local, double* d_best_score, float* d_scores,
+                                    uint8_t* d_row_status, cudaStream_t stream) {
+    if (top_n < 1 || top_n > ADVISOR_MAX_TOP_N) return ADVISOR_ERR_INVALID_ARGUMENT;
+    advisor_status st = rank_checks(m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, eps_fp16,
+                                    eps_fp32, d_best_local, d_best_score);
+    if (st != ADVISOR_OK || n_kernels == 0) return st;
+    const bool rescore = eps_scores >= 0.f;
+    float* scores = d_scores ? d_scores : reinterpret_cast<float*>(m->WS + m->W.scores);
+    uint8_t* status = d_row_status ? d_row_status : m->WS + m->W.status;
+    adv::RowSrc rs{};
+    st = rank_scores(m, d_desc, n_rows, precision, scores, status, &rs, stream);
+    if (st != ADVISOR_OK) return st;
+    return do_select_topn(m, scores, n_rows, d_seg_off, n_kernels, top_n, rs, rescore && n_rows > 0, eps_scores,
+                          eps_fp32, d_best_local, d_best_score, stream, eps_fp16 >= 0.f ? eps_fp16 : -1.f);
 }
 
 advisor_status advisor_rank_topn(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
@@ -694,22 +806,8 @@ advisor_status advisor_rank_topn(advisor_model_t m, const advisor_variant_desc* 
                                  advisor_precision precision, float eps_scores, float eps_fp32,
                                  int32_t* d_best_local, double* d_best_score, float* d_scores,
                                  uint8_t* d_row_status, cudaStream_t stream) {
-    if (!m || n_rows < 0 || n_kernels < 0 || !d_best_local || !d_best_score) return ADVISOR_ERR_INVALID_ARGUMENT;
-    if (top_n < 1 || top_n > ADVISOR_MAX_TOP_N) return ADVISOR_ERR_INVALID_ARGUMENT;
-    if (n_kernels == 0) return ADVISOR_OK;
-    if (!d_seg_off || (n_rows > 0 && (!d_desc || !aligned(d_desc, 16)))) return ADVISOR_ERR_INVALID_ARGUMENT;
-    advisor_status st = check_ready(m, n_rows);
-    if (st != ADVISOR_OK) return st;
-    if (n_kernels > m->max_kernels) return ADVISOR_ERR_OUT_OF_MEMORY;
-    const bool rescore = eps_scores >= 0.f;
-    if (rescore && eps_fp32 < 0.f) return ADVISOR_ERR_INVALID_ARGUMENT;
-    float* scores = d_scores ? d_scores : reinterpret_cast<float*>(m->WS + m->W.scores);
-    uint8_t* status = d_row_status ? d_row_status : m->WS + m->W.status;
-    adv::RowSrc rs{};
-    st = rank_scores(m, d_desc, n_rows, precision, scores, status, &rs, stream);
-    if (st != ADVISOR_OK) return st;
-    return do_select_topn(m, scores, n_rows, d_seg_off, n_kernels, top_n, rs, rescore && n_rows > 0, eps_scores,
-                          eps_fp32, d_best_local, d_best_score, stream);
+    return advisor_rank_topn_ex(m, d_desc, n_rows, d_seg_off, n_kernels, top_n, precision, eps_scores, -1.f,
+                                eps_fp32, d_best_local, d_best_score, d_scores, d_row_status, stream);
 }
 
 // Training precision: 0 FP32 SIMT, 1 BF16 / 2 FP16 tensor-core GEMMs; -1 unsupported.

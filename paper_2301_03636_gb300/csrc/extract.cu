@@ -139,6 +139,36 @@ __global__ void __launch_bounds__(256) extract_kernel(ExtractArgs a) {
     }
 }
 
+// Gathered extraction for the FP16 middle tier of the near-tie re-score:
+// image position p holds descriptor row rows[p] for p < n = min(*count_dev,
+// n_rows); positions n .. the next multiple of 128 are zero rows.  n is read
+// on the device (an earlier kernel wrote it), so the launch covers the
+// capacity with a grid-stride loop.  No status or int32 features are written.
+template <int F, int FMT>
+__global__ void __launch_bounds__(128) extract_list_kernel(ExtractArgs a) {
+    int64_t n = *a.count_dev;
+    n = n < 0 ? 0 : (n < a.n_rows ? n : a.n_rows);
+    const int64_t padded = (n + ADV_TILE_M - 1) / ADV_TILE_M * ADV_TILE_M;
+    const float inv_s = FMT == 3 ? 1.f / __ldg(a.x8_scale) : 1.f;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < padded;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int32_t f[F];
+        bool valid = false;
+        if (p < n) {
+            int64_t d[16];
+            load_desc(a.desc, a.rows[p], d);
+            valid = validate_row(d) == 0;
+            if (valid) row_features<F>(d, f);
+        }
+        if (!valid) {
+#pragma unroll
+            for (int j = 0; j < F; ++j) f[j] = 0;
+        }
+        if constexpr (FMT == 3) write_x_row_e4m3<F>(a.x_img, a.nslab, p, f, valid, a.sa, a.sc, inv_s);
+        else write_x_row<F, FMT>(a.x_img, a.nslab, p, f, valid, a.sa, a.sc);
+    }
+}
+
 // int32 features -> 16-bit standardised activation image.
 template <int F, int FMT>
 __global__ void __launch_bounds__(128) standardize_kernel(const int32_t* __restrict__ feat,
@@ -232,6 +262,30 @@ static cudaError_t launch_extract_f(const ExtractArgs& a, int fmt, cudaStream_t 
     else extract_kernel<F, 0><<<grid, block, 0, s>>>(a);
     adv_count_launch(1);
     return cudaGetLastError();
+}
+
+template <int F>
+static cudaError_t launch_extract_list_f(const ExtractArgs& a, int fmt, int num_sms, cudaStream_t s) {
+    const int64_t blocks = (a.n_rows + ADV_TILE_M - 1) / ADV_TILE_M;   // 128 threads per block
+    const unsigned grid = (unsigned)(blocks < 8 * num_sms ? blocks : 8 * num_sms);
+    if (grid == 0) return cudaSuccess;
+    if (fmt == 1) extract_list_kernel<F, 1><<<grid, 128, 0, s>>>(a);
+    else if (fmt == 2) extract_list_kernel<F, 2><<<grid, 128, 0, s>>>(a);
+    else if (fmt == 3) extract_list_kernel<F, 3><<<grid, 128, 0, s>>>(a);
+    else return cudaErrorInvalidValue;
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract_list(const ExtractArgs& a, int F, int fmt, int num_sms, cudaStream_t s) {
+    if (!a.rows || !a.count_dev || !a.x_img) return cudaErrorInvalidValue;
+    switch (F) {
+        case 32: return launch_extract_list_f<32>(a, fmt, num_sms, s);
+        case 33: return launch_extract_list_f<33>(a, fmt, num_sms, s);
+        case 64: return launch_extract_list_f<64>(a, fmt, num_sms, s);
+        case 128: return launch_extract_list_f<128>(a, fmt, num_sms, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_extract(const ExtractArgs& a, int F, int fmt, cudaStream_t s, int block) {

@@ -41,6 +41,10 @@ struct ExtractArgs {
     const float* sa;         // standardisation: z = f * sa - sc
     const float* sc;
     const float* x8_scale;   // E4M3 image (format 3): the first layer's activation scale (device)
+    // gathered extraction (launch_extract_list): image position p holds
+    // descriptor row rows[p] for p < min(*count_dev, n_rows)
+    const int64_t* rows;
+    const int* count_dev;
 };
 // Launch shapes of the hot path that a plan's autotuner may vary.  Every
 // choice but layer_path gives bit-identical results: rows, segments and tiles
@@ -59,6 +63,7 @@ struct LaunchConfig {
 bool launch_config_valid(const LaunchConfig& c);
 
 cudaError_t launch_extract(const ExtractArgs& a, int F, int fmt, cudaStream_t s, int block = 128);
+cudaError_t launch_extract_list(const ExtractArgs& a, int F, int fmt, int num_sms, cudaStream_t s);
 cudaError_t launch_standardize(const int32_t* feat, const uint8_t* status, int64_t n, int64_t npad, uint8_t* x_img,
                                int nslab, const float* sa, const float* sc, int F, int fmt, cudaStream_t s,
                                const float* x8_scale = nullptr);
@@ -85,6 +90,7 @@ struct TcArgs {
     int fmt;                               // 1 BF16, 0 F16 (instruction descriptor encoding)
     int64_t n_rows;
     int n_tiles;
+    const int* n_rows_dev;                 // nullable: rows = min(*n_rows_dev, n_rows), read on the device
     const uint8_t* status;                 // nullable
     float* scores;
     int* status_word;
@@ -99,7 +105,8 @@ struct LayerArgs {
     const uint8_t* w_img;     // weights: [a_slabs][npad rows][128 B] (the packed 16-bit image)
     int npad;                 // output width rounded up to 64
     int n_chunks;             // ceil(npad / 256)
-    int n_tiles;              // 128-row tiles
+    int n_tiles;              // 128-row tiles (capacity; the stride of `partial`)
+    const int* n_rows_dev;    // nullable: only the tiles of the first *n_rows_dev rows are computed
     const float* bias;        // [npad]
     int mode;                 // 0: ReLU -> out_img; 1: ReLU, dot with w_out -> partial
     uint8_t* out_img;         // mode 0: [tile][npad / 64][128 x 128 B]
@@ -114,7 +121,8 @@ struct LayerArgs {
 size_t mlp_layer_tc_smem_bytes();
 cudaError_t launch_mlp_layer_tc(const LayerArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_sum_partials(const float* partial, int n_parts, int64_t stride, int64_t n_rows, const float* b_out,
-                                const uint8_t* status, float* scores, int num_sms, cudaStream_t s);
+                                const uint8_t* status, float* scores, int num_sms, cudaStream_t s,
+                                const int* n_rows_dev = nullptr);
 size_t mlp_tc_smem_bytes(int nslab_max, int nmax, int n_hidden);
 
 // select.cu
@@ -127,7 +135,7 @@ struct SelectArgs {
     double* best_score;
     float eps;                 // < 0: plain argmin
     float eps32;
-    int* counters;             // [0] tier-1 candidates, [1] tier-2 candidates
+    int* counters;             // [0] tier-1 candidates, [1] tier-2 candidates, [2] FP16-tier survivors
     int* seg_state;
     int* seg_start;
     int* seg_cnt;
@@ -140,6 +148,11 @@ struct SelectArgs {
     int top_n;                 // N (best / best_score are [n_kernels][N])
     int* pos64;                // per FP32 candidate: its position in the FP64 list, or -1
     double* seg_thr;           // per kernel: the FP32 window bound
+    // FP16 middle tier (select_mid / topn_mid): y16[i] scores cand_rows[i];
+    // survivors go to cand_mid_rows, counted by counters[2]
+    float eps16;
+    const float* y16;
+    int64_t* cand_mid_rows;
 };
 cudaError_t launch_select_tier1(const SelectArgs& a, cudaStream_t s, int block = 256);
 cudaError_t launch_topn_tier1(const SelectArgs& a, cudaStream_t s, int block = 256);
@@ -147,6 +160,8 @@ cudaError_t launch_topn_tier2(const SelectArgs& a, cudaStream_t s, int block = 2
 cudaError_t launch_topn_final(const SelectArgs& a, cudaStream_t s, int block = 256);
 cudaError_t launch_select_tier2(const SelectArgs& a, cudaStream_t s, int block = 256);
 cudaError_t launch_select_final(const SelectArgs& a, cudaStream_t s, int block = 256);
+cudaError_t launch_select_mid(const SelectArgs& a, cudaStream_t s, int block = 256);
+cudaError_t launch_topn_mid(const SelectArgs& a, cudaStream_t s, int block = 256);
 
 // Variant generation (enumerate.cu).
 int64_t variant_count(int64_t depth);

@@ -85,7 +85,13 @@ __global__ void __launch_bounds__(LG_THREADS, 1) mlp_layer_tc_kernel(const __gri
     const uint32_t tmem = *tmem_holder;
 
     const int G = gridDim.x, b = blockIdx.x;
-    const int64_t n_items = (int64_t)a.n_tiles * a.n_chunks;
+    int64_t live_tiles = a.n_tiles;
+    if (a.n_rows_dev) {   // a gathered list whose length an earlier kernel wrote
+        const int64_t c = *a.n_rows_dev;
+        const int64_t t = c > 0 ? (c + ADV_TILE_M - 1) / ADV_TILE_M : 0;
+        live_tiles = t < live_tiles ? t : live_tiles;
+    }
+    const int64_t n_items = live_tiles * a.n_chunks;
     const int n_my = n_items > b ? (int)((n_items - b + G - 1) / G) : 0;   // items b, b+G, b+2G, ...
     const uint64_t lim = a.timeout_ns;
     const int ks = a.a_slabs;
@@ -267,7 +273,11 @@ __global__ void __launch_bounds__(LG_THREADS, 1) mlp_layer_tc_kernel(const __gri
 // scores[row] = b_out + sum over (chunk, half) of partial[chunk][half][row], in that order.
 __global__ void sum_partials_kernel(const float* __restrict__ partial, int n_parts, int64_t stride, int64_t n_rows,
                                     const float* __restrict__ b_out, const uint8_t* __restrict__ status,
-                                    float* __restrict__ scores) {
+                                    float* __restrict__ scores, const int* __restrict__ n_rows_dev) {
+    if (n_rows_dev) {
+        const int64_t c = *n_rows_dev;
+        n_rows = c < 0 ? 0 : (c < n_rows ? c : n_rows);
+    }
     for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n_rows;
          row += (int64_t)gridDim.x * blockDim.x) {
         float y = 0.f;
@@ -297,11 +307,12 @@ cudaError_t launch_mlp_layer_tc(const LayerArgs& a, int num_sms, cudaStream_t s)
 }
 
 cudaError_t launch_sum_partials(const float* partial, int n_parts, int64_t stride, int64_t n_rows, const float* b_out,
-                                const uint8_t* status, float* scores, int num_sms, cudaStream_t s) {
+                                const uint8_t* status, float* scores, int num_sms, cudaStream_t s,
+                                const int* n_rows_dev) {
     if (n_rows <= 0) return cudaSuccess;
     const int64_t blocks = (n_rows + 255) / 256;
     const int grid = (int)(blocks < 8 * num_sms ? blocks : 8 * num_sms);
-    sum_partials_kernel<<<grid, 256, 0, s>>>(partial, n_parts, stride, n_rows, b_out, status, scores);
+    sum_partials_kernel<<<grid, 256, 0, s>>>(partial, n_parts, stride, n_rows, b_out, status, scores, n_rows_dev);
     adv_count_launch(1);
     return cudaGetLastError();
 }

@@ -115,8 +115,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
+    int64_t n_rows = a.n_rows;
+    if (a.n_rows_dev) {   // a gathered list whose length an earlier kernel wrote
+        const int64_t c = *a.n_rows_dev;
+        n_rows = c < 0 ? 0 : (c < n_rows ? c : n_rows);
+    }
+    const int n_tiles = (int)((n_rows + ADV_TILE_M - 1) / ADV_TILE_M);
     const int G = gridDim.x, b = blockIdx.x;
-    const int n_my = a.n_tiles > b ? (a.n_tiles - b + G - 1) / G : 0;   // tiles b, b+G, b+2G, ...
+    const int n_my = n_tiles > b ? (n_tiles - b + G - 1) / G : 0;   // tiles b, b+G, b+2G, ...
     const int n_pairs = (n_my + 1) / 2;
     const uint64_t lim = a.timeout_ns;
 
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                                 tmem_wait_ld();
                                 y = ((y + y1) + y2) + y3 + __ldg(a.b_out);
                                 const int64_t row = (int64_t)(b + i * G) * ADV_TILE_M + r;
-                                if (row < a.n_rows) a.scores[row] = (a.status && a.status[row]) ? INFINITY : y;
+                                if (row < n_rows) a.scores[row] = (a.status && a.status[row]) ? INFINITY : y;
                             }
                         }
                         redph[s] ^= 1u;

@@ -156,6 +156,62 @@ __global__ void __launch_bounds__(256) select_tier2_kernel(SelectArgs a) {
     }
 }
 
+// FP16 middle tier (between tier 1 and the FP32 scorer): the tier-1
+// candidates were re-scored on the tensor cores with FP16 operands (y16,
+// |y16 - fp64| <= eps16).  The FP64 minimum row r* then has y16(r*) <=
+// fp64(r*) + eps16 <= fp64(r16) + eps16 <= y16(r16) + 2 eps16, r16 the FP16
+// minimum, so only candidates within 2*eps16 of that minimum go on to FP32.
+// A candidate whose FP16 value is not finite (FP16 range exceeded) cannot be
+// judged at this tier and always goes on.  Survivors are appended in
+// candidate order to cand_mid_rows; a kernel with a single survivor is
+// decided here.
+__device__ __forceinline__ bool mid_keep(float v, double thr) { return !finite_score(v) || (double)v <= thr; }
+
+__global__ void __launch_bounds__(256) select_mid_kernel(SelectArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < a.n_kernels; k += nwarps) {
+        if (a.seg_state[k] != 1) continue;
+        const int64_t lo = a.off[k];
+        const int start = a.seg_start[k], cnt = a.seg_cnt[k];
+        float bv = INFINITY;
+        int64_t br = -1;
+        for (int i = lane; i < cnt; i += 32) {
+            const float v = a.y16[start + i];
+            if (finite_score(v)) lex_min(bv, br, v, a.cand_rows[start + i]);
+        }
+        warp_lex_min(bv, br);
+        const double thr = br >= 0 ? (double)bv + 2.0 * (double)a.eps16 : (double)INFINITY;
+        int cnt2 = 0;
+        for (int i0 = 0; i0 < cnt; i0 += 32) {
+            const int i = i0 + lane;
+            cnt2 += __popc(__ballot_sync(0xffffffffu, i < cnt && mid_keep(a.y16[start + i], thr)));
+        }
+        if (cnt2 > 1) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&a.counters[2], cnt2);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            int done = 0;
+            for (int i0 = 0; i0 < cnt; i0 += 32) {
+                const int i = i0 + lane;
+                const bool take = i < cnt && mid_keep(a.y16[start + i], thr);
+                const int64_t r = take ? a.cand_rows[start + i] : 0;
+                done += append_ordered(take, r, a.cand_mid_rows, base, done);
+            }
+            if (lane == 0) {
+                a.seg_start[k] = base;
+                a.seg_cnt[k] = cnt2;
+            }
+        } else if (lane == 0) {   // the FP16 minimum is the only survivor
+            if (br >= 0) {
+                a.best[k] = (int32_t)(br - lo);
+                a.best_score[k] = (double)bv;
+            }
+            a.seg_state[k] = 0;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) select_final_kernel(SelectArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -373,6 +429,53 @@ __global__ void __launch_bounds__(256) topn_final_kernel(SelectArgs a) {
     }
 }
 
+// FP16 middle tier of the top N: t16 = the N-th smallest finite (FP16, row)
+// among a kernel's candidates (+inf if fewer than N are finite).  N
+// candidates have FP64 <= t16 + eps16, so the N-th smallest FP64 value is at
+// most that, and every FP64 top-N row has FP16 <= t16 + 2 eps16; the others
+// are dropped.  Non-finite FP16 values always go on.
+__global__ void __launch_bounds__(256) topn_mid_kernel(SelectArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int N = a.top_n;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < a.n_kernels; k += nwarps) {
+        if (a.seg_state[k] != 1) continue;
+        const int start = a.seg_start[k], cnt = a.seg_cnt[k];
+        const float* y = a.y16 + start;
+        float pv = -INFINITY;
+        int64_t pr = -1;
+        int t = 0;
+        for (; t < N; ++t) {
+            float bv;
+            int64_t br;
+            next_after(y, 0, cnt, pv, pr, bv, br);
+            if (br < 0) break;
+            pv = bv;
+            pr = br;
+        }
+        const double thr = t == N ? (double)pv + 2.0 * (double)a.eps16 : (double)INFINITY;
+        int cnt2 = 0;
+        for (int i0 = 0; i0 < cnt; i0 += 32) {
+            const int i = i0 + lane;
+            cnt2 += __popc(__ballot_sync(0xffffffffu, i < cnt && mid_keep(y[i], thr)));
+        }
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&a.counters[2], cnt2);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        int done = 0;
+        for (int i0 = 0; i0 < cnt; i0 += 32) {
+            const int i = i0 + lane;
+            const bool take = i < cnt && mid_keep(y[i], thr);
+            const int64_t r = take ? a.cand_rows[start + i] : 0;
+            done += append_ordered(take, r, a.cand_mid_rows, base, done);
+        }
+        if (lane == 0) {
+            a.seg_start[k] = base;
+            a.seg_cnt[k] = cnt2;
+        }
+    }
+}
+
 // One warp per segment; the kernels stride over segments, so any grid and
 // any whole number of warps per block covers them.
 static int select_grid(int64_t n_kernels, int block) {
@@ -398,6 +501,19 @@ cudaError_t launch_select_tier2(const SelectArgs& a, cudaStream_t s, int block) 
 cudaError_t launch_select_final(const SelectArgs& a, cudaStream_t s, int block) {
     if (!select_block_ok(block)) return cudaErrorInvalidValue;
     select_final_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_mid(const SelectArgs& a, cudaStream_t s, int block) {
+    if (!select_block_ok(block) || !a.y16 || !a.cand_mid_rows) return cudaErrorInvalidValue;
+    select_mid_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+cudaError_t launch_topn_mid(const SelectArgs& a, cudaStream_t s, int block) {
+    if (!select_block_ok(block) || !a.y16 || !a.cand_mid_rows) return cudaErrorInvalidValue;
+    topn_mid_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
     adv_count_launch(1);
     return cudaGetLastError();
 }
