@@ -17,6 +17,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -151,9 +152,42 @@ def cpu_baseline(desc, off, params, mu, sigma, min_seconds=10.0):
         el = time.perf_counter() - t0
         if el >= min_seconds:
             break
-    return {"value": rows / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"first {K} kernels ({len(sub)} variants) of the batched workload, FP64 C oracle "
-                      f"(extract + MLP + argmin), repeated for {el:.1f} s"}
+    cores = oracle.num_threads()
+    out = {"value": rows / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"first {K} kernels ({len(sub)} variants) of the batched workload, FP64 C oracle "
+                     f"(extract + MLP + argmin), repeated for {el:.1f} s"}
+    # the same oracle on one thread, over the first 128 kernels
+    K1 = min(128, K)
+    sub1 = desc[:off[K1]]
+    oracle.set_num_threads(1)
+    try:
+        rows1, t0 = 0, time.perf_counter()
+        while True:
+            oracle.rank(sub1, off[:K1 + 1], WL.widths, params, mu, sigma)
+            rows1 += len(sub1)
+            el1 = time.perf_counter() - t0
+            if el1 >= min_seconds / 2:
+                break
+    finally:
+        oracle.set_num_threads(cores)
+    out["single_thread"] = {"value": rows1 / el1, "unit": UNIT, "cores": 1,
+                            "sample": f"first {K1} kernels ({len(sub1)} variants), repeated for {el1:.1f} s"}
+    out["host"] = host_cpu()
+    return out
+
+
+def host_cpu():
+    """The host CPU the oracle ran on (nproc and lscpu's description)."""
+    info = {"nproc": os.cpu_count(), "machine": platform.machine()}
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in txt.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Vendor ID", "CPU(s)", "Thread(s) per core", "Socket(s)", "CPU max MHz"):
+                info[k.strip()] = v.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return info
 
 
 def serving_leg(dev):
@@ -428,6 +462,71 @@ def large_sweep_leg(dev, reps=5, rows=0):
     return out
 
 
+def kernel_rooflines_leg(dev, m, f, st, flush, reps=5):
+    """Rooflines of the hot path's other kernels, beside the headline's
+    tensor-core MLP: the FP32 scorer (the plain method) on the batched
+    workload against the measured FP32 FMA rate of the CUDA cores, and the
+    feature extraction and the segmented argmin at 2^26 rows (2^22 seeded
+    descriptors tiled 16 times; inputs far larger than L2) against the
+    measured HBM copy bandwidth."""
+    import torch
+
+    from paper_2301_03636_gb300 import advisor
+    hbm, _, src = peaks()
+    out = {}
+
+    def timed(fn):
+        tt = []
+        for i in range(reps + 1):
+            flush.fill_(i & 0xFF)
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record()
+            fn()
+            b_.record()
+            torch.cuda.synchronize()
+            if i:
+                tt.append(a_.elapsed_time(b_))
+        return float(np.median(tt))
+
+    fma = advisor.advisor_measure_fp32_fma_peak()
+    n = f.shape[0]
+    ms = timed(lambda: m.score(f, st, "fp32"))
+    ach = n * FLOP_PER_ROW / (ms / 1000.0) / 1e12
+    out["fp32_scorer"] = {"kernel": "adv::mlp_fp32_kernel", "rows": n, "ms": ms, "bound": "fp32 fma",
+                          "achieved": ach, "peak": fma, "unit": "TFLOP/s", "frac": ach / fma,
+                          "peak_source": "measured (advisor_measure_fp32_fma_peak)"}
+
+    rows = 1 << 26
+    base = torch.from_numpy(W.make_descriptors(1 << 22, 77)).to(dev)
+    d26 = base.repeat(16, 1)
+    del base
+    F = WL.n_features
+    ms = timed(lambda: advisor.advisor_extract_features(d26, F))
+    byt = rows * (128 + 4 * F + 1)
+    out["extract"] = {"kernel": "adv::extract_kernel (int32 features + status)", "rows": rows, "ms": ms,
+                      "bound": "alu (integer logarithms)", "algorithmic_bytes": byt,
+                      "achieved": byt / (ms / 1000.0) / 1e9, "peak": hbm, "unit": "GB/s",
+                      "frac": byt / (ms / 1000.0) / 1e9 / hbm, "peak_source": src + " HBM copy"}
+    del d26
+    torch.cuda.empty_cache()
+
+    K = rows // 34
+    off = torch.from_numpy(W.make_segments(K, 4, 64, seed=78, total=rows)).to(dev)
+    scores = torch.rand(rows, device=dev)
+    tiny = (32, 16, 1)
+    m4 = advisor.Model(tiny, max_rows=rows, max_kernels=K, device=dev)
+    m4.set_params(W.make_weights(tiny, 1), np.zeros(32), np.ones(32))
+    ms = timed(lambda: m4.select(scores, off))
+    byt = rows * 4 + K * (8 + 4 + 8)
+    out["select"] = {"kernel": "adv::select_tier1_kernel (argmin, no re-score)", "rows": rows, "kernels": K,
+                     "ms": ms, "bound": "hbm", "algorithmic_bytes": byt,
+                     "achieved": byt / (ms / 1000.0) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": byt / (ms / 1000.0) / 1e9 / hbm, "peak_source": src + " HBM copy"}
+    del m4, scores, off
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -637,6 +736,7 @@ def main():
         out["dslash"] = dslash_leg(dev)
         out["training"] = training_leg(dev)
         out["large_sweep"] = large_sweep_leg(dev)
+        out["kernel_rooflines"] = kernel_rooflines_leg(dev, m, f, st, flush)
         # the CPU oracle on the host cores (bounded sample)
         import oracle
         fc, sc = oracle.extract_features(W.calibration_descriptors(65536), WL.n_features)

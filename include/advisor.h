@@ -465,6 +465,12 @@ advisor_status advisor_score_variants_noalloc(advisor_model_t m, const int32_t* 
  * longer sequence.  Pass NULL, NULL to stop. */
 advisor_status advisor_model_set_profile_events(advisor_model_t m, void* ev_start, void* ev_stop);
 
+/* Measurement only: the FP32 FMA rate of this GPU's CUDA cores in TFLOP/s
+ * (2 FLOP per FMA), measured by a launch of independent FMA chains that
+ * fills every SM (fastest of three timed launches after one warm-up), the
+ * denominator of the FP32 scorer's roofline.  Synchronises `stream`. */
+advisor_status advisor_measure_fp32_fma_peak(double* h_tflops, cudaStream_t stream);
+
 /* Number of kernels this library launched since load (host-side counter of
  * successful launches; for launch accounting in benchmarks). */
 int64_t advisor_launch_count(void);

@@ -53,6 +53,7 @@ def lib():
         _lib.orc_mlp_loss_grad.argtypes = [P, P, i64, P, ctypes.c_int, P, P, P, P]
         _lib.orc_adam_step.argtypes = [P, P, P, P, i64, dbl, dbl, dbl, dbl, i64, P]
         _lib.orc_num_threads.restype = ctypes.c_int
+        _lib.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib.orc_select_topn.argtypes = [P, P, i64, ctypes.c_int, P, P]
         _lib.orc_rmsprop_step.argtypes = [P, P, P, i64, dbl, dbl, dbl, dbl, P]
         _lib.orc_mlp_rmse_grad.restype = dbl
@@ -74,6 +75,11 @@ def _c(a, dtype):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (timing only)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def log2_q16(x) -> np.ndarray:

@@ -65,6 +65,7 @@ def lib():
         "advisor_rank_ex": (st, [P, P, i64, P, i64, st, f32, f32, f32, P, P, P, P, P]),
         "advisor_rank_topn_ex": (st, [P, P, i64, P, i64, i32, st, f32, f32, f32, P, P, P, P, P]),
         "advisor_get_rescore_counts_ex": (st, [P, P, P]),
+        "advisor_measure_fp32_fma_peak": (st, [P, P]),
         "advisor_train_step": (st, [P, P, P, i64, st, P, P, P]),
         "advisor_loss_grad": (st, [P, P, P, i64, st, P, P, P]),
         "advisor_get_device_status": (st, [P, P]),
@@ -163,6 +164,13 @@ def advisor_extract_features(desc: torch.Tensor, n_features: int, stream=None):
     _check(lib().advisor_extract_features(_ptr(desc), n, n_features, _ptr(feat), _ptr(status), _stream(stream)),
            "advisor_extract_features")
     return feat, status
+
+
+def advisor_measure_fp32_fma_peak(stream=None) -> float:
+    """Measured FP32 FMA rate of the CUDA cores, TFLOP/s (measurement only)."""
+    v = ctypes.c_double()
+    _check(lib().advisor_measure_fp32_fma_peak(ctypes.byref(v), _stream(stream)), "advisor_measure_fp32_fma_peak")
+    return float(v.value)
 
 
 def advisor_variant_count(depth: int) -> int:
