@@ -50,57 +50,138 @@ __device__ __forceinline__ int append_ordered(bool take, int64_t r, int64_t* lis
     return __popc(m);
 }
 
+// Tier 1 of kernel k (rows lo .. hi-1, already checked) by the whole warp.
+__device__ __forceinline__ void tier1_segment_warp(const SelectArgs& a, int64_t k, int64_t lo, int64_t hi) {
+    const int lane = threadIdx.x & 31;
+    float bv = INFINITY;
+    int64_t br = -1;
+    for (int64_t r = lo + lane; r < hi; r += 32) {
+        const float v = a.scores[r];
+        if (finite_score(v)) lex_min(bv, br, v, r);
+    }
+    warp_lex_min(bv, br);
+    int state = 0;
+    if (br >= 0 && a.eps >= 0.f) {
+        const double thr = (double)bv + 2.0 * (double)a.eps;
+        int cnt = 0;
+        for (int64_t r0 = lo; r0 < hi; r0 += 32) {
+            const int64_t r = r0 + lane;
+            const bool take = r < hi && finite_score(a.scores[r]) && (double)a.scores[r] <= thr;
+            cnt += __popc(__ballot_sync(0xffffffffu, take));
+        }
+        if (cnt > 1) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&a.counters[0], cnt);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            int done = 0;
+            for (int64_t r0 = lo; r0 < hi; r0 += 32) {
+                const int64_t r = r0 + lane;
+                const bool take = r < hi && finite_score(a.scores[r]) && (double)a.scores[r] <= thr;
+                done += append_ordered(take, r, a.cand_rows, base, done);
+            }
+            if (lane == 0) {
+                a.seg_start[k] = base;
+                a.seg_cnt[k] = cnt;
+            }
+            state = 1;
+        }
+    }
+    if (lane == 0) {
+        a.best[k] = br >= 0 ? (int32_t)(br - lo) : -1;
+        a.best_score[k] = br >= 0 ? (double)bv : (double)INFINITY;
+        if (a.seg_state) a.seg_state[k] = state;
+    }
+}
+
+__device__ __forceinline__ bool bad_segment(const SelectArgs& a, int64_t lo, int64_t hi) {
+    return lo < 0 || hi < lo || hi > a.n_rows;
+}
+
+__device__ __forceinline__ void mark_bad_segment(const SelectArgs& a, int64_t k) {
+    atomicOr(a.status_word, ADV_DEV_BAD_SEGMENTS);
+    a.best[k] = -1;
+    a.best_score[k] = INFINITY;
+    if (a.seg_state) a.seg_state[k] = 0;
+}
+
+// One warp per kernel: for few kernels, where every row should have a lane.
 __global__ void __launch_bounds__(256) select_tier1_kernel(SelectArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < a.n_kernels; k += nwarps) {
         const int64_t lo = a.off[k], hi = a.off[k + 1];
-        if (lo < 0 || hi < lo || hi > a.n_rows) {
-            if (lane == 0) {
-                atomicOr(a.status_word, ADV_DEV_BAD_SEGMENTS);
-                a.best[k] = -1;
-                a.best_score[k] = INFINITY;
-                if (a.seg_state) a.seg_state[k] = 0;
-            }
+        if (bad_segment(a, lo, hi)) {
+            if (lane == 0) mark_bad_segment(a, k);
             continue;
         }
-        float bv = INFINITY;
-        int64_t br = -1;
-        for (int64_t r = lo + lane; r < hi; r += 32) {
-            const float v = a.scores[r];
-            if (finite_score(v)) lex_min(bv, br, v, r);
+        tier1_segment_warp(a, k, lo, hi);
+    }
+}
+
+// One lane per kernel: for many short kernels, where a warp per kernel
+// leaves the loads of each warp waiting one round trip after another.  A
+// warp takes 32 consecutive kernels; each lane scans its kernel's rows in
+// order (strict < keeps the lowest row on ties) and appends its candidates
+// in row order; kernels longer than TIER1_LANE_MAX rows are done afterwards
+// by the whole warp.
+constexpr int64_t TIER1_LANE_MAX = 96;
+
+__global__ void __launch_bounds__(256) select_tier1_lane_kernel(SelectArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; k0 < a.n_kernels;
+         k0 += nwarps * 32) {
+        const int64_t k = k0 + lane;
+        const bool have = k < a.n_kernels;
+        int64_t lo = 0, hi = 0;
+        if (have) {
+            lo = a.off[k];
+            hi = a.off[k + 1];
         }
-        warp_lex_min(bv, br);
-        int state = 0;
-        if (br >= 0 && a.eps >= 0.f) {
-            const double thr = (double)bv + 2.0 * (double)a.eps;
-            int cnt = 0;
-            for (int64_t r0 = lo; r0 < hi; r0 += 32) {
-                const int64_t r = r0 + lane;
-                const bool take = r < hi && finite_score(a.scores[r]) && (double)a.scores[r] <= thr;
-                cnt += __popc(__ballot_sync(0xffffffffu, take));
-            }
-            if (cnt > 1) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&a.counters[0], cnt);
-                base = __shfl_sync(0xffffffffu, base, 0);
-                int done = 0;
-                for (int64_t r0 = lo; r0 < hi; r0 += 32) {
-                    const int64_t r = r0 + lane;
-                    const bool take = r < hi && finite_score(a.scores[r]) && (double)a.scores[r] <= thr;
-                    done += append_ordered(take, r, a.cand_rows, base, done);
+        const bool bad = have && bad_segment(a, lo, hi);
+        const bool longseg = have && !bad && hi - lo > TIER1_LANE_MAX;
+        if (bad) mark_bad_segment(a, k);
+        if (have && !bad && !longseg) {
+            float bv = INFINITY;
+            int64_t br = -1;
+#pragma unroll 4
+            for (int64_t r = lo; r < hi; ++r) {
+                const float v = a.scores[r];
+                if (finite_score(v) && (br < 0 || v < bv)) {
+                    bv = v;
+                    br = r;
                 }
-                if (lane == 0) {
+            }
+            int state = 0;
+            if (br >= 0 && a.eps >= 0.f) {
+                const double thr = (double)bv + 2.0 * (double)a.eps;
+                int cnt = 0;
+                for (int64_t r = lo; r < hi; ++r) {
+                    const float v = a.scores[r];
+                    cnt += (finite_score(v) && (double)v <= thr) ? 1 : 0;
+                }
+                if (cnt > 1) {
+                    const int base = atomicAdd(&a.counters[0], cnt);
+                    int done = 0;
+                    for (int64_t r = lo; r < hi; ++r) {
+                        const float v = a.scores[r];
+                        if (finite_score(v) && (double)v <= thr) a.cand_rows[base + done++] = r;
+                    }
                     a.seg_start[k] = base;
                     a.seg_cnt[k] = cnt;
+                    state = 1;
                 }
-                state = 1;
             }
-        }
-        if (lane == 0) {
             a.best[k] = br >= 0 ? (int32_t)(br - lo) : -1;
             a.best_score[k] = br >= 0 ? (double)bv : (double)INFINITY;
             if (a.seg_state) a.seg_state[k] = state;
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, longseg);
+        while (todo) {
+            const int j = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t kj = k0 + j;
+            tier1_segment_warp(a, kj, __shfl_sync(0xffffffffu, lo, j), __shfl_sync(0xffffffffu, hi, j));
         }
     }
 }
@@ -486,9 +567,15 @@ static int select_grid(int64_t n_kernels, int block) {
 
 static bool select_block_ok(int block) { return block == 128 || block == 256; }
 
+// Kernels per launch from which tier 1 gives each kernel a lane instead of a warp.
+constexpr int64_t TIER1_LANE_FROM = 32768;
+
 cudaError_t launch_select_tier1(const SelectArgs& a, cudaStream_t s, int block) {
     if (!select_block_ok(block)) return cudaErrorInvalidValue;
-    select_tier1_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
+    if (a.n_kernels >= TIER1_LANE_FROM)
+        select_tier1_lane_kernel<<<select_grid((a.n_kernels + 31) / 32, block), block, 0, s>>>(a);
+    else
+        select_tier1_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
     adv_count_launch(1);
     return cudaGetLastError();
 }

@@ -1,7 +1,10 @@
 """Measurement helpers behind the benchmark's rooflines: the measured FP32
 FMA rate of the CUDA cores is plausible for the part (152 SMs x 128 FP32
 lanes at 1-2.1 GHz: 39-82 TFLOP/s), and the argmin that the benchmark times
-at 2^26 rows is the plain segmented argmin (lowest index on ties)."""
+at 2^26 rows is the plain segmented argmin (lowest index on ties).  Many
+kernels (>= 32,768) take the lane-per-kernel form of the first selection
+tier; its selections, with and without the near-tie re-score, must equal
+the oracle's (Fig. 2: the best variant per kernel)."""
 import numpy as np
 import pytest
 import torch
@@ -20,7 +23,7 @@ def test_fp32_fma_peak_plausible(gpu_lib):
 
 
 def test_select_without_rescore_is_segmented_argmin(gpu_lib):
-    rows, K = 1 << 20, (1 << 20) // 34
+    rows, K = 1 << 21, (1 << 21) // 34
     off = W.make_segments(K, 4, 64, seed=78, total=rows)
     g = torch.Generator().manual_seed(3)
     s = torch.randint(0, 1000, (rows,), generator=g).float()   # many exact ties
@@ -31,3 +34,45 @@ def test_select_without_rescore_is_segmented_argmin(gpu_lib):
     ref = np.array([int(np.argmin(sn[off[k]:off[k + 1]])) for k in range(K)])   # first minimum
     assert np.array_equal(best.cpu().numpy(), ref)
     assert np.array_equal(score.cpu().numpy(), np.array([sn[off[k] + ref[k]] for k in range(K)]))
+
+
+def test_many_kernels_lane_form_identical_to_oracle(gpu_lib):
+    """40,000 kernels of 0..40 variants, every 97th kernel 150 variants (the
+    whole-warp fallback for long kernels), invalid rows: rank with the
+    re-score (and with the FP16 tier) against the FP64 oracle."""
+    import oracle
+    widths = (32, 128, 128, 1)
+    K = 40000
+    rng = np.random.default_rng(41)
+    counts = rng.integers(0, 41, size=K)
+    counts[::97] = 150
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    n = int(off[-1])
+    d = W.make_descriptors(n, 41)
+    d[::89, 5] = 0   # invalid rows (work 0)
+    cal = W.calibration_descriptors(16384)
+    fc, sc = oracle.extract_features(cal, 32)
+    mu, sigma = oracle.fit_standardizer(fc, sc)
+    p = W.make_weights(widths, 41)
+    ref, _, y_ref, _, _ = oracle.rank(d, off, widths, p, mu, sigma)
+    m = advisor.Model(widths, max_rows=n, max_kernels=K)
+    m.set_params(p, mu, sigma)
+    fcal, scal = advisor.advisor_extract_features(torch.from_numpy(cal).cuda(), 32)
+    eps = {q: m.calibrate_eps(fcal, scal, q) for q in ("bf16", "fp16", "fp32")}
+    dt, ot = torch.from_numpy(d).cuda(), torch.from_numpy(off).cuda()
+    b, _ = m.rank(dt, ot, "bf16", eps=eps["bf16"], eps32=eps["fp32"])
+    assert np.array_equal(b.cpu().numpy(), ref)
+    b16, _ = m.rank(dt, ot, "bf16", eps=eps["bf16"], eps32=eps["fp32"], eps16=eps["fp16"])
+    assert np.array_equal(b16.cpu().numpy(), ref)
+    # without re-score: the argmin of the BF16 scores themselves (first minimum, never +inf)
+    scores = torch.empty(n, dtype=torch.float32, device="cuda")
+    b0, s0 = m.rank(dt, ot, "bf16", scores=scores)
+    y = scores.cpu().numpy()
+    exp = np.full(K, -1)
+    for k in range(K):
+        seg = y[off[k]:off[k + 1]]
+        if len(seg) and np.isfinite(seg).any():
+            exp[k] = int(np.argmin(np.where(np.isfinite(seg), seg, np.inf)))
+    assert np.array_equal(b0.cpu().numpy(), exp)
+    assert (exp[counts == 0] == -1).all()
+    assert m.device_status() == 0
