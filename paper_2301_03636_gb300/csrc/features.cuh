@@ -77,7 +77,12 @@ __device__ __forceinline__ uint32_t validate_row(const int64_t (&d)[16]) {
 
 // Binary logarithms of N values at once: the same digit-by-digit method as
 // log2_q16, with the N squaring chains advanced in lockstep so that their
-// multiplies overlap instead of waiting on each other.
+// multiplies overlap instead of waiting on each other.  Each step is written
+// without a select: with s = 31 + bit, the next mantissa is the square
+// shifted right by s (bit = 1: its high word; bit = 0: bits 31..62), and the
+// fraction collects s instead of bit, i.e. 31 extra per step, 31 * (2^16 - 1)
+// in all, taken off at the end.  This moves work from the integer ALU pipe
+// to the multiply-add pipe.
 template <int N>
 __device__ __forceinline__ void log2_q16_batch(const uint64_t (&x)[N], int32_t (&out)[N]) {
     uint32_t m[N], acc[N];
@@ -93,14 +98,13 @@ __device__ __forceinline__ void log2_q16_batch(const uint64_t (&x)[N], int32_t (
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             const uint64_t sq = (uint64_t)m[i] * (uint64_t)m[i];
-            const uint32_t hi = (uint32_t)(sq >> 32);
-            const uint32_t bit = hi >> 31;
-            m[i] = bit ? hi : (uint32_t)(sq >> 31);
-            acc[i] = (acc[i] << 1) | bit;
+            const uint32_t s = __umulhi((uint32_t)(sq >> 32), 2u) + 31u;   // 31 + (m^2 >= 2)
+            m[i] = (uint32_t)(sq >> s);
+            acc[i] = acc[i] * 2u + s;
         }
     }
 #pragma unroll
-    for (int i = 0; i < N; ++i) out[i] = (int32_t)acc[i];
+    for (int i = 0; i < N; ++i) out[i] = (int32_t)(acc[i] - 31u * 65535u);
 }
 
 // Number of logarithms behind the F features of a row: 19 for the 32 base
