@@ -267,7 +267,7 @@ bool mid_supported(const advisor_model* m) { return tc_supported(m) || wide_supp
 // Tiered selection; `src` supplies the rows for the re-score (features or descriptors).
 advisor_status do_select(advisor_model* m, const float* scores, int64_t n_rows, const int64_t* off, int64_t K,
                          adv::RowSrc src, bool rescore, float eps, float eps32, int32_t* best, double* best_score,
-                         cudaStream_t s, float eps16 = -1.f) {
+                         cudaStream_t s, float eps16 = -1.f, bool counters_zeroed = false) {
     if (K > m->max_kernels) return ADVISOR_ERR_OUT_OF_MEMORY;
     adv::SelectArgs a{};
     a.scores = scores;
@@ -291,8 +291,10 @@ advisor_status do_select(advisor_model* m, const float* scores, int64_t n_rows, 
     const bool mid = rescore && eps16 >= 0.f;
     cudaError_t e;
     if (rescore) {
-        e = cudaMemsetAsync(a.counters, 0, 4 * sizeof(int), s);
-        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+        if (!counters_zeroed) {
+            e = cudaMemsetAsync(a.counters, 0, 4 * sizeof(int), s);
+            if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+        }
         m->last_mid = mid;
     }
     e = adv::launch_select_tier1(a, s, m->cfg.select_block);
@@ -677,7 +679,8 @@ advisor_status rank_scores(advisor_model* m, const advisor_variant_desc* d_desc,
 // Top-N selection with the tiered re-score (select.cu, topn_*).
 advisor_status do_select_topn(advisor_model* m, const float* scores, int64_t n_rows, const int64_t* off, int64_t K,
                               int N, adv::RowSrc src, bool rescore, float eps, float eps32, int32_t* best,
-                              double* best_score, cudaStream_t s, float eps16 = -1.f) {
+                              double* best_score, cudaStream_t s, float eps16 = -1.f,
+                              bool counters_zeroed = false) {
     adv::SelectArgs a{};
     a.scores = scores;
     a.n_rows = n_rows;
@@ -703,8 +706,10 @@ advisor_status do_select_topn(advisor_model* m, const float* scores, int64_t n_r
     const bool mid = rescore && eps16 >= 0.f;
     cudaError_t e;
     if (rescore) {
-        e = cudaMemsetAsync(a.counters, 0, 4 * sizeof(int), s);
-        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+        if (!counters_zeroed) {
+            e = cudaMemsetAsync(a.counters, 0, 4 * sizeof(int), s);
+            if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+        }
         m->last_mid = mid;
     }
     e = adv::launch_topn_tier1(a, s, m->cfg.select_block);
@@ -767,11 +772,14 @@ advisor_status advisor_rank_ex(advisor_model_t m, const advisor_variant_desc* d_
     const bool rescore = eps_scores >= 0.f;
     float* scores = d_scores ? d_scores : reinterpret_cast<float*>(m->WS + m->W.scores);
     uint8_t* status = d_row_status ? d_row_status : m->WS + m->W.status;
+    const bool zeroed = rescore && n_rows > 0;   // zeroed ahead, so that the kernels of the chain follow one another
+    if (zeroed && cudaMemsetAsync(m->WS + m->W.counters, 0, 4 * sizeof(int), stream) != cudaSuccess)
+        return ADVISOR_ERR_CUDA;
     adv::RowSrc rs{};
     st = rank_scores(m, d_desc, n_rows, precision, scores, status, &rs, stream);
     if (st != ADVISOR_OK) return st;
     return do_select(m, scores, n_rows, d_seg_off, n_kernels, rs, rescore && n_rows > 0, eps_scores, eps_fp32,
-                     d_best_local, d_best_score, stream, eps_fp16 >= 0.f ? eps_fp16 : -1.f);
+                     d_best_local, d_best_score, stream, eps_fp16 >= 0.f ? eps_fp16 : -1.f, zeroed);
 }
 
 advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
@@ -794,11 +802,14 @@ advisor_status advisor_rank_topn_ex(advisor_model_t m, const advisor_variant_des
     const bool rescore = eps_scores >= 0.f;
     float* scores = d_scores ? d_scores : reinterpret_cast<float*>(m->WS + m->W.scores);
     uint8_t* status = d_row_status ? d_row_status : m->WS + m->W.status;
+    const bool zeroed = rescore && n_rows > 0;
+    if (zeroed && cudaMemsetAsync(m->WS + m->W.counters, 0, 4 * sizeof(int), stream) != cudaSuccess)
+        return ADVISOR_ERR_CUDA;
     adv::RowSrc rs{};
     st = rank_scores(m, d_desc, n_rows, precision, scores, status, &rs, stream);
     if (st != ADVISOR_OK) return st;
     return do_select_topn(m, scores, n_rows, d_seg_off, n_kernels, top_n, rs, rescore && n_rows > 0, eps_scores,
-                          eps_fp32, d_best_local, d_best_score, stream, eps_fp16 >= 0.f ? eps_fp16 : -1.f);
+                          eps_fp32, d_best_local, d_best_score, stream, eps_fp16 >= 0.f ? eps_fp16 : -1.f, zeroed);
 }
 
 advisor_status advisor_rank_topn(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cstddef>
+#include <utility>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -250,6 +251,36 @@ __host__ __device__ __forceinline__ uint32_t f16_idesc(uint32_t fmt, uint32_t M,
 // 128B-swizzled slab whose rows are 128 bytes (1024-byte aligned atoms).
 __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t chunk) {
     return row * 128u + ((chunk ^ (row & 7u)) << 4);
+}
+
+}  // namespace adv
+
+// Programmatic dependent launch along the ranking chain (extract -> scorer
+// -> selection tiers): a kernel launched with launch_pdl may be started while
+// the kernel before it in the stream is still running; it calls
+// griddep_wait() before it reads anything an earlier kernel wrote (the wait
+// returns once the preceding grid has completed and its writes are
+// visible), then griddep_trigger() so that the next kernel of the chain can
+// be launched in turn.  Both are no-ops for a kernel launched normally.
+namespace adv {
+
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 }  // namespace adv

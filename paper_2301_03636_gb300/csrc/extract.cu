@@ -102,6 +102,8 @@ __device__ __forceinline__ void write_x_row(uint8_t* x_img, int nslab, int64_t r
 
 template <int F, int FMT>
 __global__ void __launch_bounds__(256) extract_kernel(ExtractArgs a) {
+    griddep_wait();
+    griddep_trigger();
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= a.n_rows_padded) return;
     int32_t f[F];
@@ -256,10 +258,10 @@ static cudaError_t launch_extract_f(const ExtractArgs& a, int fmt, cudaStream_t 
     const int64_t rows = a.n_rows_padded;
     const unsigned grid = (unsigned)((rows + block - 1) / block);
     if (grid == 0) return cudaSuccess;
-    if (fmt == 1) extract_kernel<F, 1><<<grid, block, 0, s>>>(a);
-    else if (fmt == 2) extract_kernel<F, 2><<<grid, block, 0, s>>>(a);
-    else if (fmt == 3) extract_kernel<F, 3><<<grid, block, 0, s>>>(a);
-    else extract_kernel<F, 0><<<grid, block, 0, s>>>(a);
+    auto k = fmt == 1 ? extract_kernel<F, 1> : fmt == 2 ? extract_kernel<F, 2> : fmt == 3 ? extract_kernel<F, 3>
+                                                                                   : extract_kernel<F, 0>;
+    const cudaError_t e = launch_pdl(k, dim3(grid), dim3(block), 0, s, a);
+    if (e != cudaSuccess) return e;
     adv_count_launch(1);
     return cudaGetLastError();
 }

@@ -209,6 +209,8 @@ __global__ void __launch_bounds__(256, 1) mlp_fp32_list_kernel(MlpDesc m, RowSrc
     __shared__ int row_ok[RB];
     __shared__ int abort_s;
     const int tid = threadIdx.x;
+    griddep_wait();   // the candidate list and its count come from the selection kernel before
+    griddep_trigger();
     const int64_t count = src.count_dev ? (int64_t)*src.count_dev : src.count;
     const int64_t ntiles = (count + RB - 1) / RB;
     const int nh = m.nw - 2;
@@ -342,6 +344,8 @@ __global__ void __launch_bounds__(256) mlp_fp64_kernel(MlpDesc m, RowSrc src, do
     double* h1 = h0 + wmax;
     __shared__ int32_t fs[F];
     __shared__ int okf;
+    griddep_wait();
+    griddep_trigger();
     const int64_t count = src.count_dev ? (int64_t)*src.count_dev : src.count;
     for (int64_t pos = blockIdx.x; pos < count; pos += gridDim.x) {
         __syncthreads();
@@ -430,7 +434,8 @@ static cudaError_t launch_fp32_list_t(const MlpDesc& m, const RowSrc& src, float
     if (wmax4 > 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, 256, smem, s>>>(m, src, out, wmax4, kc, stages, status_word);
+    e = launch_pdl(k, dim3(grid), dim3(256), smem, s, m, src, out, wmax4, kc, stages, status_word);
+    if (e != cudaSuccess) return e;
     adv_count_launch(1);
     return cudaGetLastError();
 }
@@ -483,7 +488,8 @@ static cudaError_t launch_fp64_t(const MlpDesc& m, const RowSrc& src, double* ou
     auto k = mlp_fp64_kernel<F, FD>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, 256, smem, s>>>(m, src, out, wmax);
+    e = launch_pdl(k, dim3(grid), dim3(256), smem, s, m, src, out, wmax);
+    if (e != cudaSuccess) return e;
     adv_count_launch(1);
     return cudaGetLastError();
 }

@@ -115,6 +115,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
+    griddep_wait();   // the activation image (and a gathered row count) come from the kernel before
+    griddep_trigger();
     int64_t n_rows = a.n_rows;
     if (a.n_rows_dev) {   // a gathered list whose length an earlier kernel wrote
         const int64_t c = *a.n_rows_dev;
@@ -364,7 +366,8 @@ cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s, int ctas
     if (e != cudaSuccess) return e;
     const int cap = (ctas > 0 && ctas < num_sms) ? ctas : num_sms;   // at most one resident CTA per SM
     const int grid = a.n_tiles < cap ? a.n_tiles : cap;
-    kern<<<grid, TC_THREADS, smem, s>>>(a);
+    e = launch_pdl(kern, dim3(grid), dim3(TC_THREADS), smem, s, a);
+    if (e != cudaSuccess) return e;
     adv_count_launch(1);
     return cudaGetLastError();
 }

@@ -106,6 +106,8 @@ __device__ __forceinline__ void mark_bad_segment(const SelectArgs& a, int64_t k)
 
 // One warp per kernel: for few kernels, where every row should have a lane.
 __global__ void __launch_bounds__(256) select_tier1_kernel(SelectArgs a) {
+    griddep_wait();
+    griddep_trigger();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < a.n_kernels; k += nwarps) {
@@ -127,6 +129,8 @@ __global__ void __launch_bounds__(256) select_tier1_kernel(SelectArgs a) {
 constexpr int64_t TIER1_LANE_MAX = 96;
 
 __global__ void __launch_bounds__(256) select_tier1_lane_kernel(SelectArgs a) {
+    griddep_wait();
+    griddep_trigger();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t k0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; k0 < a.n_kernels;
@@ -187,6 +191,8 @@ __global__ void __launch_bounds__(256) select_tier1_lane_kernel(SelectArgs a) {
 }
 
 __global__ void __launch_bounds__(256) select_tier2_kernel(SelectArgs a) {
+    griddep_wait();
+    griddep_trigger();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < a.n_kernels; k += nwarps) {
@@ -294,6 +300,8 @@ __global__ void __launch_bounds__(256) select_mid_kernel(SelectArgs a) {
 }
 
 __global__ void __launch_bounds__(256) select_final_kernel(SelectArgs a) {
+    griddep_wait();
+    griddep_trigger();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < a.n_kernels; k += nwarps) {
@@ -567,29 +575,28 @@ static int select_grid(int64_t n_kernels, int block) {
 
 static bool select_block_ok(int block) { return block == 128 || block == 256; }
 
+static cudaError_t counted(cudaError_t e) {
+    if (e == cudaSuccess) adv_count_launch(1);
+    return e;
+}
+
 // Kernels per launch from which tier 1 gives each kernel a lane instead of a warp.
 constexpr int64_t TIER1_LANE_FROM = 32768;
 
 cudaError_t launch_select_tier1(const SelectArgs& a, cudaStream_t s, int block) {
     if (!select_block_ok(block)) return cudaErrorInvalidValue;
     if (a.n_kernels >= TIER1_LANE_FROM)
-        select_tier1_lane_kernel<<<select_grid((a.n_kernels + 31) / 32, block), block, 0, s>>>(a);
-    else
-        select_tier1_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
-    adv_count_launch(1);
-    return cudaGetLastError();
+        return counted(launch_pdl(select_tier1_lane_kernel, dim3(select_grid((a.n_kernels + 31) / 32, block)),
+                                  dim3(block), 0, s, a));
+    return counted(launch_pdl(select_tier1_kernel, dim3(select_grid(a.n_kernels, block)), dim3(block), 0, s, a));
 }
 cudaError_t launch_select_tier2(const SelectArgs& a, cudaStream_t s, int block) {
     if (!select_block_ok(block)) return cudaErrorInvalidValue;
-    select_tier2_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
-    adv_count_launch(1);
-    return cudaGetLastError();
+    return counted(launch_pdl(select_tier2_kernel, dim3(select_grid(a.n_kernels, block)), dim3(block), 0, s, a));
 }
 cudaError_t launch_select_final(const SelectArgs& a, cudaStream_t s, int block) {
     if (!select_block_ok(block)) return cudaErrorInvalidValue;
-    select_final_kernel<<<select_grid(a.n_kernels, block), block, 0, s>>>(a);
-    adv_count_launch(1);
-    return cudaGetLastError();
+    return counted(launch_pdl(select_final_kernel, dim3(select_grid(a.n_kernels, block)), dim3(block), 0, s, a));
 }
 
 cudaError_t launch_select_mid(const SelectArgs& a, cudaStream_t s, int block) {
