@@ -233,7 +233,14 @@ advisor_status advisor_select_best(advisor_model_t m, const float* d_scores, int
  * features of the tensor-core path going straight to 16-bit standardised
  * activations.  d_scores and d_row_status are optional outputs (nullable).
  * Near-tie re-score as in advisor_select_best (recomputes the features of the
- * candidate rows from their descriptors); eps_scores < 0 disables it. */
+ * candidate rows from their descriptors); eps_scores < 0 disables it.
+ * d_desc may also point to page-locked host memory (cudaHostAlloc /
+ * cudaHostRegister, accessible from the device through unified addressing):
+ * the kernels then read the descriptors over the CPU-GPU link while they
+ * compute, instead of the caller copying them first; the host must not
+ * change them until the call has completed on `stream`.  Any other pointer
+ * the device cannot read (e.g. pageable host memory) returns
+ * ADVISOR_ERR_INVALID_ARGUMENT. */
 advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
                             const int64_t* d_seg_off, int64_t n_kernels,
                             advisor_precision precision, float eps_scores, float eps_fp32,

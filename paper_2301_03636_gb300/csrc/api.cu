@@ -738,6 +738,18 @@ advisor_status do_select_topn(advisor_model* m, const float* scores, int64_t n_r
     return cuda_status(adv::launch_topn_final(a, s, m->cfg.select_block));
 }
 
+// Whether the device can read `p` directly: device or managed memory, or
+// page-locked host memory mapped into the unified address space.
+bool device_readable(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the error state this query leaves behind
+        return false;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeHost && at.devicePointer == p;
+}
+
 // Shared checks of the ranking calls.
 advisor_status rank_checks(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
                            const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
@@ -745,7 +757,8 @@ advisor_status rank_checks(advisor_model_t m, const advisor_variant_desc* d_desc
                            const double* d_best_score) {
     if (!m || n_rows < 0 || n_kernels < 0 || !d_best_local || !d_best_score) return ADVISOR_ERR_INVALID_ARGUMENT;
     if (n_kernels == 0) return ADVISOR_OK;
-    if (!d_seg_off || (n_rows > 0 && (!d_desc || !aligned(d_desc, 16)))) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (!d_seg_off || (n_rows > 0 && (!d_desc || !aligned(d_desc, 16) || !device_readable(d_desc))))
+        return ADVISOR_ERR_INVALID_ARGUMENT;
     advisor_status st = check_ready(m, n_rows);
     if (st != ADVISOR_OK) return st;
     if (n_kernels > m->max_kernels) return ADVISOR_ERR_OUT_OF_MEMORY;

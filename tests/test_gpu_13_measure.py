@@ -76,3 +76,36 @@ def test_many_kernels_lane_form_identical_to_oracle(gpu_lib):
     assert np.array_equal(b0.cpu().numpy(), exp)
     assert (exp[counts == 0] == -1).all()
     assert m.device_status() == 0
+
+
+def test_descriptors_in_pinned_host_memory(gpu_lib):
+    """advisor_rank and a plan reading the descriptors straight from
+    page-locked host memory give the same selections as from device memory."""
+    widths = (64, 256, 256, 256, 1)
+    off = W.make_segments(300, 4, 64, seed=31)
+    n = int(off[-1])
+    d = W.make_descriptors(n, 31)
+    m = advisor.Model(widths, max_rows=n, max_kernels=300)
+    m.set_params(W.make_weights(widths, 31), np.zeros(64), np.full(64, 8.0))
+    dd, ot = torch.from_numpy(d).cuda(), torch.from_numpy(off).cuda()
+    dh = torch.from_numpy(d).pin_memory()
+    for eps in (-1.0, 0.05):
+        b_dev, s_dev = m.rank(dd, ot, "bf16", eps=eps, eps32=1e-4)
+        b_host, s_host = m.rank(dh, ot, "bf16", eps=eps, eps32=1e-4)
+        assert torch.equal(b_dev, b_host) and torch.equal(s_dev, s_host)
+    plan = m.plan_rank(dh, ot, "bf16", 0.05, 1e-4)
+    b_plan, s_plan = plan.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(b_plan, b_dev) and torch.equal(s_plan, s_dev)
+
+
+def test_pageable_host_descriptors_rejected(gpu_lib):
+    """A pointer the device cannot read is refused before any launch."""
+    widths = (32, 16, 1)
+    m = advisor.Model(widths, max_rows=64, max_kernels=1)
+    m.set_params(W.make_weights(widths, 1), np.zeros(32), np.ones(32))
+    d = torch.from_numpy(W.make_descriptors(64, 1))          # ordinary (pageable) host memory
+    o = torch.tensor([0, 64], dtype=torch.int64, device="cuda")
+    with pytest.raises(advisor.AdvisorError) as e:
+        m.rank(d, o, "bf16")
+    assert e.value.code == 1
