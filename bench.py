@@ -694,17 +694,38 @@ def main():
         best_h.copy_(plan_h.best, non_blocking=True)
         bs_h.copy_(plan_h.best_score, non_blocking=True)
 
-    ms_copy = time_e2e(e2e_copy_step)
-    ms_host = time_e2e(e2e_host_step)
+    # the copy split over four streams (several copy engines at once)
+    side = [torch.cuda.Stream(dev) for _ in range(4)]
+    bounds = np.linspace(0, n, len(side) + 1).astype(np.int64)
+
+    def e2e_split_step():
+        ready = torch.cuda.Event()
+        ready.record(stream)
+        done = []
+        for i, st_ in enumerate(side):
+            st_.wait_event(ready)
+            with torch.cuda.stream(st_):
+                desc[bounds[i]:bounds[i + 1]].copy_(desc_h[bounds[i]:bounds[i + 1]], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(st_)
+            done.append(ev)
+        offs.copy_(off_h, non_blocking=True)
+        for ev in done:
+            stream.wait_event(ev)
+        plan.launch()
+        best_h.copy_(plan.best, non_blocking=True)
+        bs_h.copy_(plan.best_score, non_blocking=True)
+
+    modes = {"descriptors and offsets copied from pinned host memory": time_e2e(e2e_copy_step),
+             "descriptors copied in four concurrent chunks, offsets copied": time_e2e(e2e_split_step),
+             "descriptors read by the kernels from pinned host memory, offsets copied": time_e2e(e2e_host_step)}
     same = bool(torch.equal(plan_h.best, plan.best))
-    ms_e2e = min(ms_copy, ms_host)
+    mode = min(modes, key=modes.get)
+    ms_e2e = modes[mode]
     e2e = {"value": n * world / (ms_e2e / 1000.0), "unit": UNIT,
            "h2d_bytes_per_step": int(desc_h.numel() * 8 + off_h.numel() * 8),
-           "d2h_bytes_per_step": int(K * 4 + K * 8),
-           "mode": ("descriptors read by the kernels from pinned host memory, offsets copied" if ms_host <= ms_copy
-                    else "descriptors and offsets copied from pinned host memory"),
-           "ms_per_step": ms_e2e, "copy_in_ms_per_step": ms_copy, "host_read_ms_per_step": ms_host,
-           "same_selection": same}
+           "d2h_bytes_per_step": int(K * 4 + K * 8), "mode": mode, "ms_per_step": ms_e2e,
+           "ms_per_step_by_mode": modes, "same_selection": same}
 
     # ---- roofline of the dominant kernel (the tensor-core MLP) ----
     hbm, tf, src = peaks()

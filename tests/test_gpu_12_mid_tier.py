@@ -4,6 +4,8 @@ FP16 image and scored on the tensor cores before the FP32 tier.  Selections
 (Fig. 2: the best variant, or the top N, per kernel) must stay identical to
 the FP64 oracle's; the FP16 tier sees exactly the tier-1 candidates and
 passes on no more rows than it received."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -149,7 +151,8 @@ def test_mid_tier_argument_rules(gpu_lib, narrow):
 def test_large_sweep_fp8_mid_tier_full_size_sampled(gpu_lib):
     """The large sweep at full size (2^20 variants of 65,536 kernels) in the
     benchmark's tiered configuration (E4M3 layers, FP16 middle tier, FP32,
-    FP64): the oracle re-ranks a seeded sample of 256 kernels."""
+    FP64): all 65,536 selections against the oracle's stored ones, and the
+    oracle re-ranks a seeded sample of 256 kernels."""
     wl = W.LARGE_SWEEP
     off = wl.offsets()
     n, K = int(off[-1]), wl.n_kernels
@@ -169,6 +172,8 @@ def test_large_sweep_fp8_mid_tier_full_size_sampled(gpu_lib):
     c16, c32, c64 = m.rescore_counts_ex()
     print(f"near-tie rows: FP16 {c16} ({c16 / n:.3f}), FP32 {c32} ({c32 / n:.4f}), FP64 {c64}")
     assert c32 < c16
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "large_sweep_best.npy")
+    assert np.array_equal(b, np.load(golden).astype(np.int32))   # every kernel, against the oracle's answers
     ks = np.sort(np.random.default_rng(12).choice(K, 256, replace=False))
     rows = [d[off[k]:off[k + 1]] for k in ks]
     sub_off = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)

@@ -3,6 +3,8 @@ sweep's 128-1024-1024-1024-1 network, Sec. 5 Exp. 3 shape family): scores
 against the FP64 oracle within the bound the model's own calibration gives,
 and selections after the tiered near-tie re-score identical to the oracle's
 (Fig. 2: the best variant per kernel)."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -14,6 +16,7 @@ from paper_2301_03636_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 WIDE = (128, 1024, 1024, 1024, 1)
+GOLDEN_LARGE_SWEEP = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "large_sweep_best.npy")
 
 
 @pytest.fixture(scope="module")
@@ -80,8 +83,9 @@ def test_large_sweep_full_size_sampled_kernels(gpu_lib):
     """The large sweep at full size (2^20 variants of 65,536 kernels, counts
     2..64): one rank call on the GPU over every kernel, in the launch
     configuration the benchmark uses (BF16 layers + FP32 / FP64 near-tie
-    re-score); the oracle re-ranks a seeded sample of 256 kernels and the
-    selections must agree."""
+    re-score).  All 65,536 selections must equal the oracle's stored ones
+    (tests/golden/large_sweep_best.npy, written by the oracle), and the
+    oracle re-ranks a seeded sample of 256 kernels here as well."""
     wl = W.LARGE_SWEEP
     off = wl.offsets()
     n, K = int(off[-1]), wl.n_kernels
@@ -100,6 +104,8 @@ def test_large_sweep_full_size_sampled_kernels(gpu_lib):
     b = best.cpu().numpy()
     c32, c64 = m.rescore_counts()
     print(f"near-tie rows: {c32} FP32 ({c32 / n:.4f} of all), {c64} FP64")
+    golden = np.load(GOLDEN_LARGE_SWEEP).astype(np.int32)
+    assert np.array_equal(b, golden)
     ks = np.sort(np.random.default_rng(11).choice(K, 256, replace=False))
     rows = [d[off[k]:off[k + 1]] for k in ks]
     sub_off = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)

@@ -112,3 +112,22 @@ def test_library_variant_count_matches_table1():
     for depth, count in _table1().items():
         assert advisor.advisor_variant_count(depth) == count
     assert advisor.advisor_variant_count(0) == 0 and advisor.advisor_variant_count(5) == 0
+
+
+def test_large_sweep_golden_matches_oracle_on_a_sample():
+    """tests/golden/large_sweep_best.npy (the oracle's best variant of every
+    kernel of the full large sweep, used by the GPU tests) agrees with the
+    oracle recomputed here on a seeded sample of kernels."""
+    import os
+    wl = W.LARGE_SWEEP
+    golden = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "large_sweep_best.npy"))
+    off = wl.offsets()
+    assert golden.shape == (wl.n_kernels,) and golden.dtype == np.int8
+    d = wl.descriptors()
+    fc, sc = oracle.extract_features(W.calibration_descriptors(16384), wl.n_features)
+    mu, sigma = oracle.fit_standardizer(fc, sc)
+    ks = np.sort(np.random.default_rng(5).choice(wl.n_kernels, 48, replace=False))
+    rows = [d[off[k]:off[k + 1]] for k in ks]
+    sub_off = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    ref = oracle.rank(np.concatenate(rows), sub_off, wl.widths, wl.weights(), mu, sigma)[0]
+    assert np.array_equal(golden[ks].astype(np.int32), ref)
