@@ -247,6 +247,23 @@ advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_des
                             int32_t* d_best_local, double* d_best_score, float* d_scores,
                             uint8_t* d_row_status, cudaStream_t stream);
 
+/* advisor_rank with the descriptors in page-locked host memory (h_desc,
+ * cudaHostAlloc / cudaHostRegister) and a caller-owned device buffer d_desc
+ * of n_rows descriptors that receives them: the copy runs in n_stages chunks
+ * of whole 128-row tiles (1 <= n_stages <= ADVISOR_MAX_STAGES) on a stream of
+ * the model's own, and each chunk is extracted and scored on `stream` as soon
+ * as it has arrived, so that the copies overlap the scoring; the selection
+ * follows once every chunk is scored.  Same results as advisor_rank on
+ * d_desc.  The host must not change h_desc until the call has completed on
+ * `stream`.  Errors: those of advisor_rank; ADVISOR_ERR_INVALID_ARGUMENT for
+ * an h_desc that is not page-locked host memory or n_stages out of range. */
+#define ADVISOR_MAX_STAGES 16
+advisor_status advisor_rank_staged(advisor_model_t m, const advisor_variant_desc* h_desc,
+                                   advisor_variant_desc* d_desc, int64_t n_rows, const int64_t* d_seg_off,
+                                   int64_t n_kernels, advisor_precision precision, float eps_scores,
+                                   float eps_fp32, int32_t* d_best_local, double* d_best_score, float* d_scores,
+                                   uint8_t* d_row_status, int32_t n_stages, cudaStream_t stream);
+
 /* advisor_rank with an FP16 tensor-core tier between the first scores and
  * the FP32 re-score (a7 of Fig. 2's selection, made cheaper for wide models
  * and coarse first tiers).  eps_fp16 >= 0 enables it: the tier-1 candidates
@@ -323,6 +340,15 @@ advisor_status advisor_plan_rank(advisor_model_t m, const advisor_variant_desc* 
                                  int32_t autotune, cudaStream_t stream, advisor_plan_t* out);
 
 /* Replay the plan on `stream` (asynchronous: one graph launch). */
+/* advisor_plan_rank for advisor_rank_staged: the plan replays the staged
+ * copy of h_desc into d_desc together with the ranking (refill h_desc in
+ * place between replays). */
+advisor_status advisor_plan_rank_staged(advisor_model_t m, const advisor_variant_desc* h_desc,
+                                        advisor_variant_desc* d_desc, int64_t n_rows, const int64_t* d_seg_off,
+                                        int64_t n_kernels, advisor_precision precision, float eps_scores,
+                                        float eps_fp32, int32_t* d_best_local, double* d_best_score,
+                                        float* d_scores, uint8_t* d_row_status, int32_t n_stages,
+                                        int32_t autotune, cudaStream_t stream, advisor_plan_t* out);
 advisor_status advisor_plan_launch(advisor_plan_t p, cudaStream_t stream);
 
 /* The configuration the plan was captured with; *replay_us (nullable) the

@@ -86,6 +86,9 @@ def lib():
         "advisor_enumerate_variants": (st, [P, i64, P, i64, P, P, P]),
         "advisor_model_set_launch_config": (st, [P, P]),
         "advisor_plan_rank": (st, [P, P, i64, P, i64, st, f32, f32, P, P, P, P, i32, P, ctypes.POINTER(P)]),
+        "advisor_rank_staged": (st, [P, P, P, i64, P, i64, st, f32, f32, P, P, P, P, i32, P]),
+        "advisor_plan_rank_staged": (st, [P, P, P, i64, P, i64, st, f32, f32, P, P, P, P, i32, i32, P,
+                                          ctypes.POINTER(P)]),
         "advisor_plan_launch": (st, [P, P]),
         "advisor_plan_info": (st, [P, P, P, P]),
         "advisor_plan_destroy": (st, [P]),
@@ -334,6 +337,25 @@ class Model:
         """A Plan replaying rank() on these buffers (refill desc / offsets in place between launches)."""
         return Plan(self, desc, offsets, precision, eps, eps32, autotune, stream)
 
+    def rank_staged(self, h_desc, d_desc, offsets, precision="bf16", eps=-1.0, eps32=0.0, n_stages=4,
+                    scores=None, status=None, stream=None):
+        """rank() on descriptors in pinned host memory (h_desc), copied into the device buffer
+        d_desc in n_stages chunks that overlap the scoring (advisor_rank_staged)."""
+        K = offsets.shape[0] - 1
+        best = torch.empty(K, dtype=torch.int32, device=self.device)
+        best_score = torch.empty(K, dtype=torch.float64, device=self.device)
+        _check(lib().advisor_rank_staged(self.handle, _ptr(h_desc), _ptr(d_desc), h_desc.shape[0], _ptr(offsets), K,
+                                         _prec(precision), float(eps), float(eps32), _ptr(best), _ptr(best_score),
+                                         _ptr(scores), _ptr(status), int(n_stages), _stream(stream)),
+               "advisor_rank_staged")
+        return best, best_score
+
+    def plan_rank_staged(self, h_desc, d_desc, offsets, precision="bf16", eps=-1.0, eps32=0.0, n_stages=4,
+                         autotune=False, stream=None):
+        """A Plan replaying rank_staged() (refill h_desc / offsets in place between launches)."""
+        return Plan(self, d_desc, offsets, precision, eps, eps32, autotune, stream, h_desc=h_desc,
+                    n_stages=n_stages)
+
     def rank_topn(self, desc, offsets, top_n, precision="bf16", eps=-1.0, eps32=0.0, scores=None, status=None,
                   stream=None, eps16=None):
         """The top_n best variants of every kernel: (best [K][top_n] int32, score [K][top_n] float64)."""
@@ -442,19 +464,27 @@ class Plan:
     scores / status in place."""
 
     def __init__(self, model: Model, desc, offsets, precision="bf16", eps=-1.0, eps32=0.0, autotune=False,
-                 stream=None):
+                 stream=None, h_desc=None, n_stages=1):
         self.model = model
-        self.desc, self.offsets = desc, offsets
+        self.desc, self.offsets, self.h_desc = desc, offsets, h_desc
         K = offsets.shape[0] - 1
         self.best = torch.empty(K, dtype=torch.int32, device=model.device)
         self.best_score = torch.empty(K, dtype=torch.float64, device=model.device)
         self.scores = torch.empty(desc.shape[0], dtype=torch.float32, device=model.device)
         self.status = torch.empty(desc.shape[0], dtype=torch.uint8, device=model.device)
         h = ctypes.c_void_p()
-        _check(lib().advisor_plan_rank(model.handle, _ptr(desc), desc.shape[0], _ptr(offsets), K, _prec(precision),
-                                       float(eps), float(eps32), _ptr(self.best), _ptr(self.best_score),
-                                       _ptr(self.scores), _ptr(self.status), 1 if autotune else 0, _stream(stream),
-                                       ctypes.byref(h)), "advisor_plan_rank")
+        if h_desc is None:
+            _check(lib().advisor_plan_rank(model.handle, _ptr(desc), desc.shape[0], _ptr(offsets), K,
+                                           _prec(precision), float(eps), float(eps32), _ptr(self.best),
+                                           _ptr(self.best_score), _ptr(self.scores), _ptr(self.status),
+                                           1 if autotune else 0, _stream(stream), ctypes.byref(h)),
+                   "advisor_plan_rank")
+        else:
+            _check(lib().advisor_plan_rank_staged(model.handle, _ptr(h_desc), _ptr(desc), desc.shape[0],
+                                                  _ptr(offsets), K, _prec(precision), float(eps), float(eps32),
+                                                  _ptr(self.best), _ptr(self.best_score), _ptr(self.scores),
+                                                  _ptr(self.status), int(n_stages), 1 if autotune else 0,
+                                                  _stream(stream), ctypes.byref(h)), "advisor_plan_rank_staged")
         self.handle = h
 
     def launch(self, stream=None):

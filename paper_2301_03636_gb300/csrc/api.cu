@@ -49,7 +49,16 @@ struct advisor_model {
     int saved_fmt = 0;             // precision of the last advisor_forward_saved: 0 FP32, 1 BF16, 2 FP16
     adv::LtContext* lt = nullptr;  // cuBLASLt handle of the 16-bit training GEMMs (created on first use)
     bool last_mid = false;         // the last re-scoring selection ran the FP16 middle tier
-    ~advisor_model() { adv::lt_destroy(lt); }
+    // advisor_rank_staged: the stream that copies the descriptor chunks and the
+    // events that hand each chunk to the scoring stream (created on first use)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t stage_ev[ADVISOR_MAX_STAGES + 1] = {};
+    ~advisor_model() {
+        adv::lt_destroy(lt);
+        for (cudaEvent_t e : stage_ev)
+            if (e) cudaEventDestroy(e);
+        if (copy_stream) cudaStreamDestroy(copy_stream);
+    }
 };
 
 namespace {
@@ -632,12 +641,21 @@ namespace {
 // a1-a5 of the ranking calls: descriptors -> scores and row status; *rs
 // receives where the re-score tiers read the rows from (the FP32 path keeps
 // the int32 features, the tensor-core paths re-extract from the descriptors).
+//
+// row0 (a multiple of the 128-row tile) scores rows row0 .. row0 + n_rows - 1
+// of the arrays that d_desc, scores and status point to, into the matching
+// part of the workspace; *rs still refers to the whole arrays.
 advisor_status rank_scores(advisor_model* m, const advisor_variant_desc* d_desc, int64_t n_rows,
                            advisor_precision precision, float* scores, uint8_t* status, adv::RowSrc* rs,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, int64_t row0 = 0) {
     *rs = adv::RowSrc{nullptr, d_desc, nullptr, nullptr, 0, nullptr};
-    if (n_rows == 0) return ADVISOR_OK;
     const adv::ModelLayout& L = m->L;
+    if (precision == ADVISOR_FP32) *rs = adv::RowSrc{reinterpret_cast<int32_t*>(m->WS + m->W.feat32), nullptr,
+                                                     nullptr, nullptr, 0, nullptr};
+    if (n_rows == 0) return ADVISOR_OK;
+    d_desc += row0;
+    scores += row0;
+    status += row0;
     adv::ExtractArgs a{};
     a.desc = d_desc;
     a.n_rows = n_rows;
@@ -647,14 +665,12 @@ advisor_status rank_scores(advisor_model* m, const advisor_variant_desc* d_desc,
     cudaError_t e;
     if (precision == ADVISOR_FP32) {
         a.n_rows_padded = n_rows;
-        a.feat = reinterpret_cast<int32_t*>(m->WS + m->W.feat32);
+        a.feat = reinterpret_cast<int32_t*>(m->WS + m->W.feat32) + row0 * L.F;
         e = adv::launch_extract(a, L.F, 0, stream, m->cfg.extract_block);
         if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
         adv::RowSrc src{a.feat, nullptr, nullptr, nullptr, n_rows, status};
         e = adv::launch_mlp_fp32(mlp_desc(m), src, scores, m->num_sms, false, stream);
-        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
-        *rs = adv::RowSrc{a.feat, nullptr, nullptr, nullptr, 0, nullptr};
-        return ADVISOR_OK;
+        return e == cudaSuccess ? ADVISOR_OK : ADVISOR_ERR_CUDA;
     }
     if (precision == ADVISOR_FP8_E4M3) {
         if (!wide_supported(m)) return ADVISOR_ERR_UNSUPPORTED;
@@ -666,8 +682,8 @@ advisor_status rank_scores(advisor_model* m, const advisor_variant_desc* d_desc,
     if (!fused && m->L.n_hidden < 1) return ADVISOR_ERR_UNSUPPORTED;
     const int fi = precision == ADVISOR_BF16 ? 0 : (precision == ADVISOR_FP16 ? 1 : 2);
     a.n_rows_padded = ((n_rows + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
-    a.x_img = m->WS + m->W.x_img;
     a.nslab = fi == 2 ? L.nslab8[0] : L.nslab[0];
+    a.x_img = m->WS + m->W.x_img + (size_t)(row0 / ADV_TILE_M) * a.nslab * ADV_X_SLAB_BYTES;
     a.x8_scale = reinterpret_cast<const float*>(m->P + L.p_fp8) + ADV_FP8_X_SCALE;
     e = adv::launch_extract(a, L.F, fi + 1, stream, m->cfg.extract_block);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
@@ -793,6 +809,60 @@ advisor_status advisor_rank_ex(advisor_model_t m, const advisor_variant_desc* d_
     if (st != ADVISOR_OK) return st;
     return do_select(m, scores, n_rows, d_seg_off, n_kernels, rs, rescore && n_rows > 0, eps_scores, eps_fp32,
                      d_best_local, d_best_score, stream, eps_fp16 >= 0.f ? eps_fp16 : -1.f, zeroed);
+}
+
+advisor_status advisor_rank_staged(advisor_model_t m, const advisor_variant_desc* h_desc,
+                                   advisor_variant_desc* d_desc, int64_t n_rows, const int64_t* d_seg_off,
+                                   int64_t n_kernels, advisor_precision precision, float eps_scores,
+                                   float eps_fp32, int32_t* d_best_local, double* d_best_score, float* d_scores,
+                                   uint8_t* d_row_status, int32_t n_stages, cudaStream_t stream) {
+    if (n_stages < 1 || n_stages > ADVISOR_MAX_STAGES) return ADVISOR_ERR_INVALID_ARGUMENT;
+    advisor_status st = rank_checks(m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, -1.f,
+                                    eps_fp32, d_best_local, d_best_score);
+    if (st != ADVISOR_OK || n_kernels == 0) return st;
+    if (n_rows > 0) {
+        cudaPointerAttributes at{};
+        if (!h_desc || cudaPointerGetAttributes(&at, h_desc) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            return ADVISOR_ERR_INVALID_ARGUMENT;   // the copies need page-locked host memory
+        }
+    }
+    if (!m->copy_stream) {
+        if (cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            m->copy_stream = nullptr;
+            return ADVISOR_ERR_CUDA;
+        }
+        for (cudaEvent_t& e : m->stage_ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return ADVISOR_ERR_CUDA;
+    }
+    const bool rescore = eps_scores >= 0.f;
+    float* scores = d_scores ? d_scores : reinterpret_cast<float*>(m->WS + m->W.scores);
+    uint8_t* status = d_row_status ? d_row_status : m->WS + m->W.status;
+    const bool zeroed = rescore && n_rows > 0;
+    if (zeroed && cudaMemsetAsync(m->WS + m->W.counters, 0, 4 * sizeof(int), stream) != cudaSuccess)
+        return ADVISOR_ERR_CUDA;
+    // chunks of whole 128-row tiles: the copy of chunk c + 1 overlaps the scoring of chunk c
+    const int64_t tiles = (n_rows + ADV_TILE_M - 1) / ADV_TILE_M;
+    const int64_t chunk = ((tiles + n_stages - 1) / n_stages) * ADV_TILE_M;
+    if (cudaEventRecord(m->stage_ev[0], stream) != cudaSuccess ||
+        cudaStreamWaitEvent(m->copy_stream, m->stage_ev[0], 0) != cudaSuccess)
+        return ADVISOR_ERR_CUDA;
+    adv::RowSrc rs{};
+    int c = 0;
+    for (int64_t r0 = 0; r0 < n_rows; r0 += chunk, ++c) {
+        const int64_t rows = n_rows - r0 < chunk ? n_rows - r0 : chunk;
+        if (cudaMemcpyAsync(d_desc + r0, h_desc + r0, (size_t)rows * sizeof(advisor_variant_desc),
+                            cudaMemcpyHostToDevice, m->copy_stream) != cudaSuccess ||
+            cudaEventRecord(m->stage_ev[c + 1], m->copy_stream) != cudaSuccess ||
+            cudaStreamWaitEvent(stream, m->stage_ev[c + 1], 0) != cudaSuccess)
+            return ADVISOR_ERR_CUDA;
+        st = rank_scores(m, d_desc, rows, precision, scores, status, &rs, stream, r0);
+        if (st != ADVISOR_OK) return st;
+    }
+    if (n_rows == 0) rank_scores(m, d_desc, 0, precision, scores, status, &rs, stream);
+    else if (c == 0) return ADVISOR_ERR_CUDA;
+    return do_select(m, scores, n_rows, d_seg_off, n_kernels, rs, rescore && n_rows > 0, eps_scores, eps_fp32,
+                     d_best_local, d_best_score, stream, -1.f, zeroed);
 }
 
 advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,

@@ -44,6 +44,8 @@ struct RankCall {
     double* best_score;
     float* scores;
     uint8_t* status;
+    const advisor_variant_desc* h_desc;   // non-null: advisor_rank_staged from these host descriptors into desc
+    int32_t n_stages;
 };
 
 bool same(const advisor_launch_config& a, const advisor_launch_config& b) {
@@ -64,8 +66,12 @@ advisor_status capture(const RankCall& r, cudaStream_t cap, cudaGraph_t* g_out, 
     *x_out = nullptr;
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return ADVISOR_ERR_CUDA;
     const long long before = advisor_launch_count();
-    const advisor_status st = advisor_rank(r.m, r.desc, r.n_rows, r.off, r.n_kernels, r.precision, r.eps, r.eps32,
-                                           r.best, r.best_score, r.scores, r.status, cap);
+    const advisor_status st =
+        r.h_desc ? advisor_rank_staged(r.m, r.h_desc, const_cast<advisor_variant_desc*>(r.desc), r.n_rows, r.off,
+                                       r.n_kernels, r.precision, r.eps, r.eps32, r.best, r.best_score, r.scores,
+                                       r.status, r.n_stages, cap)
+                 : advisor_rank(r.m, r.desc, r.n_rows, r.off, r.n_kernels, r.precision, r.eps, r.eps32, r.best,
+                                r.best_score, r.scores, r.status, cap);
     // the launches were only recorded; replays account for them instead
     adv_count_launch(-(int)(advisor_launch_count() - before));
     cudaGraph_t g = nullptr;
@@ -138,19 +144,12 @@ bool try_candidate(const RankCall& r, const advisor_launch_config& c, cudaStream
     return st == ADVISOR_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-advisor_status advisor_plan_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
-                                 const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
-                                 float eps_scores, float eps_fp32, int32_t* d_best_local, double* d_best_score,
-                                 float* d_scores, uint8_t* d_row_status, int32_t autotune, cudaStream_t stream,
-                                 advisor_plan_t* out) {
+// Autotune (optionally) and capture one ranking call into a plan.
+advisor_status make_plan(const RankCall& r, int32_t autotune, cudaStream_t stream, advisor_plan_t* out) {
+    advisor_model_t m = r.m;
+    const int64_t n_rows = r.n_rows;
     if (!m || !out) return ADVISOR_ERR_INVALID_ARGUMENT;
     *out = nullptr;
-    const RankCall r{m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, eps_fp32,
-                     d_best_local, d_best_score, d_scores, d_row_status};
     advisor_launch_config saved{};
     advisor_status st = advisor_model_get_launch_config(m, &saved);
     if (st != ADVISOR_OK) return st;
@@ -217,6 +216,32 @@ advisor_status advisor_plan_rank(advisor_model_t m, const advisor_variant_desc* 
     p->replay_us = autotune ? best_us : 0.f;
     *out = p;
     return ADVISOR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+advisor_status advisor_plan_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                                 const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
+                                 float eps_scores, float eps_fp32, int32_t* d_best_local, double* d_best_score,
+                                 float* d_scores, uint8_t* d_row_status, int32_t autotune, cudaStream_t stream,
+                                 advisor_plan_t* out) {
+    const RankCall r{m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, eps_fp32,
+                     d_best_local, d_best_score, d_scores, d_row_status, nullptr, 1};
+    return make_plan(r, autotune, stream, out);
+}
+
+advisor_status advisor_plan_rank_staged(advisor_model_t m, const advisor_variant_desc* h_desc,
+                                        advisor_variant_desc* d_desc, int64_t n_rows, const int64_t* d_seg_off,
+                                        int64_t n_kernels, advisor_precision precision, float eps_scores,
+                                        float eps_fp32, int32_t* d_best_local, double* d_best_score,
+                                        float* d_scores, uint8_t* d_row_status, int32_t n_stages,
+                                        int32_t autotune, cudaStream_t stream, advisor_plan_t* out) {
+    if (!h_desc) return ADVISOR_ERR_INVALID_ARGUMENT;
+    const RankCall r{m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, eps_fp32,
+                     d_best_local, d_best_score, d_scores, d_row_status, h_desc, n_stages};
+    return make_plan(r, autotune, stream, out);
 }
 
 advisor_status advisor_plan_launch(advisor_plan_t p, cudaStream_t stream) {

@@ -109,3 +109,33 @@ def test_pageable_host_descriptors_rejected(gpu_lib):
     with pytest.raises(advisor.AdvisorError) as e:
         m.rank(d, o, "bf16")
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("n_stages", [1, 3, 8])
+def test_staged_copy_rank_equals_rank(gpu_lib, n_stages):
+    """advisor_rank_staged (pinned host descriptors copied in chunks that
+    overlap the scoring) and its plan select exactly what advisor_rank
+    selects on the same descriptors in device memory."""
+    widths = (64, 256, 256, 256, 1)
+    off = W.make_segments(500, 4, 64, seed=33)
+    n = int(off[-1])
+    d = W.make_descriptors(n, 33)
+    m = advisor.Model(widths, max_rows=n, max_kernels=500)
+    m.set_params(W.make_weights(widths, 33), np.zeros(64), np.full(64, 8.0))
+    dd, ot = torch.from_numpy(d).cuda(), torch.from_numpy(off).cuda()
+    dh = torch.from_numpy(d).pin_memory()
+    for prec, eps in (("bf16", 0.05), ("fp32", 1e-3), ("bf16", -1.0)):
+        s_ref = torch.empty(n, device="cuda")
+        s_stg = torch.empty(n, device="cuda")
+        b_ref, bs_ref = m.rank(dd, ot, prec, eps=eps, eps32=1e-4, scores=s_ref)
+        stage = torch.zeros_like(dd)
+        b, bs = m.rank_staged(dh, stage, ot, prec, eps=eps, eps32=1e-4, n_stages=n_stages, scores=s_stg)
+        torch.cuda.synchronize()
+        assert torch.equal(stage, dd)
+        assert torch.equal(s_stg, s_ref) and torch.equal(b, b_ref) and torch.equal(bs, bs_ref)
+    stage = torch.zeros_like(dd)
+    plan = m.plan_rank_staged(dh, stage, ot, "bf16", 0.05, 1e-4, n_stages=n_stages)
+    b_plan, _ = plan.launch()
+    torch.cuda.synchronize()
+    b_ref, _ = m.rank(dd, ot, "bf16", eps=0.05, eps32=1e-4)
+    assert torch.equal(b_plan, b_ref)
