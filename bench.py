@@ -718,7 +718,7 @@ def main():
 
     # copy-in in chunks that overlap the scoring of the chunks before them
     staged = {}
-    for ns in (4, 8):
+    for ns in (3, 4, 6):
         ps = m.plan_rank_staged(desc_h, desc, offs, prec, eps, eps32, n_stages=ns, autotune=True)
 
         def e2e_staged_step(ps=ps):
