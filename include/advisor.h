@@ -389,8 +389,9 @@ advisor_status advisor_rank_topn_ex(advisor_model_t m, const advisor_variant_des
 
 /* a8: one training step (Sec. 3 training mode; Sec. 5 Exp. 3): forward,
  * loss = 0.5 * mean (y - label)^2 over the n_rows rows (labels: ln runtime),
- * hand-written backward, Adam update of the FP32 master weights followed by
- * a repack of the 16-bit copies.  precision ADVISOR_FP32 (SIMT) or
+ * hand-written backward, Adam update of the FP32 master weights; the derived
+ * inference copies are marked stale and rebuilt by the next scoring call or
+ * plan replay (advisor_model_refresh).  precision ADVISOR_FP32 (SIMT) or
  * ADVISOR_BF16 / ADVISOR_FP16 (16-bit operands for the forward/backward
  * GEMMs, FP32 accumulation and master weights).  h_adam = {lr, beta1, beta2,
  * eps, weight_decay} (host floats, copied at call time).  d_loss (nullable)
@@ -443,6 +444,12 @@ advisor_status advisor_backward(advisor_model_t m, const float* d_dy, int64_t n_
 /* Rebuild the derived copies (16-bit tensor-core images, transposed copy,
  * padded biases) after the FP32 master parameters were changed in place. */
 advisor_status advisor_model_repack(advisor_model_t m, cudaStream_t stream);
+
+/* The training steps update the FP32 masters only and mark the derived
+ * copies stale; every scoring call (and every plan replay) rebuilds them
+ * first when they are.  This call does that rebuild now, on `stream`, and is
+ * a no-op when nothing changed. */
+advisor_status advisor_model_refresh(advisor_model_t m, cudaStream_t stream);
 
 /* Byte offset of the FP32 master parameters inside the parameter block (so
  * that a caller can view them as a tensor, e.g. for an external optimizer). */

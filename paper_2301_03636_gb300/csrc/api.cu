@@ -53,6 +53,9 @@ struct advisor_model {
     // events that hand each chunk to the scoring stream (created on first use)
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t stage_ev[ADVISOR_MAX_STAGES + 1] = {};
+    // the master parameters changed (an optimizer step) since the derived
+    // inference copies were last built: rebuilt before the next scoring call
+    bool images_stale = false;
     ~advisor_model() {
         adv::lt_destroy(lt);
         for (cudaEvent_t e : stage_ev)
@@ -164,6 +167,19 @@ bool use_fused(const advisor_model* m, advisor_precision p) {
 
 cudaError_t launch_wide(advisor_model* m, const uint8_t* x_img, int64_t n_rows, const uint8_t* status, float* scores,
                         int fi, cudaStream_t s, const int* n_rows_dev = nullptr);
+
+// Rebuild the derived inference copies when an optimizer step has changed
+// the masters since they were built.  Inside a stream capture the rebuild is
+// recorded into the graph and the model stays marked (eager calls still
+// rebuild before they score).
+cudaError_t ensure_images(advisor_model* m, cudaStream_t s) {
+    if (!m->images_stale) return cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return cudaErrorUnknown;
+    const cudaError_t e = adv::launch_repack(m->L, m->P, s);
+    if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone) m->images_stale = false;
+    return e;
+}
 
 advisor_status check_ready(const advisor_model* m, int64_t n_rows) {
     if (!m || !m->P || !m->WS || !m->params_set) return ADVISOR_ERR_INVALID_ARGUMENT;
@@ -539,6 +555,7 @@ advisor_status advisor_model_set_params(advisor_model_t m, const float* d_params
     e = adv::launch_set_params(m->L, m->P, d_params_fp32, d_mu, d_sigma, stream);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     m->params_set = true;
+    m->images_stale = false;   // set_params builds the derived copies
     m->adam_step = 0;
     m->fp8_calibrated = false;
     return ADVISOR_OK;
@@ -582,6 +599,7 @@ advisor_status advisor_score_variants(advisor_model_t m, const int32_t* d_feat_q
     if (n_rows == 0) return ADVISOR_OK;
     advisor_status st = check_ready(m, n_rows);
     if (st != ADVISOR_OK) return st;
+    if (ensure_images(m, stream) != cudaSuccess) return ADVISOR_ERR_CUDA;
     if (precision == ADVISOR_FP32) {
         adv::RowSrc src{d_feat_q16, nullptr, nullptr, nullptr, n_rows, d_row_status};
         return cuda_status(adv::launch_mlp_fp32(mlp_desc(m), src, d_scores, m->num_sms, false, stream));
@@ -614,6 +632,7 @@ advisor_status advisor_score_variants_fp64(advisor_model_t m, const int32_t* d_f
     if (!m || n_rows < 0 || !d_feat_q16 || !d_scores) return ADVISOR_ERR_INVALID_ARGUMENT;
     if (n_rows == 0) return ADVISOR_OK;
     if (!m->P || !m->params_set) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (ensure_images(m, stream) != cudaSuccess) return ADVISOR_ERR_CUDA;
     adv::RowSrc src{d_feat_q16, nullptr, nullptr, nullptr, n_rows, d_row_status};
     return cuda_status(adv::launch_mlp_fp64(mlp_desc(m), src, d_scores, m->num_sms, stream));
 }
@@ -629,6 +648,7 @@ advisor_status advisor_select_best(advisor_model_t m, const float* d_scores, int
     if (rescore && (eps_fp32 < 0.f || !aligned(d_feat_q16, 16))) return ADVISOR_ERR_INVALID_ARGUMENT;
     advisor_status st = check_ready(m, n_rows);
     if (st != ADVISOR_OK) return st;
+    if (rescore && ensure_images(m, stream) != cudaSuccess) return ADVISOR_ERR_CUDA;
     adv::RowSrc src{d_feat_q16, nullptr, nullptr, nullptr, 0, nullptr};
     return do_select(m, d_scores, n_rows, d_seg_off, n_kernels, src, rescore, eps_scores, eps_fp32, d_best_local,
                      d_best_score, stream);
@@ -798,6 +818,7 @@ advisor_status advisor_rank_ex(advisor_model_t m, const advisor_variant_desc* d_
     advisor_status st = rank_checks(m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, eps_fp16,
                                     eps_fp32, d_best_local, d_best_score);
     if (st != ADVISOR_OK || n_kernels == 0) return st;
+    if (ensure_images(m, stream) != cudaSuccess) return ADVISOR_ERR_CUDA;
     const bool rescore = eps_scores >= 0.f;
     float* scores = d_scores ? d_scores : reinterpret_cast<float*>(m->WS + m->W.scores);
     uint8_t* status = d_row_status ? d_row_status : m->WS + m->W.status;
@@ -820,6 +841,7 @@ advisor_status advisor_rank_staged(advisor_model_t m, const advisor_variant_desc
     advisor_status st = rank_checks(m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, -1.f,
                                     eps_fp32, d_best_local, d_best_score);
     if (st != ADVISOR_OK || n_kernels == 0) return st;
+    if (ensure_images(m, stream) != cudaSuccess) return ADVISOR_ERR_CUDA;
     if (n_rows > 0) {
         cudaPointerAttributes at{};
         if (!h_desc || cudaPointerGetAttributes(&at, h_desc) != cudaSuccess || at.type != cudaMemoryTypeHost) {
@@ -882,6 +904,7 @@ advisor_status advisor_rank_topn_ex(advisor_model_t m, const advisor_variant_des
     advisor_status st = rank_checks(m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, eps_fp16,
                                     eps_fp32, d_best_local, d_best_score);
     if (st != ADVISOR_OK || n_kernels == 0) return st;
+    if (ensure_images(m, stream) != cudaSuccess) return ADVISOR_ERR_CUDA;
     const bool rescore = eps_scores >= 0.f;
     float* scores = d_scores ? d_scores : reinterpret_cast<float*>(m->WS + m->W.scores);
     uint8_t* status = d_row_status ? d_row_status : m->WS + m->W.status;
@@ -930,6 +953,7 @@ advisor_status advisor_train_step(advisor_model_t m, const int32_t* d_feat_q16, 
                                                          stream);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     m->adam_step = step;
+    m->images_stale = true;
     return ADVISOR_OK;
 }
 
@@ -954,6 +978,7 @@ advisor_status advisor_train_step_ex(advisor_model_t m, const int32_t* d_feat_q1
                                               d_feat_q16, d_labels, n_rows, o, step, d_loss, stream);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     m->adam_step = step;
+    m->images_stale = true;
     return ADVISOR_OK;
 }
 
@@ -1009,7 +1034,14 @@ advisor_status advisor_backward(advisor_model_t m, const float* d_dy, int64_t n_
 
 advisor_status advisor_model_repack(advisor_model_t m, cudaStream_t stream) {
     if (!m || !m->P) return ADVISOR_ERR_INVALID_ARGUMENT;
-    return cuda_status(adv::launch_repack(m->L, m->P, stream));
+    const advisor_status st = cuda_status(adv::launch_repack(m->L, m->P, stream));
+    if (st == ADVISOR_OK) m->images_stale = false;
+    return st;
+}
+
+advisor_status advisor_model_refresh(advisor_model_t m, cudaStream_t stream) {
+    if (!m || !m->P) return ADVISOR_ERR_INVALID_ARGUMENT;
+    return cuda_status(ensure_images(m, stream));
 }
 
 size_t advisor_model_master_offset(advisor_model_t m) { return m ? m->L.p_master : 0; }
@@ -1036,6 +1068,11 @@ advisor_status advisor_get_device_status(advisor_model_t m, cudaStream_t stream)
 
 // Read-only view of a bound model for the no-allocation scoring entry point
 // (noalloc.cu); allocates nothing.
+// Rebuild stale derived copies before a no-allocation scoring call; 0 on a CUDA error.
+int adv_model_prepare(advisor_model_t m, cudaStream_t stream) {
+    return m && ensure_images(m, stream) == cudaSuccess ? 1 : 0;
+}
+
 int adv_model_noalloc_view(advisor_model_t m, int fmt_idx, adv::NoallocModelView* out) {
     if (!m || !out) return 0;
     out->ready = (m->P != nullptr && m->params_set) ? 1 : 0;

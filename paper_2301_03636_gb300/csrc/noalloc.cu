@@ -67,6 +67,7 @@ extern "C" advisor_status advisor_score_variants_noalloc(advisor_model_t m, cons
     if (!adv_model_noalloc_view(m, precision == ADVISOR_BF16 ? 0 : 1, &v) || !v.ready)
         return ADVISOR_ERR_INVALID_ARGUMENT;
     if (!v.tc_ok) return ADVISOR_ERR_UNSUPPORTED;
+    if (!adv_model_prepare(m, stream)) return ADVISOR_ERR_CUDA;
     if (v.nslab0 > NOSCRATCH_MAX_SLABS) return ADVISOR_ERR_UNSUPPORTED;
     void* scratch = nullptr;
     if (noalloc_scratch(&scratch) != cudaSuccess) return ADVISOR_ERR_CUDA;

@@ -21,3 +21,4 @@ struct NoallocModelView {
 
 // Provided by api.cu: a read-only view of a bound model (allocates nothing).
 extern "C" int adv_model_noalloc_view(advisor_model_t m, int fmt_idx, adv::NoallocModelView* out);
+extern "C" int adv_model_prepare(advisor_model_t m, cudaStream_t stream);

@@ -23,6 +23,7 @@
 extern "C" void adv_count_launch(int n);
 
 struct advisor_plan {
+    advisor_model_t model = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     advisor_launch_config cfg{};
@@ -153,6 +154,8 @@ advisor_status make_plan(const RankCall& r, int32_t autotune, cudaStream_t strea
     advisor_launch_config saved{};
     advisor_status st = advisor_model_get_launch_config(m, &saved);
     if (st != ADVISOR_OK) return st;
+    st = advisor_model_refresh(m, stream);
+    if (st != ADVISOR_OK) return st;
     if (cudaStreamSynchronize(stream) != cudaSuccess) return ADVISOR_ERR_CUDA;
     cudaStream_t cap = nullptr;
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return ADVISOR_ERR_CUDA;
@@ -212,6 +215,7 @@ advisor_status make_plan(const RankCall& r, int32_t autotune, cudaStream_t strea
         delete p;
         return st;
     }
+    p->model = m;
     p->cfg = best;
     p->replay_us = autotune ? best_us : 0.f;
     *out = p;
@@ -246,6 +250,9 @@ advisor_status advisor_plan_rank_staged(advisor_model_t m, const advisor_variant
 
 advisor_status advisor_plan_launch(advisor_plan_t p, cudaStream_t stream) {
     if (!p || !p->exec) return ADVISOR_ERR_INVALID_ARGUMENT;
+    // derived copies an optimizer step left stale are rebuilt before the replay
+    const advisor_status st = advisor_model_refresh(p->model, stream);
+    if (st != ADVISOR_OK) return st;
     if (cudaGraphLaunch(p->exec, stream) != cudaSuccess) return ADVISOR_ERR_CUDA;
     adv_count_launch(p->kernels);
     return ADVISOR_OK;

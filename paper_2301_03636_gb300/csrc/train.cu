@@ -349,9 +349,7 @@ cudaError_t launch_adam_update(const ModelLayout& L, uint8_t* P, const float* gr
                                                   reinterpret_cast<float*>(P + L.p_adam_v), L.n_params, adam, c1,
                                                   c2);
     adv_count_launch(1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_repack(L, P, s);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_train_step_ex(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
@@ -375,9 +373,7 @@ cudaError_t launch_train_step_ex(const ModelLayout& L, const TrainLayout& T, uin
                                                      reinterpret_cast<float*>(P + L.p_adam_v), L.n_params, o.h.lr,
                                                      o.alpha, o.h.eps, o.h.weight_decay);
     adv_count_launch(1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_repack(L, P, s);
+    return cudaGetLastError();
 }
 
 }  // namespace adv

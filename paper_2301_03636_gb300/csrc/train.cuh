@@ -51,6 +51,9 @@ cudaError_t launch_backward(const ModelLayout& L, const TrainLayout& T, uint8_t*
 cudaError_t launch_mse_loss(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const float* labels, int64_t n,
                             float* d_loss, cudaStream_t s);
 // Adam update of the master weights (step counts from 1), then the repack.
+// The optimizer kernels update the FP32 masters only; the derived inference
+// copies (16-bit and E4M3 images, transposed copy, padded biases) are rebuilt
+// by the caller before the next scoring call (launch_repack).
 cudaError_t launch_adam_update(const ModelLayout& L, uint8_t* P, const float* grad, const AdamHyper& adam,
                                int64_t step, cudaStream_t s);
 

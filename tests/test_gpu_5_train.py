@@ -179,3 +179,33 @@ def test_tensor_core_training_meets_nrmse_criterion(gpu_lib):
     print(f"bf16: loss {first:.4f} -> {last:.4f}; validation RMSE {ev['rmse']:.4f} NRMSE {ev['nrmse']:.4f}")
     assert last < 0.25 * first
     assert ev["nrmse"] < metrics.SUCCESS_NRMSE
+
+
+def test_scoring_after_training_uses_the_updated_weights(gpu_lib):
+    """A training step updates the FP32 masters only; the next scoring call
+    (eager or a plan replay) rebuilds the derived 16-bit images first, so its
+    scores equal those of a model given the updated masters afresh."""
+    import numpy as np
+    from paper_2301_03636_gb300 import workloads as W
+    widths = (64, 256, 256, 256, 1)
+    off = W.make_segments(64, 4, 64, seed=21)
+    n = int(off[-1])
+    d = torch.from_numpy(W.make_descriptors(n, 21)).cuda()
+    o = torch.from_numpy(off).cuda()
+    f, st = advisor.advisor_extract_features(d, 64)
+    mu, sg = advisor.advisor_fit_standardizer(f, st)
+    m = advisor.Model(widths, max_rows=max(n, 4096), max_kernels=64)
+    m.set_params(W.make_weights(widths, 21), mu, sg)
+    plan = m.plan_rank(d, o, "bf16")
+    t = torch.from_numpy(W.make_labels(d.cpu().numpy(), 21)).cuda()
+    for _ in range(3):
+        m.train_step(f, t, "bf16", lr=1e-2)
+    y = m.score(f, st, "bf16")
+    ref = advisor.Model(widths, max_rows=max(n, 4096), max_kernels=64)
+    ref.set_params(m.get_params().cpu().numpy(), mu, sg)
+    assert torch.equal(y, ref.score(f, st, "bf16"))
+    m.train_step(f, t, "bf16", lr=1e-2)                    # stale again: the replay rebuilds
+    plan.launch()
+    torch.cuda.synchronize()
+    ref.set_params(m.get_params().cpu().numpy(), mu, sg)
+    assert torch.equal(plan.scores, ref.score(f, st, "bf16"))
