@@ -936,6 +936,23 @@ int train_fmt(advisor_model* m, advisor_precision p) {
     return p == ADVISOR_BF16 ? 1 : 2;
 }
 
+// The fused 16-bit training forward, for models the fused scorer covers (else nullptr).
+const adv::FusedFwd* fused_fwd(advisor_model* m, int fmt, adv::FusedFwd* ff) {
+    if (fmt == 0 || !tc_supported(m)) return nullptr;
+    const adv::ModelLayout& L = m->L;
+    ff->tc = tc_args(m, nullptr, 0, nullptr, nullptr, fmt == 1 ? 0 : 1);
+    ff->x_img = m->WS + m->W.x_img;
+    ff->num_sms = m->num_sms;
+    ff->ctas = m->cfg.tc_ctas;
+    for (int l = 0; l < L.n_hidden; ++l) {
+        ff->img16[0][l] = m->P + L.p_w16[0][l];
+        ff->img16[1][l] = m->P + L.p_w16[1][l];
+        ff->bias_pad[l] = reinterpret_cast<float*>(m->P + L.p_bias_off[l]);
+    }
+    ff->wout_pad = reinterpret_cast<float*>(m->P + L.p_wout_pad);
+    return ff;
+}
+
 advisor_status advisor_train_step(advisor_model_t m, const int32_t* d_feat_q16, const float* d_labels,
                                   int64_t n_rows, advisor_precision precision, const float* h_adam, float* d_loss,
                                   cudaStream_t stream) {
@@ -946,11 +963,12 @@ advisor_status advisor_train_step(advisor_model_t m, const int32_t* d_feat_q16, 
     if (fmt < 0) return ADVISOR_ERR_UNSUPPORTED;
     const adv::AdamHyper h{h_adam[0], h_adam[1], h_adam[2], h_adam[3], h_adam[4]};
     const int64_t step = m->adam_step + 1;
+    adv::FusedFwd ff{};
     cudaError_t e = fmt == 0 ? adv::launch_train_step(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), d_feat_q16,
                                                       d_labels, n_rows, &h, step, nullptr, d_loss, m->num_sms, stream)
                              : adv::launch_train_step_tc(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), m->lt,
                                                          fmt, d_feat_q16, d_labels, n_rows, &h, step, nullptr, d_loss,
-                                                         stream);
+                                                         stream, fused_fwd(m, fmt, &ff));
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     m->adam_step = step;
     m->images_stale = true;
@@ -974,8 +992,10 @@ advisor_status advisor_train_step_ex(advisor_model_t m, const int32_t* d_feat_q1
     o.h = adv::AdamHyper{opt->lr, opt->beta1, opt->beta2, opt->eps, opt->weight_decay};
     o.alpha = opt->alpha;
     const int64_t step = m->adam_step + 1;
+    adv::FusedFwd ff{};
     cudaError_t e = adv::launch_train_step_ex(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), m->lt, fmt,
-                                              d_feat_q16, d_labels, n_rows, o, step, d_loss, stream);
+                                              d_feat_q16, d_labels, n_rows, o, step, d_loss, stream,
+                                              fused_fwd(m, fmt, &ff));
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     m->adam_step = step;
     m->images_stale = true;
@@ -990,10 +1010,11 @@ advisor_status advisor_loss_grad(advisor_model_t m, const int32_t* d_feat_q16, c
     if (st != ADVISOR_OK) return st;
     const int fmt = train_fmt(m, precision);
     if (fmt < 0) return ADVISOR_ERR_UNSUPPORTED;
+    adv::FusedFwd ff{};
     if (fmt != 0)
         return cuda_status(adv::launch_train_step_tc(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), m->lt, fmt,
                                                      d_feat_q16, d_labels, n_rows, nullptr, 0, d_grad, d_loss,
-                                                     stream));
+                                                     stream, fused_fwd(m, fmt, &ff)));
     return cuda_status(adv::launch_train_step(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), d_feat_q16,
                                               d_labels, n_rows, nullptr, 0, d_grad, d_loss, m->num_sms, stream));
 }
@@ -1012,10 +1033,11 @@ advisor_status advisor_forward_saved(advisor_model_t m, const int32_t* d_feat_q1
     if (st != ADVISOR_OK) return st;
     const int fmt = train_fmt(m, precision);
     if (fmt < 0) return ADVISOR_ERR_UNSUPPORTED;
+    adv::FusedFwd ff{};
     cudaError_t e = fmt == 0 ? adv::launch_forward_saved(m->L, m->T, m->WS + m->W.train, mlp_desc(m), d_feat_q16,
                                                          n_rows, d_y, stream)
                              : adv::launch_forward_saved_tc(m->L, m->T, m->WS + m->W.train, mlp_desc(m), m->lt, fmt,
-                                                            d_feat_q16, n_rows, d_y, stream);
+                                                            d_feat_q16, n_rows, d_y, stream, fused_fwd(m, fmt, &ff));
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     m->saved_rows = n_rows;
     m->saved_fmt = fmt;

@@ -95,6 +95,10 @@ struct TcArgs {
     float* scores;
     int* status_word;
     unsigned long long timeout_ns;
+    // training forward (nullable per layer): hidden layer l's post-ReLU 16-bit
+    // activations, row-major [n_rows][save_ld[l]] (save_ld[l] a multiple of 8)
+    void* save_act[ADV_MAX_LAYERS];
+    int save_ld[ADV_MAX_LAYERS];
 };
 cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s, int ctas = 0);
 

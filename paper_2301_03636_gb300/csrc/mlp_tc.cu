@@ -55,7 +55,7 @@ __device__ __forceinline__ uint32_t relu_pack(float lo, float hi) {
     return d;
 }
 
-template <int FMT>
+template <int FMT, bool SAVE>
 __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_constant__ TcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_addr(smem_raw);
@@ -258,6 +258,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                     const uint32_t t_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * a.nmax);
                     uint8_t* my_act = act[s];
                     float y4[4] = {0.f, 0.f, 0.f, 0.f};
+                    // training: this layer's 16-bit activations also go to global memory, row-major
+                    const int64_t grow = (int64_t)(b + i * G) * ADV_TILE_M + r;
+                    uint8_t* save = SAVE && a.save_act[l] && grow < n_rows
+                                        ? reinterpret_cast<uint8_t*>(a.save_act[l]) + (size_t)grow * a.save_ld[l] * 2
+                                        : nullptr;
                     for (int c0 = cb; c0 < cb + cw; c0 += 32) {
                         const bool two = c0 + 16 < cb + cw;     // a second 16-column group in this step
                         uint32_t v0[16], v1[16];
@@ -289,8 +294,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                                     const uint32_t chunk = (uint32_t)(((c & 63) >> 3) + q);
                                     *reinterpret_cast<uint4*>(slab + sw128_offset(r, chunk)) =
                                         make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                                    if (SAVE && save && c + 8 * q < a.save_ld[l])
+                                        *reinterpret_cast<uint4*>(save + (size_t)(c + 8 * q) * 2) =
+                                            make_uint4(pk[0], pk[1], pk[2], pk[3]);
                                 }
                             } else {
+                                if (SAVE && save) {
+#pragma unroll
+                                    for (int q = 0; q < 2; ++q) {
+                                        uint32_t pk[4];
+#pragma unroll
+                                        for (int t = 0; t < 4; ++t) {
+                                            const int cc = 8 * q + 2 * t;
+                                            pk[t] = relu_pack<FMT>(__uint_as_float(v[cc]) + bf[16 * h + cc],
+                                                                   __uint_as_float(v[cc + 1]) + bf[16 * h + cc + 1]);
+                                        }
+                                        if (c + 8 * q < a.save_ld[l])
+                                            *reinterpret_cast<uint4*>(save + (size_t)(c + 8 * q) * 2) =
+                                                make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                                    }
+                                }
                                 const float4* w4 = reinterpret_cast<const float4*>(bias_s + a.n_hidden * a.nmax + c);
 #pragma unroll
                                 for (int u = 0; u < 4; ++u) {
@@ -361,7 +384,10 @@ cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s, int ctas
     int nslab_max = 1;
     for (int l = 0; l < a.n_hidden; ++l) nslab_max = a.nslab[l] > nslab_max ? a.nslab[l] : nslab_max;
     const size_t smem = mlp_tc_smem_bytes(nslab_max, a.nmax, a.n_hidden);
-    auto kern = a.fmt == 1 ? mlp_tc_kernel<1> : mlp_tc_kernel<0>;
+    bool save = false;
+    for (int l = 0; l < a.n_hidden; ++l) save = save || a.save_act[l] != nullptr;
+    auto kern = a.fmt == 1 ? (save ? mlp_tc_kernel<1, true> : mlp_tc_kernel<1, false>)
+                           : (save ? mlp_tc_kernel<0, true> : mlp_tc_kernel<0, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int cap = (ctas > 0 && ctas < num_sms) ? ctas : num_sms;   // at most one resident CTA per SM

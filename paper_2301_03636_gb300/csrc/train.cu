@@ -354,11 +354,12 @@ cudaError_t launch_adam_update(const ModelLayout& L, uint8_t* P, const float* gr
 
 cudaError_t launch_train_step_ex(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
                                  const MlpDesc& md, LtContext* lt, int fmt, const int32_t* feat, const float* labels,
-                                 int64_t n, const TrainOptions& o, int64_t step, float* d_loss, cudaStream_t s) {
+                                 int64_t n, const TrainOptions& o, int64_t step, float* d_loss, cudaStream_t s,
+                                 const FusedFwd* ff) {
     float* grad = reinterpret_cast<float*>(TW + T.grad);
     float* loss = reinterpret_cast<float*>(TW + T.loss);
     cudaError_t e = fmt == 0 ? launch_forward_saved(L, T, TW, md, feat, n, nullptr, s)
-                             : launch_forward_saved_tc(L, T, TW, md, lt, fmt, feat, n, nullptr, s);
+                             : launch_forward_saved_tc(L, T, TW, md, lt, fmt, feat, n, nullptr, s, ff);
     if (e != cudaSuccess) return e;
     e = launch_mse_loss(L, T, TW, labels, n, o.loss == 1 ? nullptr : d_loss, s);
     if (e != cudaSuccess) return e;

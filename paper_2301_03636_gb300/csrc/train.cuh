@@ -71,10 +71,28 @@ struct TrainOptions {
     float alpha;
 };
 struct LtContext;
+
+// The 16-bit training forward through the fused tensor-core scorer (for
+// models it covers, hidden widths multiples of 8): one launch packs this
+// step's weights (the scorer's swizzled 16-bit images, the padded biases and
+// output row, and the row-major 16-bit copies the backward GEMMs use), the
+// features are standardised into the scorer's image and the row-major copy,
+// and the scorer writes each hidden layer's activations and the output.
+struct FusedFwd {
+    TcArgs tc;                              // scores -> the output y; save_act set by the forward
+    uint8_t* x_img;                         // workspace image of the batch
+    int num_sms, ctas;
+    uint8_t* img16[2][ADV_MAX_LAYERS];      // [BF16, FP16][hidden layer] images in the parameter block
+    float* bias_pad[ADV_MAX_LAYERS];
+    float* wout_pad;
+};
+
 // One training step with these options; fmt 0 FP32 SIMT, 1 BF16, 2 FP16.
+// ff (nullable): the fused forward for fmt 1 / 2.
 cudaError_t launch_train_step_ex(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
                                  const MlpDesc& md, LtContext* lt, int fmt, const int32_t* feat, const float* labels,
-                                 int64_t n, const TrainOptions& o, int64_t step, float* d_loss, cudaStream_t s);
+                                 int64_t n, const TrainOptions& o, int64_t step, float* d_loss, cudaStream_t s,
+                                 const FusedFwd* ff = nullptr);
 
 // 16-bit operands on the tensor cores (train_tc.cu); fmt 1 BF16, 2 FP16.
 struct LtContext;
@@ -82,12 +100,12 @@ LtContext* lt_create();
 void lt_destroy(LtContext* c);
 cudaError_t launch_forward_saved_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
                                     LtContext* lt, int fmt, const int32_t* feat, int64_t n, float* d_y,
-                                    cudaStream_t s);
+                                    cudaStream_t s, const FusedFwd* ff = nullptr);
 cudaError_t launch_backward_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
                                LtContext* lt, int fmt, const float* d_dy, int64_t n, float* d_grad, cudaStream_t s);
 cudaError_t launch_train_step_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
                                  const MlpDesc& md, LtContext* lt, int fmt, const int32_t* feat, const float* labels,
                                  int64_t n, const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const FusedFwd* ff = nullptr);
 
 }  // namespace adv

@@ -501,11 +501,141 @@ struct Tc {
 
 }  // namespace
 
+// One launch per step: for every hidden layer the scorer's swizzled BF16 and
+// FP16 images (as pack_w16_kernel), the row-major copy in the training format,
+// the zero-padded bias, and the padded output row.
+struct PackTrainArgs {
+    const float* W[ADV_MAX_LAYERS];
+    const float* b[ADV_MAX_LAYERS];
+    int fo[ADV_MAX_LAYERS], fi[ADV_MAX_LAYERS], npad[ADV_MAX_LAYERS], kpad[ADV_MAX_LAYERS], npad8[ADV_MAX_LAYERS];
+    uint8_t* img_bf16[ADV_MAX_LAYERS];
+    uint8_t* img_f16[ADV_MAX_LAYERS];
+    void* rm[ADV_MAX_LAYERS];
+    float* bias_pad[ADV_MAX_LAYERS];
+    int64_t start[ADV_MAX_LAYERS + 1];   // first chunk of each layer; start[n_hidden] = the output row's
+    const float* w_out;
+    int w_out_n, w_out_pad_n;
+    float* wout_pad;
+    int n_hidden;
+};
+
+template <typename T>
+__global__ void pack_train_kernel(const __grid_constant__ PackTrainArgs p) {
+    const int64_t total = p.start[p.n_hidden] + p.w_out_pad_n;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
+        if (c >= p.start[p.n_hidden]) {   // the padded output row
+            const int j = (int)(c - p.start[p.n_hidden]);
+            p.wout_pad[j] = j < p.w_out_n ? p.w_out[j] : 0.f;
+            continue;
+        }
+        int l = 0;
+        while (c >= p.start[l + 1]) ++l;
+        const int64_t cl = c - p.start[l];
+        const int fo = p.fo[l], fi = p.fi[l];
+        const int64_t img_chunks = (int64_t)p.npad[l] * p.kpad[l] / 8;
+        if (cl >= img_chunks) {           // the padded bias
+            const int j = (int)(cl - img_chunks);
+            p.bias_pad[l][j] = j < fo ? p.b[l][j] : 0.f;
+            continue;
+        }
+        const int n = (int)(cl / (p.kpad[l] / 8));
+        const int kc = (int)(cl % (p.kpad[l] / 8));
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = kc * 8 + e;
+            v[e] = (n < fo && k < fi) ? p.W[l][(size_t)n * fi + k] : 0.f;
+        }
+        uint32_t wb[4], wh[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+            __half2 hh = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+            wb[i] = *reinterpret_cast<uint32_t*>(&hb);
+            wh[i] = *reinterpret_cast<uint32_t*>(&hh);
+        }
+        const size_t off = (size_t)(kc / 8) * p.npad[l] * ADV_SLAB_ROW_BYTES + sw128_offset((uint32_t)n, (uint32_t)(kc % 8));
+        *reinterpret_cast<uint4*>(p.img_bf16[l] + off) = make_uint4(wb[0], wb[1], wb[2], wb[3]);
+        *reinterpret_cast<uint4*>(p.img_f16[l] + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+        if (n < fo) {
+            T* rm = reinterpret_cast<T*>(p.rm[l]) + (size_t)n * fi;
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (kc * 8 + e < fi) rm[kc * 8 + e] = to16<T>(v[e]);
+        }
+    }
+}
+
+template <typename T>
+static cudaError_t forward_fused(const ModelLayout& L, const TrainLayout& Tl, uint8_t* TW, const MlpDesc& md,
+                                 int fmt, const int32_t* feat, int64_t n, const FusedFwd& ff, cudaStream_t s) {
+    PackTrainArgs p{};
+    p.n_hidden = L.n_hidden;
+    int64_t at = 0;
+    for (int l = 0; l < L.n_hidden; ++l) {
+        p.W[l] = md.W[l];
+        p.b[l] = md.b[l];
+        p.fo[l] = L.widths[l + 1];
+        p.fi[l] = L.widths[l];
+        p.npad[l] = L.npad[l];
+        p.kpad[l] = L.kpad[l];
+        p.npad8[l] = L.npad8[l];
+        p.img_bf16[l] = ff.img16[0][l];
+        p.img_f16[l] = ff.img16[1][l];
+        p.rm[l] = TW + Tl.w16[l];
+        p.bias_pad[l] = ff.bias_pad[l];
+        p.start[l] = at;
+        at += (int64_t)L.npad[l] * L.kpad[l] / 8 + L.npad8[l];
+    }
+    p.start[L.n_hidden] = at;
+    p.w_out = md.W[L.n_hidden];
+    p.w_out_n = L.widths[L.n_hidden];
+    p.w_out_pad_n = L.npad8[L.n_hidden - 1];
+    p.wout_pad = ff.wout_pad;
+    const int64_t total = at + p.w_out_pad_n;
+    pack_train_kernel<T><<<grid_n(total), 256, 0, s>>>(p);
+    T* x16 = reinterpret_cast<T*>(TW + Tl.x16);
+    if (vec_ok(n, L.F) && L.F % 8 == 0)
+        stdz16_vec_kernel<T><<<grid_n(n * L.F / 8), 256, 0, s>>>(feat, (int)n, L.F, md.sa, md.sc, x16);
+    else
+        stdz16_kernel<T><<<grid_n(n * L.F), 256, 0, s>>>(feat, n, L.F, md.sa, md.sc, x16);
+    adv_count_launch(2);
+    const int64_t npad_rows = ((n + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
+    cudaError_t e = launch_standardize(feat, nullptr, n, npad_rows, ff.x_img, L.nslab[0], md.sa, md.sc, L.F,
+                                       fmt == 1 ? 1 : 2, s);
+    if (e != cudaSuccess) return e;
+    TcArgs a = ff.tc;
+    a.x_img = ff.x_img;
+    a.n_rows = n;
+    a.n_tiles = (int)(npad_rows / ADV_TILE_M);
+    a.status = nullptr;
+    a.scores = reinterpret_cast<float*>(TW + Tl.act[L.n_layers]);
+    a.fmt = fmt == 1 ? 1 : 0;   // instruction-descriptor code
+    for (int l = 0; l < L.n_hidden; ++l) {
+        a.w_img[l] = ff.img16[fmt == 1 ? 0 : 1][l];
+        a.save_act[l] = TW + Tl.h16[l];
+        a.save_ld[l] = L.widths[l + 1];
+    }
+    return launch_mlp_tc(a, ff.num_sms, s, ff.ctas);
+}
+
+// Whether the fused forward covers this model: the fused scorer fits and
+// every hidden layer's row-major activations keep 16-byte chunks aligned.
+static bool fused_forward_ok(const ModelLayout& L) {
+    if (!L.tc_ok || L.n_hidden < 1) return false;
+    for (int l = 0; l < L.n_hidden; ++l)
+        if (L.widths[l + 1] % 8 != 0) return false;
+    return true;
+}
+
 cudaError_t launch_forward_saved_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
                                     LtContext* lt, int fmt, const int32_t* feat, int64_t n, float* d_y,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, const FusedFwd* ff) {
     cudaError_t e;
-    if (fmt == 1) e = Tc<__nv_bfloat16>{L, T, TW, md, lt, CUDA_R_16BF}.forward(feat, n, s);
+    if (ff && fused_forward_ok(L))
+        e = fmt == 1 ? forward_fused<__nv_bfloat16>(L, T, TW, md, fmt, feat, n, *ff, s)
+                     : forward_fused<__half>(L, T, TW, md, fmt, feat, n, *ff, s);
+    else if (fmt == 1) e = Tc<__nv_bfloat16>{L, T, TW, md, lt, CUDA_R_16BF}.forward(feat, n, s);
     else e = Tc<__half>{L, T, TW, md, lt, CUDA_R_16F}.forward(feat, n, s);
     if (e != cudaSuccess || !d_y) return e;
     return launch_copy_f32(reinterpret_cast<const float*>(TW + T.act[L.n_layers]), d_y, n, s);
@@ -524,9 +654,9 @@ cudaError_t launch_backward_tc(const ModelLayout& L, const TrainLayout& T, uint8
 cudaError_t launch_train_step_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
                                  const MlpDesc& md, LtContext* lt, int fmt, const int32_t* feat, const float* labels,
                                  int64_t n, const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const FusedFwd* ff) {
     float* grad = d_grad_out ? d_grad_out : reinterpret_cast<float*>(TW + T.grad);
-    cudaError_t e = launch_forward_saved_tc(L, T, TW, md, lt, fmt, feat, n, nullptr, s);
+    cudaError_t e = launch_forward_saved_tc(L, T, TW, md, lt, fmt, feat, n, nullptr, s, ff);
     if (e != cudaSuccess) return e;
     e = launch_mse_loss(L, T, TW, labels, n, d_loss, s);
     if (e != cudaSuccess) return e;
