@@ -230,7 +230,7 @@ __global__ void stdz16_vec_kernel(const int32_t* __restrict__ feat, int n, int F
 // (the bias gradient), and in MODE 1 part1[block][j] = sum_r dy[r] h[r][j]
 // (the output-row gradient).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) dz_colsum16_kernel(const float* __restrict__ c, const float* __restrict__ dy,
+__global__ void __launch_bounds__(256) dz_colsum16_kernel(const void* __restrict__ c, const float* __restrict__ dy,
                                                           const float* __restrict__ wo, const T* __restrict__ h,
                                                           int n, int w, T* __restrict__ dz, float* __restrict__ part0,
                                                           float* __restrict__ part1) {
@@ -248,7 +248,9 @@ __global__ void __launch_bounds__(256) dz_colsum16_kernel(const float* __restric
         float hv[8], g[8], o[8];
         unpack8<T>(reinterpret_cast<const uint4*>(h)[v], hv);
         if (MODE == 0) {
-            load8f(c + (size_t)v * 8, g);
+            load8f(reinterpret_cast<const float*>(c) + (size_t)v * 8, g);
+        } else if (MODE == 2) {   // dX already rounded to 16 bits by the GEMM: the same dZ as rounding after the mask
+            unpack8<T>(reinterpret_cast<const uint4*>(c)[v], g);
         } else {
             const float d = dy[r];
 #pragma unroll
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(256) dz_colsum16_kernel(const float* __restric
 struct LtContext {
     cublasLtHandle_t h = nullptr;
     struct Entry {
-        int key[9];
+        int key[10];
         cublasLtMatmulAlgo_t algo;
         bool used = false;
     };
@@ -316,10 +318,13 @@ void lt_destroy(LtContext* c) {
 
 // Column-major D[m x n] (FP32, ld ldd) = op(A) op(B) with 16-bit A (stored
 // ta ? k x m : m x k, ld lda) and B (stored tb ? n x k : k x n, ld ldb).
+// D = op(A) op(B) in FP32 accumulation, D stored as dt (FP32, or the operands'
+// 16-bit type, rounded to nearest).
 static cudaError_t lt_gemm(LtContext* c, bool ta, bool tb, int m, int n, int k, const void* A, int lda, const void* B,
-                           int ldb, float* D, int ldd, cudaDataType_t ab, void* ws, size_t ws_bytes, cudaStream_t s) {
+                           int ldb, void* D, int ldd, cudaDataType_t ab, void* ws, size_t ws_bytes, cudaStream_t s,
+                           cudaDataType_t dt = CUDA_R_32F) {
     if (!c) return cudaErrorInvalidValue;
-    const int key[9] = {ta, tb, m, n, k, lda, ldb, ldd, (int)ab};
+    const int key[10] = {ta, tb, m, n, k, lda, ldb, ldd, (int)ab, (int)dt};
     cublasLtMatmulDesc_t op = nullptr;
     cublasLtMatrixLayout_t la = nullptr, lb = nullptr, ld = nullptr;
     cublasStatus_t st = cublasLtMatmulDescCreate(&op, CUBLAS_COMPUTE_32F, CUDA_R_32F);
@@ -328,10 +333,10 @@ static cudaError_t lt_gemm(LtContext* c, bool ta, bool tb, int m, int n, int k, 
     if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSB, &opb, sizeof(opb));
     if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatrixLayoutCreate(&la, ab, ta ? k : m, ta ? m : k, lda);
     if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatrixLayoutCreate(&lb, ab, tb ? n : k, tb ? k : n, ldb);
-    if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatrixLayoutCreate(&ld, CUDA_R_32F, m, n, ldd);
+    if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatrixLayoutCreate(&ld, dt, m, n, ldd);
     LtContext::Entry* hit = nullptr;
     for (auto& e : c->cache)
-        if (e.used && std::equal(key, key + 9, e.key)) { hit = &e; break; }
+        if (e.used && std::equal(key, key + 10, e.key)) { hit = &e; break; }
     if (st == CUBLAS_STATUS_SUCCESS && !hit) {
         cublasLtMatmulPreference_t pref = nullptr;
         st = cublasLtMatmulPreferenceCreate(&pref);
@@ -347,7 +352,7 @@ static cudaError_t lt_gemm(LtContext* c, bool ta, bool tb, int m, int n, int k, 
             for (auto& e : c->cache)
                 if (!e.used) { hit = &e; break; }
             if (!hit) hit = &c->cache[0];   // full: replace the first entry
-            std::copy(key, key + 9, hit->key);
+            std::copy(key, key + 10, hit->key);
             hit->algo = res.algo;
             hit->used = true;
         } else if (st == CUBLAS_STATUS_SUCCESS) {
@@ -486,10 +491,11 @@ struct Tc {
                                     grad + L.layer_w_off[l], fi, ab, ws(), T_.lt_ws_bytes, s);
             if (e != cudaSuccess) return e;
             if (l == 0) break;
+            // dX in the 16-bit type: the masked dZ is stored in 16 bits anyway
             e = lt_gemm(lt, false, false, fi, (int)n, fo, w16(l), fi, dz16(cur), fo, c32(), fi, ab, ws(),
-                        T_.lt_ws_bytes, s);
+                        T_.lt_ws_bytes, s, ab);
             if (e != cudaSuccess) return e;
-            dz_colsum16_kernel<T, 0><<<blocks, 256, 0, s>>>(c32(), nullptr, nullptr, h16(l - 1), (int)n, fi,
+            dz_colsum16_kernel<T, 2><<<blocks, 256, 0, s>>>(c32(), nullptr, nullptr, h16(l - 1), (int)n, fi,
                                                             dz16(cur ^ 1), p0, nullptr);
             splitsum(p0, blocks, fi, grad + L.layer_b_off[l - 1], s);
             adv_count_launch(2);
