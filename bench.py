@@ -331,27 +331,38 @@ def dslash_leg(dev, reps=50):
     L = advisor.lib()
     total = torch.empty(1, dtype=torch.int64, device=dev)
 
-    def step():
-        L.advisor_enumerate_variants(ctypes.c_void_p(k.data_ptr()), K, ctypes.c_void_p(v.data_ptr()), n,
-                                     ctypes.c_void_p(off.data_ptr()), ctypes.c_void_p(total.data_ptr()),
-                                     ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
-        m.rank(v, off, "bf16", eps, eps32, best=best, best_score=bsc)
+    eps16 = m.calibrate_eps(fcal, scal, "fp16")
 
-    for _ in range(5):
-        step()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-    for a, b in ev:
-        a.record()
-        step()
-        b.record()
-    torch.cuda.synchronize()
-    ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    def run(e16):
+        def step():
+            L.advisor_enumerate_variants(ctypes.c_void_p(k.data_ptr()), K, ctypes.c_void_p(v.data_ptr()), n,
+                                         ctypes.c_void_p(off.data_ptr()), ctypes.c_void_p(total.data_ptr()),
+                                         ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
+            m.rank(v, off, "bf16", eps, eps32, best=best, best_score=bsc, eps16=e16)
+
+        for _ in range(5):
+            step()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record()
+            step()
+            b.record()
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in ev]))
+
+    ms = run(None)
     c32, c64 = m.rescore_counts()
+    ref = best.clone()
+    ms16 = run(eps16)
+    c16t, c32t, c64t = m.rescore_counts_ex()
     return {"workload": f"{K} Dslash-shaped kernels (depth 4, lattice trip counts), 84 variants each = {n}, "
                         "enumerated on the GPU and ranked with 64-256-256-256-1 (bf16 + re-score)",
             "variants": n, "ms_per_step": ms, "variants_per_s": n / (ms / 1000.0), "kernels_per_s": K / (ms / 1000.0),
-            "near_tie_fp32_rows": c32, "near_tie_fp64_rows": c64}
+            "near_tie_fp32_rows": c32, "near_tie_fp64_rows": c64,
+            "fp16tier": {"ms_per_step": ms16, "variants_per_s": n / (ms16 / 1000.0), "near_tie_fp16_rows": c16t,
+                         "near_tie_fp32_rows": c32t, "near_tie_fp64_rows": c64t,
+                         "same_selection": bool(torch.equal(best, ref))}}
 
 
 def large_sweep_leg(dev, reps=5, rows=0):
