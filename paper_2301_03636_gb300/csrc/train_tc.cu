@@ -224,8 +224,9 @@ __global__ void stdz16_vec_kernel(const int32_t* __restrict__ feat, int n, int F
 }
 
 // dZ = 16-bit(g masked by h > 0) for a block of VEC_ROWS rows, with
-//   MODE 0: g[r][j] = c[r][j]                 (hidden layers)
 //   MODE 1: g[r][j] = dy[r] w_out[j]          (last hidden layer)
+//   MODE 2: g[r][j] = c[r][j], the dX GEMM's result in the 16-bit type (hidden
+//           layers; rounding before the mask gives the same dZ as after it)
 // plus the block's column sums in row order: part0[block][j] = sum_r dZ[r][j]
 // (the bias gradient), and in MODE 1 part1[block][j] = sum_r dy[r] h[r][j]
 // (the output-row gradient).
@@ -247,9 +248,7 @@ __global__ void __launch_bounds__(256) dz_colsum16_kernel(const void* __restrict
         const int v = r * w8 + cg;
         float hv[8], g[8], o[8];
         unpack8<T>(reinterpret_cast<const uint4*>(h)[v], hv);
-        if (MODE == 0) {
-            load8f(reinterpret_cast<const float*>(c) + (size_t)v * 8, g);
-        } else if (MODE == 2) {   // dX already rounded to 16 bits by the GEMM: the same dZ as rounding after the mask
+        if (MODE == 2) {
             unpack8<T>(reinterpret_cast<const uint4*>(c)[v], g);
         } else {
             const float d = dy[r];
