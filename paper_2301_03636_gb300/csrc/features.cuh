@@ -277,24 +277,27 @@ __device__ __forceinline__ void row_features(const int64_t (&d)[16], int32_t (&f
     uint64_t x[N];
     row_log_args<F>(d, x);
     int32_t L[N];
+    // Logarithms that follow from others are not computed again:
+    //  - L(min(T, P)) = min(L(T), L(P)): the digit-by-digit logarithm is
+    //    non-decreasing (a larger argument has a larger exponent, or the same
+    //    exponent and a mantissa whose truncated squarings never fall below);
+    //  - level 0's prefix product is trip[0] and its suffix product the whole
+    //    trip product (trips past the depth are 1 in a valid row).
+    constexpr int M = N - (F >= 64 ? 3 : 1);
+    auto derived = [](int i) { return i == A_MIN || (F >= 64 && (i == A_LEVEL || i == A_LEVEL + 1)); };
+    uint64_t y[M];
+    int32_t ly[M];
+#pragma unroll
+    for (int i = 0, j = 0; i < N; ++i)
+        if (!derived(i)) y[j++] = x[i];
+    log2_q16_batch<M>(y, ly);
+#pragma unroll
+    for (int i = 0, j = 0; i < N; ++i)
+        if (!derived(i)) L[i] = ly[j++];
+    L[A_MIN] = L[A_T] < L[A_PAR] ? L[A_T] : L[A_PAR];
     if constexpr (F >= 64) {
-        // level 0's prefix product is trip[0] and its suffix product the whole trip
-        // product (trips past the depth are 1 in a valid row): their logarithms are
-        // copied instead of computed again
-        constexpr int M = N - 2;
-        uint64_t y[M];
-        int32_t ly[M];
-#pragma unroll
-        for (int i = 0, j = 0; i < N; ++i)
-            if (i != A_LEVEL && i != A_LEVEL + 1) y[j++] = x[i];
-        log2_q16_batch<M>(y, ly);
-#pragma unroll
-        for (int i = 0, j = 0; i < N; ++i)
-            if (i != A_LEVEL && i != A_LEVEL + 1) L[i] = ly[j++];
         L[A_LEVEL] = L[A_T0];
         L[A_LEVEL + 1] = L[A_T];
-    } else {
-        log2_q16_batch<N>(x, L);
     }
     row_features_from_logs<F>(d, L, f);
 }

@@ -59,3 +59,19 @@ def test_against_float_log_small_known_values():
     assert oracle.log2_q16([3]).tolist()[0] in (103871, 103872)
     assert oracle.log2_q16([10]).tolist()[0] in (217705, 217706)
     assert math.floor(65536 * math.log2(3)) == 103872
+
+
+def test_log_of_min_is_min_of_logs():
+    """The digit-by-digit logarithm is non-decreasing, so L(min(a, b)) =
+    min(L(a), L(b)) exactly (the GPU feature kernels derive L(min(T, P)) that
+    way instead of computing it again)."""
+    rng = np.random.default_rng(17)
+    a = rng.integers(1, 2**62, 50000, dtype=np.uint64) >> rng.integers(0, 62, 50000).astype(np.uint64)
+    b = rng.integers(1, 2**62, 50000, dtype=np.uint64) >> rng.integers(0, 62, 50000).astype(np.uint64)
+    a = np.maximum(a, np.uint64(1))
+    b = np.maximum(b, np.uint64(1))
+    la, lb = oracle.log2_q16(a), oracle.log2_q16(b)
+    assert np.array_equal(oracle.log2_q16(np.minimum(a, b)), np.minimum(la, lb))
+    # neighbours, where a truncation could in principle reorder the values
+    x = rng.integers(2**20, 2**62, 20000, dtype=np.uint64)
+    assert (oracle.log2_q16(x + np.uint64(1)) >= oracle.log2_q16(x)).all()
