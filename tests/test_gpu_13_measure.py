@@ -139,3 +139,27 @@ def test_staged_copy_rank_equals_rank(gpu_lib, n_stages):
     torch.cuda.synchronize()
     b_ref, _ = m.rank(dd, ot, "bf16", eps=0.05, eps32=1e-4)
     assert torch.equal(b_plan, b_ref)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_staged_copy_rank_wide_model(gpu_lib, precision):
+    """The staged copy-in on a model scored layer by layer (hidden width 1024),
+    including E4M3 layers: the same selections as advisor_rank."""
+    widths = (128, 1024, 1024, 1024, 1)
+    off = W.make_segments(96, 2, 64, seed=35)
+    n = int(off[-1])
+    d = W.make_descriptors(n, 35)
+    m = advisor.Model(widths, max_rows=max(n, 16384), max_kernels=96)
+    cal = torch.from_numpy(W.calibration_descriptors(16384)).cuda()
+    fcal, scal = advisor.advisor_extract_features(cal, 128)
+    mu, sg = advisor.advisor_fit_standardizer(fcal, scal)
+    m.set_params(W.make_weights(widths, 35), mu, sg)
+    m.calibrate_fp8(fcal)
+    eps, eps32 = m.calibrate_eps(fcal, scal, precision), m.calibrate_eps(fcal, scal, "fp32")
+    dd, ot = torch.from_numpy(d).cuda(), torch.from_numpy(off).cuda()
+    b_ref, s_ref = m.rank(dd, ot, precision, eps=eps, eps32=eps32)
+    stage = torch.zeros_like(dd)
+    b, s = m.rank_staged(torch.from_numpy(d).pin_memory(), stage, ot, precision, eps=eps, eps32=eps32, n_stages=5)
+    torch.cuda.synchronize()
+    assert torch.equal(b, b_ref) and torch.equal(s, s_ref)
+    assert m.device_status() == 0
