@@ -665,6 +665,8 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = n * world / (ms / 1000.0)
+    # rows the last replay sent to the FP32 and FP64 re-score tiers
+    c32, c64 = m.rescore_counts()
 
     # ---- end to end through the public API with host buffers ----
     desc_h = torch.from_numpy(desc_np).pin_memory()
@@ -770,6 +772,7 @@ def main():
            "config": {"workload": WL.name, "kernels": K, "variants": n, "features": WL.n_features,
                       "mlp": "-".join(map(str, WL.widths)), "precision": prec, "l2": "flushed (512 MB write) "
                       "between steps", "near_tie_rescore": "fp32 then fp64", "eps": eps, "eps32": eps32,
+                      "near_tie_fp32_rows": c32, "near_tie_fp64_rows": c64, "near_tie_fraction": c32 / n,
                       "batching": "one CUDA graph per step (advisor_plan_rank, autotuned launch shapes)",
                       "launch_config": tuned["config"], "kernels_per_step": tuned["kernels_per_replay"]},
            "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clk}

@@ -102,6 +102,8 @@ def test_plan_replays_match_direct_and_read_refilled_inputs(gpu_lib, setup):
     d = torch.from_numpy(setup["d_a"]).cuda()
     o = torch.from_numpy(setup["off"]).cuda()
     direct_a = _direct(m, d, o, "bf16", eps, eps32)
+    counts_a = m.rescore_counts()
+    assert counts_a[0] > 0   # near ties exist on this workload
     plan = m.plan_rank(d, o, "bf16", eps, eps32, autotune=False)
     info = plan.info()
     assert info["kernels_per_replay"] == 7   # extract, scorer, tier 1, FP32, tier 2, FP64, final
@@ -113,6 +115,7 @@ def test_plan_replays_match_direct_and_read_refilled_inputs(gpu_lib, setup):
     assert advisor.launch_count() - n0 == 3 * info["kernels_per_replay"]
     for a, b in zip((plan.best, plan.best_score, plan.scores, plan.status), direct_a):
         assert torch.equal(a, b)
+    assert m.rescore_counts() == counts_a   # a replay leaves the tier counts the direct call leaves
     # refill the bound descriptor buffer in place: the next replay ranks the new rows
     d.copy_(torch.from_numpy(setup["d_b"]).cuda())
     plan.launch()
