@@ -47,7 +47,7 @@ typedef enum {
     ADVISOR_ERR_OUT_OF_MEMORY = 3,    /* workspace or parameter block too small */
     ADVISOR_ERR_CUDA = 4,
     ADVISOR_ERR_TIMEOUT = 5,          /* device status: a bounded wait gave up */
-    ADVISOR_ERR_UNSUPPORTED = 6,      /* shape or precision this build does not run */
+    ADVISOR_ERR_UNSUPPORTED = 6,      /* shape or precision the library does not run */
     ADVISOR_ERR_BAD_SEGMENTS = 7      /* device status: segment offsets not monotone / out of range */
 } advisor_status;
 

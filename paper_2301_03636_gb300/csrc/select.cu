@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) select_tier2_kernel(SelectArgs a) {
 // fp64(r*) + eps16 <= fp64(r16) + eps16 <= y16(r16) + 2 eps16, r16 the FP16
 // minimum, so only candidates within 2*eps16 of that minimum go on to FP32.
 // A candidate whose FP16 value is not finite (FP16 range exceeded) cannot be
-// judged at this tier and always goes on.  Survivors are appended in
+// ruled out at this tier and always goes on.  Survivors are appended in
 // candidate order to cand_mid_rows; a kernel with a single survivor is
 // decided here.
 __device__ __forceinline__ bool mid_keep(float v, double thr) { return !finite_score(v) || (double)v <= thr; }
