@@ -44,11 +44,45 @@ D3_LEVELS = [
 ]
 
 
-@pytest.mark.parametrize("d,base,levels", [(D1, D1_BASE, D1_LEVELS), (D3, D3_BASE, D3_LEVELS)])
-def test_hand_worked(d, base, levels):
+# depth 2, trips (32, 16), flops 4, bytes 16, h2d 2^20, d2h 0, 256 teams x 64
+# threads, 'teams distribute parallel for collapse(2)' on loop 0 (combined:
+# both loops distributed and parallel), dynamic, data mode 0.
+D2 = desc(2, [32, 16], 4, 16, 1 << 20, 0, 256, 64, 0, 0, 2, 1, 0)
+# T = 2^9, FL = 2^11, BY = 2^13, MB = 2^20, P = 2^14, D = Q = 32*16 = 2^9
+D2_BASE = [2 * Q, 5 * Q, 4 * Q, 0, 0, 9 * Q, 2 * Q, 4 * Q, 11 * Q, 13 * Q, 20 * Q, 0, 20 * Q, 8 * Q, 6 * Q,
+           14 * Q, 9 * Q, 9 * Q, 0, 1 * Q, 3 * Q, -2 * Q, -7 * Q, 0, Q, 0, 0, 0, 0, 2 * Q, Q, 9 * Q]
+D2_LEVELS = [
+    [5 * Q, Q, Q, Q, 5 * Q, 9 * Q, 9 * Q, 7 * Q],
+    [4 * Q, Q, Q, Q, 9 * Q, 4 * Q, 8 * Q, 6 * Q],
+    [0] * 8,
+    [0] * 8,
+]
+
+# depth 4 (the Dslash nest shape), trips (32, 32, 32, 16), flops 1024, bytes
+# 2048, h2d = d2h = 2^24, 1024 teams x 128 threads, 'teams distribute
+# collapse(2)' on loops 0-1 and 'parallel for collapse(2)' on loops 2-3,
+# static, data mode 1.
+D4 = desc(4, [32, 32, 32, 16], 1024, 2048, 1 << 24, 1 << 24, 1024, 128, 2, 2, 2, 0, 1)
+# T = 2^19, FL = 2^29, BY = 2^30, MB = 2^25, P = 2^17, D = 2^10, Q = 2^9
+D4_BASE = [4 * Q, 5 * Q, 5 * Q, 5 * Q, 4 * Q, 19 * Q, 10 * Q, 11 * Q, 29 * Q, 30 * Q, 24 * Q, 24 * Q, 25 * Q,
+           10 * Q, 7 * Q, 17 * Q, 10 * Q, 9 * Q, 2 * Q, 0, 2 * Q, -1 * Q, 5 * Q, Q, 0, 0, Q, 2 * Q, 2 * Q,
+           2 * Q, 0, 17 * Q]
+D4_LEVELS = [
+    [5 * Q, Q, 0, Q, 5 * Q, 19 * Q, 16 * Q, 15 * Q],
+    [5 * Q, Q, 0, Q, 10 * Q, 14 * Q, 16 * Q, 15 * Q],
+    [5 * Q, 0, Q, Q, 15 * Q, 9 * Q, 16 * Q, 15 * Q],
+    [4 * Q, 0, Q, Q, 19 * Q, 4 * Q, 15 * Q, 14 * Q],
+]
+
+
+@pytest.mark.parametrize("d,base,levels,collapsed", [(D1, D1_BASE, D1_LEVELS, 1), (D2, D2_BASE, D2_LEVELS, 2),
+                                                     (D3, D3_BASE, D3_LEVELS, 3), (D4, D4_BASE, D4_LEVELS, 4)])
+def test_hand_worked(d, base, levels, collapsed):
     f32, st = oracle.extract_features(d, 32)
     assert st.tolist() == [0]
     assert f32[0].tolist() == base
+    f33, _ = oracle.extract_features(d, 33)   # the base features and dist_collapse + pf_collapse
+    assert f33[0].tolist() == base + [collapsed * Q]
     f64, _ = oracle.extract_features(d, 64)
     assert f64[0, :32].tolist() == base
     assert f64[0, 32:].tolist() == sum(levels, [])
