@@ -29,6 +29,22 @@ def test_random_rows_bit_exact(gpu_lib, F, n):
     assert np.array_equal(f.cpu().numpy(), f_ref)
 
 
+@pytest.mark.parametrize("F", [32, 33, 64])
+def test_hand_worked_rows(gpu_lib, F):
+    """The four hand-worked descriptors of the oracle's pins, on the GPU:
+    every feature equals the value written out by hand."""
+    from tests.test_oracle_features import (D1, D1_BASE, D1_LEVELS, D2, D2_BASE, D2_LEVELS, D3, D3_BASE,
+                                            D3_LEVELS, D4, D4_BASE, D4_LEVELS, Q)
+    d = np.stack([D1, D2, D3, D4])
+    want = []
+    for base, levels, collapsed in ((D1_BASE, D1_LEVELS, 1), (D2_BASE, D2_LEVELS, 2), (D3_BASE, D3_LEVELS, 3),
+                                    (D4_BASE, D4_LEVELS, 4)):
+        want.append(base if F == 32 else base + [collapsed * Q] if F == 33 else base + sum(levels, []))
+    f, st = advisor.advisor_extract_features(torch.from_numpy(d).cuda(), F)
+    assert st.cpu().numpy().tolist() == [0, 0, 0, 0]
+    assert f.cpu().numpy().tolist() == want
+
+
 def test_empty_call(gpu_lib):
     f, st = advisor.advisor_extract_features(torch.empty((0, 16), dtype=torch.int64, device="cuda"), 64)
     assert f.shape == (0, 64) and st.shape == (0,)
