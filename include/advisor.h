@@ -511,6 +511,16 @@ advisor_status advisor_model_set_profile_events(advisor_model_t m, void* ev_star
  * denominator of the FP32 scorer's roofline.  Synchronises `stream`. */
 advisor_status advisor_measure_fp32_fma_peak(double* h_tflops, cudaStream_t stream);
 
+/* Failure-detection self-test of the device-side bounded waits: launches one
+ * thread that waits, with the bounded mbarrier wait every pipelined kernel of
+ * the library uses, on a barrier nothing arrives at.  After timeout_ns
+ * (1,000 .. 1,000,000,000 ns, else ADVISOR_ERR_INVALID_ARGUMENT) the wait
+ * gives up, records the timeout in the model's status word and the kernel
+ * returns, leaving no copy in flight and no tensor memory held: the next
+ * advisor_get_device_status returns ADVISOR_ERR_TIMEOUT (and clears it), and
+ * the model stays usable.  Asynchronous on `stream`. */
+advisor_status advisor_model_check_wait_timeout(advisor_model_t m, int64_t timeout_ns, cudaStream_t stream);
+
 /* Number of kernels this library launched since load (host-side counter of
  * successful launches; for launch accounting in benchmarks). */
 int64_t advisor_launch_count(void);

@@ -66,6 +66,7 @@ def lib():
         "advisor_rank_topn_ex": (st, [P, P, i64, P, i64, i32, st, f32, f32, f32, P, P, P, P, P]),
         "advisor_get_rescore_counts_ex": (st, [P, P, P]),
         "advisor_measure_fp32_fma_peak": (st, [P, P]),
+        "advisor_model_check_wait_timeout": (st, [P, i64, P]),
         "advisor_train_step": (st, [P, P, P, i64, st, P, P, P]),
         "advisor_loss_grad": (st, [P, P, P, i64, st, P, P, P]),
         "advisor_get_device_status": (st, [P, P]),
@@ -440,6 +441,13 @@ class Model:
 
     def device_status(self, stream=None) -> int:
         return int(lib().advisor_get_device_status(self.handle, _stream(stream)))
+
+    def check_wait_timeout(self, timeout_ns: int, stream=None):
+        """Failure-detection self-test: a bounded device wait on a barrier nothing
+        arrives at runs out after timeout_ns and records the timeout in the status
+        word (advisor_model_check_wait_timeout); read it with device_status()."""
+        _check(lib().advisor_model_check_wait_timeout(self.handle, int(timeout_ns), _stream(stream)),
+               "advisor_model_check_wait_timeout")
 
     def calibrate_fp8(self, feat, stream=None):
         """Static per-tensor activation scales for FP8 scoring from a calibration

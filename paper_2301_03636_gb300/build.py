@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libadvisor.so")
 SOURCES = ["api.cu", "extract.cu", "mlp_simt.cu", "mlp_tc.cu", "mlp_layer_tc.cu", "select.cu", "pack.cu", "train.cu",
-           "train_tc.cu", "noalloc.cu", "plan.cu", "enumerate.cu", "peak.cu"]
+           "train_tc.cu", "noalloc.cu", "plan.cu", "enumerate.cu", "peak.cu",
+           "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -10,6 +10,7 @@
 #include "pack.cuh"
 #include "train.cuh"
 #include "noalloc.cuh"
+#include "selftest.cuh"
 
 namespace {
 
@@ -1086,6 +1087,14 @@ advisor_status advisor_get_device_status(advisor_model_t m, cudaStream_t stream)
     if (h & ADV_DEV_TIMEOUT) return ADVISOR_ERR_TIMEOUT;
     if (h & ADV_DEV_BAD_SEGMENTS) return ADVISOR_ERR_BAD_SEGMENTS;
     return ADVISOR_OK;
+}
+
+advisor_status advisor_model_check_wait_timeout(advisor_model_t m, int64_t timeout_ns, cudaStream_t stream) {
+    if (!m || !m->P) return ADVISOR_ERR_INVALID_ARGUMENT;
+    if (timeout_ns < 1000 || timeout_ns > 1000000000) return ADVISOR_ERR_INVALID_ARGUMENT;
+    return adv::launch_wait_timeout_check(status_word(m), (uint64_t)timeout_ns, stream) == cudaSuccess
+               ? ADVISOR_OK
+               : ADVISOR_ERR_CUDA;
 }
 
 // Read-only view of a bound model for the no-allocation scoring entry point
