@@ -46,6 +46,24 @@ def test_standardizer_against_moments():
     assert np.all(sigma[sd == 0] == 1.0)  # e.g. level-3 features of depth <= 3 rows
 
 
+def test_standardizer_closed_form():
+    """Feature j of valid row i is a_j when i is even and b_j when i is odd
+    (equal counts): the mean is (a_j + b_j) / 2 and the population standard
+    deviation |a_j - b_j| / 2, exactly; a constant feature gets sigma 1; rows
+    marked invalid (here carrying huge values) are left out."""
+    F, n = 8, 1000
+    a = np.array([0, 1, 2, 3, -4, 5, 7, 7], dtype=np.int64) * 65536
+    b = np.array([2, 1, 6, 3, 4, -5, 7, 9], dtype=np.int64) * 65536
+    f = np.where((np.arange(n) % 2 == 0)[:, None], a, b).astype(np.int32)
+    st = np.zeros(n, dtype=np.uint8)
+    bad = np.full((3, F), 1 << 30, dtype=np.int32)
+    f = np.concatenate([f, bad])
+    st = np.concatenate([st, np.ones(3, dtype=np.uint8)])
+    mu, sigma = oracle.fit_standardizer(f, st)
+    assert mu.tolist() == [1.0, 1.0, 4.0, 3.0, 0.0, 0.0, 7.0, 8.0]
+    assert sigma.tolist() == [1.0, 1.0, 2.0, 1.0, 4.0, 5.0, 1.0, 1.0]   # constants (j = 1, 3, 6) -> 1
+
+
 def test_zero_weights_constant_output_and_all_ties():
     widths = (32, 16, 16, 1)
     p = np.zeros(W.param_count(widths), dtype=np.float32)
