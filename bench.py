@@ -216,7 +216,7 @@ def serving_leg(dev):
     runs = []
     for rate in (2000, 10000, 50000):
         n = int(min(4000, rate * 0.5))
-        qs = serving.make_queries(n, float(rate), W.SEEDS["c3"] + rate)
+        qs = serving.make_queries(n, float(rate), W.SEEDS["serving"] + rate)
         _, st = serving.run_serving(base, params, mu, sigma, qs, "bf16", eps, eps32, pipelines=3)
         st["rate_per_s"] = rate
         runs.append(st)
@@ -230,8 +230,8 @@ def training_leg(dev, steps=20):
 
     from paper_2301_03636_gb300 import advisor
     wl = W.TRAINING
-    d = torch.from_numpy(W.make_descriptors(65536, W.SEEDS["c4"])).to(dev)
-    t = torch.from_numpy(W.make_labels(d.cpu().numpy(), W.SEEDS["c4"])).to(dev)
+    d = torch.from_numpy(W.make_descriptors(65536, W.SEEDS["training"])).to(dev)
+    t = torch.from_numpy(W.make_labels(d.cpu().numpy(), W.SEEDS["training"])).to(dev)
     f, st = advisor.advisor_extract_features(d, wl.n_features)
     mu, sigma = advisor.advisor_fit_standardizer(f, st)
     m = advisor.Model(wl.widths, max_rows=65536, max_kernels=1, device=dev)

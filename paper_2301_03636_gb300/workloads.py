@@ -43,7 +43,7 @@ F_TEAMS, F_THREADS = 9, 10
 F_PF_POS, F_DIST_COLLAPSE, F_PF_COLLAPSE, F_SCHEDULE, F_DATA_MODE = 11, 12, 13, 14, 15
 
 # Seeds of the named workloads and of the standardisation calibration sample.
-SEEDS = {"c1": 1, "c2": 2, "c3": 3, "c4": 4, "c4_val": 40, "c5": 5}
+SEEDS = {"plain": 1, "batched": 2, "serving": 3, "training": 4, "training_validation": 40, "sweep": 5}
 CALIBRATION_SEED = 0xC0FFEE
 WEIGHT_SEED_OFFSET = 100
 
@@ -199,11 +199,11 @@ class Workload:
 
 
 # The named workloads (sizes from the benchmark descriptions).
-PLAIN_FP32_512 = Workload("plain_fp32_64x8", (32, 128, 128, 1), 64, 8, 8, None, SEEDS["c1"])
-BATCHED_4096 = Workload("batched_4096k_f64_256x3", (64, 256, 256, 256, 1), 4096, 4, 64, None, SEEDS["c2"])
-SERVING = Workload("serving_f32_128x2", (32, 128, 128, 1), 1, 4, 512, None, SEEDS["c3"])
-TRAINING = Workload("train_b65536_f64_256x3", (64, 256, 256, 256, 1), 1, 65536, 65536, None, SEEDS["c4"], "glorot")
-LARGE_SWEEP = Workload("sweep_1m_f128_1024x3", (128, 1024, 1024, 1024, 1), 65536, 2, 64, 1 << 20, SEEDS["c5"])
+PLAIN_FP32_512 = Workload("plain_fp32_64x8", (32, 128, 128, 1), 64, 8, 8, None, SEEDS["plain"])
+BATCHED_4096 = Workload("batched_4096k_f64_256x3", (64, 256, 256, 256, 1), 4096, 4, 64, None, SEEDS["batched"])
+SERVING = Workload("serving_f32_128x2", (32, 128, 128, 1), 1, 4, 512, None, SEEDS["serving"])
+TRAINING = Workload("train_b65536_f64_256x3", (64, 256, 256, 256, 1), 1, 65536, 65536, None, SEEDS["training"], "glorot")
+LARGE_SWEEP = Workload("sweep_1m_f128_1024x3", (128, 1024, 1024, 1024, 1), 65536, 2, 64, 1 << 20, SEEDS["sweep"])
 
 WORKLOADS = {w.name: w for w in (PLAIN_FP32_512, BATCHED_4096, SERVING, TRAINING, LARGE_SWEEP)}
 

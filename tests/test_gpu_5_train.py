@@ -113,9 +113,9 @@ def test_training_is_deterministic_and_resumable(gpu_lib):
 
 def test_training_workload_meets_nrmse_criterion(gpu_lib):
     wl = W.TRAINING
-    d_tr = W.make_descriptors(65536, W.SEEDS["c4"])
-    d_va = W.make_descriptors(16384, W.SEEDS["c4_val"])
-    t_tr, t_va = W.make_labels(d_tr, W.SEEDS["c4"]), W.make_labels(d_va, W.SEEDS["c4_val"])
+    d_tr = W.make_descriptors(65536, W.SEEDS["training"])
+    d_va = W.make_descriptors(16384, W.SEEDS["training_validation"])
+    t_tr, t_va = W.make_labels(d_tr, W.SEEDS["training"]), W.make_labels(d_va, W.SEEDS["training_validation"])
     f_tr, s_tr = advisor.advisor_extract_features(torch.from_numpy(d_tr).cuda(), 64)
     f_va, _ = advisor.advisor_extract_features(torch.from_numpy(d_va).cuda(), 64)
     mu, sigma = advisor.advisor_fit_standardizer(f_tr, s_tr)   # the training split's statistics
@@ -163,9 +163,9 @@ def test_tensor_core_autograd_function(gpu_lib):
 
 def test_tensor_core_training_meets_nrmse_criterion(gpu_lib):
     wl = W.TRAINING
-    d_tr = W.make_descriptors(65536, W.SEEDS["c4"])
-    d_va = W.make_descriptors(16384, W.SEEDS["c4_val"])
-    t_tr, t_va = W.make_labels(d_tr, W.SEEDS["c4"]), W.make_labels(d_va, W.SEEDS["c4_val"])
+    d_tr = W.make_descriptors(65536, W.SEEDS["training"])
+    d_va = W.make_descriptors(16384, W.SEEDS["training_validation"])
+    t_tr, t_va = W.make_labels(d_tr, W.SEEDS["training"]), W.make_labels(d_va, W.SEEDS["training_validation"])
     f_tr, s_tr = advisor.advisor_extract_features(torch.from_numpy(d_tr).cuda(), 64)
     f_va, _ = advisor.advisor_extract_features(torch.from_numpy(d_va).cuda(), 64)
     mu, sigma = advisor.advisor_fit_standardizer(f_tr, s_tr)

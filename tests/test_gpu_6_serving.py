@@ -24,7 +24,7 @@ def served():
     base.set_params(params, mu, sigma)
     eps = base.calibrate_eps(fcal, scal, "bf16")
     eps32 = base.calibrate_eps(fcal, scal, "fp32")
-    queries = serving.make_queries(1500, 20000.0, W.SEEDS["c3"])
+    queries = serving.make_queries(1500, 20000.0, W.SEEDS["serving"])
     done, st = serving.run_serving(base, params, mu, sigma, queries, "bf16", eps, eps32, pipelines=3)
     print("serving stats:", st)
     return dict(base=base, done=done, st=st, eps=eps, eps32=eps32, mu=mu.cpu().numpy(),
