@@ -21,7 +21,9 @@
  *  - Pointers prefixed d_ are device pointers, h_ host pointers.  Device
  *    buffers must be 256-byte aligned (cudaMalloc and torch allocations are).
  *  - Asynchrony: calls enqueue kernels on `stream` and return without
- *    synchronising, except advisor_get_device_status.
+ *    synchronising, except the few whose description says they synchronise
+ *    (advisor_get_device_status, advisor_get_rescore_counts[_ex], plan
+ *    creation, advisor_measure_fp32_fma_peak).
  *  - Errors: argument errors are returned immediately and nothing is
  *    enqueued.  Per-row descriptor errors are reported in d_row_status.
  *    Errors found on the device (malformed segment offsets, a wait that ran
