@@ -52,6 +52,32 @@ def parse():
     return ap.parse_args()
 
 
+def topn_leg(m, desc, offs, eps, eps32, n, flush, stream, top_n=10, reps=50):
+    """Top N per kernel (Fig. 2: the variants sorted by predicted cost, the N
+    best kept) on the batched workload: advisor_rank_topn with the BF16
+    scorer and the tiered re-score, direct calls (not a plan), L2 flushed
+    between calls.  Its first column must equal advisor_rank's selection."""
+    import torch
+    b1, _ = m.rank(desc, offs, "bf16", eps, eps32)
+    for _ in range(3):
+        best, _ = m.rank_topn(desc, offs, top_n, "bf16", eps, eps32)
+    torch.cuda.synchronize()
+    tt = []
+    for i in range(reps):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        best, _ = m.rank_topn(desc, offs, top_n, "bf16", eps, eps32)
+        b.record(stream)
+        tt.append((a, b))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in tt]))
+    c32, c64 = m.rescore_counts()
+    return {"top_n": top_n, "ms_per_step": ms, "variants_per_s": n / (ms / 1000.0), "near_tie_fp32_rows": c32,
+            "near_tie_fp64_rows": c64, "first_column_equals_rank": bool(torch.equal(best[:, 0], b1)),
+            "calls": "advisor_rank_topn, one direct call per step"}
+
+
 def err_stats(y, y64):
     """Max and 99th percentile of |y - y64| over the rows (y64: the FP64 scorer's values)."""
     e = (y.double() - y64.double()).abs().cpu().numpy()
@@ -811,6 +837,10 @@ def main():
             extras[p] = {"variants_per_s": n / (msp / 1000.0), "ms_per_step": msp,
                          **err_stats(y, y64), "eps": e_p}
         out["precisions"] = extras
+        try:
+            out["topn"] = topn_leg(m, desc, offs, eps, eps32, n, flush, stream)
+        except Exception as e:   # reported in the line; the other legs still run
+            out["topn"] = {"error": repr(e)}
         out["serving"] = serving_leg(dev)
         srv10 = [r for r in out["serving"]["runs"] if r["rate_per_s"] == 10000]
         out["p99_query_ms"] = srv10[0]["p99_ms"] if srv10 else None
