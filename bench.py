@@ -52,30 +52,46 @@ def parse():
     return ap.parse_args()
 
 
-def topn_leg(m, desc, offs, eps, eps32, n, flush, stream, top_n=10, reps=50):
+def topn_leg(m, desc, offs, eps, eps32, n, flush, stream, top_n=10, reps=50, eps16=None):
     """Top N per kernel (Fig. 2: the variants sorted by predicted cost, the N
     best kept) on the batched workload: advisor_rank_topn with the BF16
     scorer and the tiered re-score, direct calls (not a plan), L2 flushed
-    between calls.  Its first column must equal advisor_rank's selection."""
+    between calls; with eps16, again with the FP16 tensor-core tier
+    (advisor_rank_topn_ex).  The first column must equal advisor_rank's
+    selection, and the FP16 tier must not change any entry."""
     import torch
     b1, _ = m.rank(desc, offs, "bf16", eps, eps32)
-    for _ in range(3):
-        best, _ = m.rank_topn(desc, offs, top_n, "bf16", eps, eps32)
-    torch.cuda.synchronize()
-    tt = []
-    for i in range(reps):
-        flush.fill_(i & 0xFF)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        best, _ = m.rank_topn(desc, offs, top_n, "bf16", eps, eps32)
-        b.record(stream)
-        tt.append((a, b))
-    torch.cuda.synchronize()
-    ms = float(np.mean([a.elapsed_time(b) for a, b in tt]))
+
+    def timed(e16):
+        for _ in range(3):
+            best, _ = m.rank_topn(desc, offs, top_n, "bf16", eps, eps32, eps16=e16)
+        torch.cuda.synchronize()
+        tt = []
+        for i in range(reps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            best, _ = m.rank_topn(desc, offs, top_n, "bf16", eps, eps32, eps16=e16)
+            b.record(stream)
+            tt.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in tt])), best
+
+    ms, best = timed(None)
     c32, c64 = m.rescore_counts()
-    return {"top_n": top_n, "ms_per_step": ms, "variants_per_s": n / (ms / 1000.0), "near_tie_fp32_rows": c32,
-            "near_tie_fp64_rows": c64, "first_column_equals_rank": bool(torch.equal(best[:, 0], b1)),
-            "calls": "advisor_rank_topn, one direct call per step"}
+    out = {"top_n": top_n, "ms_per_step": ms, "variants_per_s": n / (ms / 1000.0), "near_tie_fp32_rows": c32,
+           "near_tie_fp64_rows": c64, "first_column_equals_rank": bool(torch.equal(best[:, 0], b1)),
+           "calls": "advisor_rank_topn, one direct call per step"}
+    if eps16 is not None:
+        try:
+            ms16, best16 = timed(eps16)
+            c16, c32t, c64t = m.rescore_counts_ex()
+            out["fp16tier"] = {"eps16": eps16, "ms_per_step": ms16, "variants_per_s": n / (ms16 / 1000.0),
+                               "near_tie_fp16_rows": c16, "near_tie_fp32_rows": c32t, "near_tie_fp64_rows": c64t,
+                               "same_entries_as_without": bool(torch.equal(best16, best))}
+        except Exception as e:   # reported in the line; the plain measurement stands
+            out["fp16tier"] = {"error": repr(e)}
+    return out
 
 
 def err_stats(y, y64):
@@ -838,7 +854,7 @@ def main():
                          **err_stats(y, y64), "eps": e_p}
         out["precisions"] = extras
         try:
-            out["topn"] = topn_leg(m, desc, offs, eps, eps32, n, flush, stream)
+            out["topn"] = topn_leg(m, desc, offs, eps, eps32, n, flush, stream, eps16=m_eps.get("fp16"))
         except Exception as e:   # reported in the line; the other legs still run
             out["topn"] = {"error": repr(e)}
         out["serving"] = serving_leg(dev)
