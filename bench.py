@@ -857,23 +857,31 @@ def main():
             extras[p] = {"variants_per_s": n / (msp / 1000.0), "ms_per_step": msp,
                          **err_stats(y, y64), "eps": e_p}
         out["precisions"] = extras
-        try:
-            out["topn"] = topn_leg(m, desc, offs, eps, eps32, n, flush, stream, eps16=m_eps.get("fp16"))
-        except Exception as e:   # reported in the line; the other legs still run
-            out["topn"] = {"error": repr(e)}
-        out["serving"] = serving_leg(dev)
-        srv10 = [r for r in out["serving"]["runs"] if r["rate_per_s"] == 10000]
+        def leg(name, fn):
+            # a leg that fails is reported in its own entry; the line and the other legs stand
+            try:
+                out[name] = fn()
+            except Exception as e:
+                out[name] = {"error": repr(e)}
+
+        leg("topn", lambda: topn_leg(m, desc, offs, eps, eps32, n, flush, stream, eps16=m_eps.get("fp16")))
+        leg("serving", lambda: serving_leg(dev))
+        runs = out["serving"].get("runs", [])
+        srv10 = [r for r in runs if r["rate_per_s"] == 10000]
         out["p99_query_ms"] = srv10[0]["p99_ms"] if srv10 else None
-        out["plain_512"] = plain_latency_leg(dev)
-        out["dslash"] = dslash_leg(dev)
-        out["training"] = training_leg(dev)
-        out["large_sweep"] = large_sweep_leg(dev)
-        out["kernel_rooflines"] = kernel_rooflines_leg(dev, m, f, st, flush)
-        # the CPU oracle on the host cores (bounded sample)
-        import oracle
-        fc, sc = oracle.extract_features(W.calibration_descriptors(65536), WL.n_features)
-        mu_o, sg_o = oracle.fit_standardizer(fc, sc)
-        out["cpu_baseline"] = cpu_baseline(desc_np, off, params, mu_o, sg_o)
+        leg("plain_512", lambda: plain_latency_leg(dev))
+        leg("dslash", lambda: dslash_leg(dev))
+        leg("training", lambda: training_leg(dev))
+        leg("large_sweep", lambda: large_sweep_leg(dev))
+        leg("kernel_rooflines", lambda: kernel_rooflines_leg(dev, m, f, st, flush))
+
+        def cpu_leg():
+            # the CPU oracle on the host cores (bounded sample)
+            import oracle
+            fc, sc = oracle.extract_features(W.calibration_descriptors(65536), WL.n_features)
+            mu_o, sg_o = oracle.fit_standardizer(fc, sc)
+            return cpu_baseline(desc_np, off, params, mu_o, sg_o)
+        leg("cpu_baseline", cpu_leg)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
