@@ -131,3 +131,22 @@ def test_large_sweep_golden_matches_oracle_on_a_sample():
     sub_off = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
     ref = oracle.rank(np.concatenate(rows), sub_off, wl.widths, wl.weights(), mu, sigma)[0]
     assert np.array_equal(golden[ks].astype(np.int32), ref)
+
+
+def test_topn_on_the_papers_summit_variants():
+    """The oracle's top N on the 84 Summit Dslash variants the paper plots
+    with their measured and predicted runtimes (Fig. plot_variants_summit,
+    tests/golden/summit_dslash_84.txt): the 10 variants with the smallest
+    predicted runtime share 6 with the 10 fastest measured ones (the data
+    behind the paper's top-ten remark), in the order of the printed values,
+    and the first entry is the argmin."""
+    a = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "summit_dslash_84.txt"))
+    actual, pred = a[:, 1], a[:, 2]
+    off = np.array([0, 84], dtype=np.int64)
+    tp, sp = oracle.select_topn(pred, off, 10)
+    ta, _ = oracle.select_topn(actual, off, 10)
+    assert len(set(tp[0].tolist()) & set(ta[0].tolist())) == 6
+    assert tp[0].tolist() == np.argsort(pred, kind="stable")[:10].tolist()
+    assert sp[0].tolist() == np.sort(pred)[:10].tolist()
+    b, s = oracle.select_best(pred, off)
+    assert b[0] == tp[0][0] and s[0] == sp[0][0]
