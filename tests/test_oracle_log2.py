@@ -75,3 +75,20 @@ def test_log_of_min_is_min_of_logs():
     # neighbours, where a truncation could in principle reorder the values
     x = rng.integers(2**20, 2**62, 20000, dtype=np.uint64)
     assert (oracle.log2_q16(x + np.uint64(1)) >= oracle.log2_q16(x)).all()
+
+
+def test_squaring_that_lands_on_two_gives_the_exact_floor():
+    """0xB504F334 = 3,037,000,500 is the one 32-bit mantissa whose square,
+    truncated to Q1.31, is exactly 2.0 (its square lies in
+    [2^63, 2^63 + 2^31)); 2 counts as >= 2, so the first digit is 1 and the
+    rest are 0.  Since log2 of it lies just above 31.5, the digit-by-digit
+    result is then the exact floor of 65536 log2 x: 2^L <= x^65536 < 2^(L+1).
+    The same holds for the mantissa at every binary shift."""
+    m = 0xB504F334
+    assert (1 << 63) <= m * m < (1 << 63) + (1 << 31)
+    xs = [m << s for s in range(33)]
+    L = oracle.log2_q16(np.array(xs, dtype=np.uint64)).tolist()
+    assert L == [(31 + s) * 65536 + 32768 for s in range(33)]
+    for x, l in ((xs[0], L[0]), (xs[32], L[32])):
+        p = x ** 65536
+        assert (1 << l) <= p < (1 << (l + 1))

@@ -185,8 +185,28 @@ def test_duplicate_min_row_lower_index_wins():
     assert best[0] == 0
 
 
+def _fd_mismatches(loss_of, p, g, h=2.0 ** -20, tol_abs=1e-8, tol_rel=1e-6):
+    """Indices where the central difference of loss_of over every parameter
+    disagrees with the analytic gradient g.  Parameters sit on a 2^-12 grid
+    and h = 2^-20, so p +- h is exact in FP32; between ReLU kinks the output
+    is affine in each parameter, so the difference is exact up to rounding
+    (and O(h^2) for the RMSE), and only a kink crossed inside +-h can
+    disagree."""
+    bad = []
+    for i in range(len(p)):
+        pp, pm = p.copy(), p.copy()
+        pp[i] += np.float32(h)
+        pm[i] -= np.float32(h)
+        assert float(pp[i]) - float(p[i]) == h and float(p[i]) - float(pm[i]) == h
+        fd = (loss_of(pp) - loss_of(pm)) / (2 * h)
+        if abs(fd - g[i]) > tol_abs + tol_rel * abs(g[i]):
+            bad.append(i)
+    return bad
+
+
 def test_gradient_against_finite_differences():
-    # Parameters on a 2^-12 grid and steps of 2^-12 keep w +- h exact in FP32.
+    """Every entry of the MSE gradient (weights and biases of every layer)
+    against central differences of the loss."""
     widths = (32, 12, 8, 1)
     rng = np.random.Generator(np.random.PCG64(5))
     p = (np.round(rng.normal(0, 0.4, size=W.param_count(widths)) * 4096) / 4096).astype(np.float32)
@@ -196,18 +216,8 @@ def test_gradient_against_finite_differences():
     loss, g = oracle.loss_grad(f, t, widths, p, mu, sigma)
     y = oracle.mlp_forward(f, widths, p, mu, sigma)
     assert abs(loss - 0.5 * np.mean((y - t.astype(np.float64)) ** 2)) < 1e-12
-    h = 2.0 ** -12
-    errs = []
-    for i in rng.choice(len(p), size=60, replace=False):
-        pp, pm = p.copy(), p.copy()
-        pp[i] += h
-        pm[i] -= h
-        lp = oracle.loss_grad(f, t, widths, pp, mu, sigma)[0]
-        lm = oracle.loss_grad(f, t, widths, pm, mu, sigma)[0]
-        fd = (lp - lm) / (2 * h)
-        errs.append(abs(fd - g[i]) / max(1e-6, abs(g[i]), abs(fd)))
-    errs = np.array(errs)
-    assert np.median(errs) < 1e-6 and np.quantile(errs, 0.9) < 1e-4
+    bad = _fd_mismatches(lambda q: oracle.loss_grad(f, t, widths, q, mu, sigma)[0], p, g)
+    assert len(bad) <= 2, bad   # at most a ReLU kink or two inside +-h
 
 
 def test_adam_first_step_closed_form():
@@ -232,16 +242,8 @@ def test_rmse_gradient_against_finite_differences():
     loss, g = oracle.rmse_grad(f, t, widths, p, mu, sigma)
     y = oracle.mlp_forward(f, widths, p, mu, sigma)
     assert abs(loss - np.sqrt(np.mean((y - t.astype(np.float64)) ** 2))) < 1e-12
-    h = 2.0 ** -12
-    errs = []
-    for i in rng.choice(len(p), size=50, replace=False):
-        pp, pm = p.copy(), p.copy()
-        pp[i] += h
-        pm[i] -= h
-        fd = (oracle.rmse_grad(f, t, widths, pp, mu, sigma)[0] - oracle.rmse_grad(f, t, widths, pm, mu, sigma)[0]) / (2 * h)
-        errs.append(abs(fd - g[i]) / max(1e-6, abs(g[i]), abs(fd)))
-    errs = np.array(errs)
-    assert np.median(errs) < 1e-6 and np.quantile(errs, 0.9) < 1e-4
+    bad = _fd_mismatches(lambda q: oracle.rmse_grad(f, t, widths, q, mu, sigma)[0], p, g)
+    assert len(bad) <= 2, bad
 
 
 def test_rmsprop_first_steps_closed_form():
