@@ -36,7 +36,9 @@ def build(force: bool = False) -> str:
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        # ADVISOR_ORACLE_LIB: another build of advisor_oracle.c (the mutation
+        # test runs the pins against copies with planted mistakes)
+        _lib = ctypes.CDLL(os.environ.get("ADVISOR_ORACLE_LIB") or build())
         P = ctypes.c_void_p
         i64, i32, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         _lib.orc_log2_q16.restype = i32
