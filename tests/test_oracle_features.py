@@ -133,6 +133,21 @@ def test_validation_bits(field, value, bit):
     assert not feat.any()
 
 
+@pytest.mark.parametrize("field,lo,hi,bit", [
+    (1, 1, 1 << 24, 2), (2, 1, 1 << 24, 2), (3, 1, 1 << 24, 2),   # trip counts of the three loops
+    (5, 1, 1 << 32, 4), (6, 1, 1 << 32, 4),                       # flops, bytes per iteration
+    (7, 0, 1 << 48, 8), (8, 0, 1 << 48, 8),                       # mapped bytes each way
+    (9, 1, 1 << 24, 16), (10, 1, 1 << 24, 16),                    # teams, threads
+])
+def test_validation_ranges_both_sides(field, lo, hi, bit):
+    """Both ends of every range: the bound itself is valid, one past it is not."""
+    for value, bad in ((lo - 1, True), (lo, False), (hi, False), (hi + 1, True)):
+        d = D3.copy()
+        d[field] = value
+        st = int(oracle.validate(d)[0])
+        assert bool(st & bit) == bad, (field, value, st)
+
+
 def test_overflow_range_bit():
     d = desc(4, [1 << 24, 1 << 24, 1 << 2, 1], 1, 1, 0, 0, 1, 1, 0, 0, 1, 0, 0)  # T = 2^50
     assert oracle.validate(d)[0] == 64
