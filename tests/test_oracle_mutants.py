@@ -38,6 +38,23 @@ MUTANTS = {
     "features: a one-loop distribute counted as collapsed": (
         "int collapsed = (is_dist[i] && dist_n >= 2) || (is_pf[i] && pc >= 2);",
         "int collapsed = (is_dist[i] && dist_n >= 1) || (is_pf[i] && pc >= 2);"),
+    "features: level bytes use the flops": (
+        "g[6] = orc_log2_q16((uint64_t)(t[i] * bytes));", "g[6] = orc_log2_q16((uint64_t)(t[i] * flops));"),
+    "features: prefix product leaves out its own level": (
+        "for (int j = 0; j <= i; j++) prefix = prefix * t[j];", "for (int j = 0; j < i; j++) prefix = prefix * t[j];"),
+    "features: pair partner off by one": (
+        "int bb = 1 + ((a - 1 + s) % 22);", "int bb = 1 + ((a + s) % 22);"),
+    "features: pair difference reversed": ("f[64 + u] = b[a] - b[bb];", "f[64 + u] = b[bb] - b[a];"),
+    "features: collapse count of the 33-feature input": (
+        "f[32] = (int32_t)(dc + pc) * Q1;", "f[32] = (int32_t)pc * Q1;"),
+    "validation: teams bound": (
+        "if (d[9] < 1 || d[9] > P2(24) || d[10] < 1 || d[10] > P2(24)) st |= ORC_BAD_PARALLELISM;",
+        "if (d[9] < 1 || d[9] > P2(25) || d[10] < 1 || d[10] > P2(24)) st |= ORC_BAD_PARALLELISM;"),
+    "validation: distribute collapse may exceed the parallel-for loop": (
+        "else             { if (dc < 1 || dc > pf_pos) vok = 0; }",
+        "else             { if (dc < 1 || dc > pf_pos + 1) vok = 0; }"),
+    "variant count: the combined case counted like the others": (
+        "combos += (x == 0 ? 1 : x) * (depth - x);", "combos += (x + 1) * (depth - x);"),
     "validation: trip count bound": (
         "if (i < depth) { if (t < 1 || t > P2(24)) st |= ORC_BAD_TRIP; }",
         "if (i < depth) { if (t < 1 || t > P2(25)) st |= ORC_BAD_TRIP; }"),
@@ -76,6 +93,10 @@ MUTANTS = {
         "for (int64_t dm = 0; dm < 2; dm++)\n                            for (int64_t sched = 0; sched < 3; sched++) {"),
     "loss: factor 1/2 dropped": ("loss = loss + 0.5 * e * e;", "loss = loss + e * e;"),
     "gradient: bias gradient overwritten per row": ("gb[j] = gb[j] + dz;", "gb[j] = dz;"),
+    "top N: a missing entry padded with the last score": (
+        "score[k * N + t] = bi < 0 ? INFINITY : bv;\n            if (bi >= 0) { pv = bv; pi = bi; }",
+        "score[k * N + t] = bi < 0 ? pv : bv;\n            if (bi >= 0) { pv = bv; pi = bi; }"),
+    "argmin: empty segment scored 0": ("best_score[k] = bs;", "best_score[k] = bi < 0 ? 0.0 : bs;"),
     "gradient: 1/n dropped": ("dcur[0] = e / (double)n;", "dcur[0] = e;"),
     "gradient: ReLU derivative dropped": (
         "dprev[k] = (pre[aoff[l - 1] + k] > 0.0) ? s : 0.0;", "dprev[k] = s;"),
@@ -104,7 +125,7 @@ def _compile(src_text, out_dir):
 
 
 def _run_pins(so):
-    env = dict(os.environ, ADVISOR_ORACLE_LIB=so, OMP_NUM_THREADS="2")
+    env = dict(os.environ, ADVISOR_ORACLE_LIB=so, OMP_NUM_THREADS="1")
     return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
 
@@ -116,7 +137,7 @@ def test_pins_catch_every_planted_mistake(tmp_path):
     jobs = {"unmodified": _compile(src, str(tmp_path / "control"))}
     for i, (name, (orig, bad)) in enumerate(MUTANTS.items()):
         jobs[name] = _compile(src.replace(orig, bad), str(tmp_path / f"m{i}"))
-    with cf.ThreadPoolExecutor(max_workers=4) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
         res = dict(zip(jobs, ex.map(_run_pins, jobs.values())))
     control = res.pop("unmodified")
     assert control.returncode == 0, control.stdout[-3000:]
