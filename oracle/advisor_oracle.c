@@ -25,7 +25,8 @@
  *
  * Parity pins: every function here is checked in tests/test_oracle_*.py
  * against hand-worked descriptors, closed forms, invariants, brute force or
- * finite differences (see the test files).
+ * finite differences (see the test files), and tests/test_oracle_mutants.py
+ * checks that mistakes planted in copies of this file fail those pins.
  */
 #include <math.h>
 #include <stdint.h>
