@@ -51,3 +51,16 @@ def test_library_does_not_link_the_oracle():
         return
     needed = re.findall(r"\(NEEDED\).*\[(.+)\]", r.stdout)
     assert needed and not any("oracle" in n for n in needed), needed
+
+
+def test_product_path_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """With no built library there is no fallback: loading it, and any call
+    that reaches it, raises."""
+    import pytest
+    from paper_2301_03636_gb300 import advisor
+    monkeypatch.setattr(advisor, "_lib", None)
+    monkeypatch.setattr(advisor, "library_path", lambda: str(tmp_path / "libadvisor.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        advisor.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        advisor.launch_count()
