@@ -57,3 +57,30 @@ def test_unbound_model_is_rejected(L):
     assert L.advisor_model_create(ctypes.cast(arr, ctypes.c_void_p), 4, ctypes.byref(h)) == 0
     assert L.advisor_score_variants(h, ctypes.c_void_p(256), None, 10, 0, ctypes.c_void_p(256), None) == 1
     assert L.advisor_model_destroy(h) == 0
+
+
+def test_newer_entry_points_reject_bad_arguments(L):
+    """Argument checks of the staged, top-N, plan and self-test calls return
+    ADVISOR_ERR_INVALID_ARGUMENT on the host, before anything is enqueued."""
+    P, i64, i32, f32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float
+    L = ctypes.CDLL(advisor.library_path())   # own function objects: the binding's argtypes stay as they are
+    L.advisor_model_create.argtypes = [P, i32, P]
+    L.advisor_model_destroy.argtypes = [P]
+    L.advisor_rank_staged.argtypes = [P, P, P, i64, P, i64, i32, f32, f32, P, P, P, P, i32, P]
+    L.advisor_rank_topn.argtypes = [P, P, i64, P, i64, i32, i32, f32, f32, P, P, P, P, P]
+    L.advisor_model_check_wait_timeout.argtypes = [P, i64, P]
+    L.advisor_plan_launch.argtypes = [P, P]
+    L.advisor_get_rescore_counts.argtypes = [P, P, P]
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int32 * 4)(32, 128, 128, 1)
+    assert L.advisor_model_create(ctypes.cast(arr, ctypes.c_void_p), 4, ctypes.byref(h)) == 0
+    dev = ctypes.c_void_p(256)   # never dereferenced: every call below is refused first
+    for stages in (0, 17):       # 1 .. ADVISOR_MAX_STAGES
+        assert L.advisor_rank_staged(h, dev, dev, 10, dev, 1, 1, -1.0, 0.0, dev, dev, None, None, stages, None) == 1
+    for n in (0, 129):           # 1 .. ADVISOR_MAX_TOP_N
+        assert L.advisor_rank_topn(h, dev, 10, dev, 1, n, 1, -1.0, 0.0, dev, dev, None, None, None) == 1
+    assert L.advisor_model_check_wait_timeout(None, 1000000, None) == 1
+    assert L.advisor_model_check_wait_timeout(h, 1000000, None) == 1   # unbound model
+    assert L.advisor_plan_launch(None, None) == 1
+    assert L.advisor_get_rescore_counts(h, None, None) == 1
+    assert L.advisor_model_destroy(h) == 0
