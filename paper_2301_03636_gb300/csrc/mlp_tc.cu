@@ -34,17 +34,6 @@ namespace adv {
 constexpr int TC_STAGES = 2;
 constexpr int TC_THREADS = 32 * (2 + 16 + (TC_STAGES - 1));   // producer 0, MMA, 16 epilogue, producers 1..
 
-// Diagnostic timeline of CTA 0 (clock64 stamps), compiled in only with
-// -DADV_TC_TRACE; the library build never defines it.
-#ifdef ADV_TC_TRACE
-__device__ unsigned long long g_tc_trace[32768];
-#define TC_TRACE(idx) \
-    do { if (blockIdx.x == 0) g_tc_trace[(idx)] = clock64(); } while (0)
-#else
-#define TC_TRACE(idx) \
-    do { } while (0)
-#endif
-
 // ReLU + round-to-nearest + pack two FP32 values into 16-bit pairs (lo in
 // the low half); FP16 saturates to the largest finite value.
 template <int FMT>
@@ -145,12 +134,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                     for (int s = 0; s < ns && ok; ++s) {
                         for (int k = 0; k < a.nslab[l]; ++k, ++idx) {
                             if (idx % TC_STAGES != q) continue;
-                            TC_TRACE(8192 + 2 * (idx & 4095));
                             if (!mbar_wait_bounded(&w_empty[q], phase ^ 1u, a.status_word, abort_flag, lim)) {
                                 ok = false;
                                 break;
                             }
-                            TC_TRACE(8192 + 2 * (idx & 4095) + 1);
                             mbar_expect_tx(&w_full[q], sb);
                             bulk_g2s(wst + q * stage_bytes, a.w_img[l] + (size_t)k * sb, sb, &w_full[q]);
                             ++mine;
@@ -174,7 +161,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                 for (int l = 0; l < a.n_hidden && ok; ++l) {
                     const uint32_t idesc = f16_idesc((uint32_t)FMT, 128u, (uint32_t)a.npad[l]);
                     for (int s = 0; s < ns && ok; ++s) {
-                        TC_TRACE(((p * 8 + l) * 2 + s) * 4 + 0);
                         if (l == 0) {
                             ok = mbar_wait_bounded(&x_full[s], xph[s], a.status_word, abort_flag, lim);
                             xph[s] ^= 1u;
@@ -184,7 +170,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                             aph[s] ^= 1u;
                         }
                         if (!ok) break;
-                        TC_TRACE(((p * 8 + l) * 2 + s) * 4 + 1);
                         tc_fence_after();
                         const uint32_t d_tmem = tmem + (uint32_t)(s * a.nmax);
                         for (int k = 0; k < a.nslab[l]; ++k) {
@@ -204,7 +189,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                         }
                         if (!ok) break;
                         umma_commit(&acc_full[s]);
-                        TC_TRACE(((p * 8 + l) * 2 + s) * 4 + 2);
                     }
                 }
             }
@@ -220,7 +204,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
         const int quad = warp & 3;                  // TMEM lane quadrant
         const uint32_t r = (uint32_t)(quad * 32 + lane);
         const bool leader = e == 0 && lane == 0;
-        const bool tr = (e & 3) == 0 && lane == 0;
         const int nslab0 = a.nslab[0];
         const uint32_t x_bytes = (uint32_t)nslab0 * ADV_X_SLAB_BYTES;
         uint32_t accph[2] = {0, 0}, redph[2] = {0, 0}, xph[2] = {0, 0};
@@ -245,13 +228,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                 const int cb = j * cw;
                 for (int s = 0; s < ns; ++s) {
                     const int i = 2 * p + s;                // tile index within this CTA
-                    if (tr) TC_TRACE(4096 + ((i * 8 + l) * 2 + (j & 1)) * 4 + 0);
                     const bool got = mbar_wait_bounded(&acc_full[s], accph[s], a.status_word, abort_flag, lim);
                     __syncwarp();   // tcgen05.ld / st / wait are warp-collective (.sync.aligned)
                     if (!got) { ok = false; break; }
                     accph[s] ^= 1u;
                     if (l == 0) { x_pending[s] = 0; xph[s] ^= 1u; }   // the MMAs consumed the X tile
-                    if (tr) TC_TRACE(4096 + ((i * 8 + l) * 2 + (j & 1)) * 4 + 1);
                     tc_fence_after();
                     // the X buffer of this slot is free: every MMA that read it has completed
                     if (last && leader && i + 2 < n_my) { load_x(s, b + (i + 2) * G); x_pending[s] = 1; }
@@ -354,7 +335,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                         }
                         redph[s] ^= 1u;
                     }
-                    if (tr) TC_TRACE(4096 + ((i * 8 + l) * 2 + (j & 1)) * 4 + 2);
                     tc_fence_before();
                     mbar_arrive(&act_ready[s]);
                 }
@@ -397,15 +377,5 @@ cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s, int ctas
     adv_count_launch(1);
     return cudaGetLastError();
 }
-
-#ifdef ADV_TC_TRACE
-extern "C" int advisor_debug_read_tc_trace(unsigned long long* host, int n) {
-    return cudaMemcpyFromSymbol(host, g_tc_trace, (size_t)n * sizeof(unsigned long long)) == cudaSuccess ? 0 : 1;
-}
-extern "C" int advisor_debug_clear_tc_trace(void) {
-    static unsigned long long zeros[32768];
-    return cudaMemcpyToSymbol(g_tc_trace, zeros, sizeof(zeros)) == cudaSuccess ? 0 : 1;
-}
-#endif
 
 }  // namespace adv
