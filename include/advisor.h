@@ -266,6 +266,15 @@ advisor_status advisor_rank_staged(advisor_model_t m, const advisor_variant_desc
                                    float eps_fp32, int32_t* d_best_local, double* d_best_score, float* d_scores,
                                    uint8_t* d_row_status, int32_t n_stages, cudaStream_t stream);
 
+/* advisor_rank_staged with the FP16 tensor-core tier of advisor_rank_ex
+ * (eps_fp16 >= 0; same argument rules as advisor_rank_ex). */
+advisor_status advisor_rank_staged_ex(advisor_model_t m, const advisor_variant_desc* h_desc,
+                                      advisor_variant_desc* d_desc, int64_t n_rows, const int64_t* d_seg_off,
+                                      int64_t n_kernels, advisor_precision precision, float eps_scores,
+                                      float eps_fp16, float eps_fp32, int32_t* d_best_local, double* d_best_score,
+                                      float* d_scores, uint8_t* d_row_status, int32_t n_stages,
+                                      cudaStream_t stream);
+
 /* advisor_rank with an FP16 tensor-core tier between the first scores and
  * the FP32 re-score (a7 of Fig. 2's selection, made cheaper for wide models
  * and coarse first tiers).  eps_fp16 >= 0 enables it: the tier-1 candidates
@@ -341,7 +350,6 @@ advisor_status advisor_plan_rank(advisor_model_t m, const advisor_variant_desc* 
                                  double* d_best_score, float* d_scores, uint8_t* d_row_status,
                                  int32_t autotune, cudaStream_t stream, advisor_plan_t* out);
 
-/* Replay the plan on `stream` (asynchronous: one graph launch). */
 /* advisor_plan_rank for advisor_rank_staged: the plan replays the staged
  * copy of h_desc into d_desc together with the ranking (refill h_desc in
  * place between replays). */
@@ -351,6 +359,25 @@ advisor_status advisor_plan_rank_staged(advisor_model_t m, const advisor_variant
                                         float eps_fp32, int32_t* d_best_local, double* d_best_score,
                                         float* d_scores, uint8_t* d_row_status, int32_t n_stages,
                                         int32_t autotune, cudaStream_t stream, advisor_plan_t* out);
+
+/* advisor_plan_rank / advisor_plan_rank_staged with the FP16 tensor-core
+ * tier of advisor_rank_ex captured into the plan (eps_fp16 >= 0; same
+ * argument rules as advisor_rank_ex).  Replays give the same selections as
+ * advisor_rank_ex with these arguments. */
+advisor_status advisor_plan_rank_ex(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                                    const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
+                                    float eps_scores, float eps_fp16, float eps_fp32, int32_t* d_best_local,
+                                    double* d_best_score, float* d_scores, uint8_t* d_row_status, int32_t autotune,
+                                    cudaStream_t stream, advisor_plan_t* out);
+advisor_status advisor_plan_rank_staged_ex(advisor_model_t m, const advisor_variant_desc* h_desc,
+                                           advisor_variant_desc* d_desc, int64_t n_rows, const int64_t* d_seg_off,
+                                           int64_t n_kernels, advisor_precision precision, float eps_scores,
+                                           float eps_fp16, float eps_fp32, int32_t* d_best_local,
+                                           double* d_best_score, float* d_scores, uint8_t* d_row_status,
+                                           int32_t n_stages, int32_t autotune, cudaStream_t stream,
+                                           advisor_plan_t* out);
+
+/* Replay the plan on `stream` (asynchronous: one graph launch). */
 advisor_status advisor_plan_launch(advisor_plan_t p, cudaStream_t stream);
 
 /* The configuration the plan was captured with; *replay_us (nullable) the
@@ -479,22 +506,26 @@ advisor_status advisor_get_rescore_counts(advisor_model_t m, int64_t* h_counts, 
  * without that tier), [1] = rows re-scored in FP32, [2] = in FP64. */
 advisor_status advisor_get_rescore_counts_ex(advisor_model_t m, int64_t* h_counts, cudaStream_t stream);
 
-/* Tensor-core scoring that allocates nothing: the same computation and
- * result as advisor_score_variants with ADVISOR_BF16 or ADVISOR_FP16, for
- * callers that cannot provide device memory for a workspace (code where
- * cudaMalloc is not allowed, e.g. host callbacks or hosts that forbid device
- * allocations after start-up).  The paper has no counterpart: this is an
- * interface convenience.  The 16-bit activation image lives in a fixed
- * device array inside the library: 16,384 rows of up to 128 features
- * (4 MiB on every GPU that loads the library, held until exit); n_rows
- * beyond 16,384 returns ADVISOR_ERR_OUT_OF_MEMORY before anything is
- * enqueued.  The model must be bound and loaded (set_params); its workspace
- * is not used.  The first call on a device looks up the array's device
- * address (once per device, with that device current), so make that first
- * call before any stream capture.  All calls on a device share the array;
- * each call rewrites every part it reads, but calls whose kernels overlap on
- * the GPU (e.g. on two streams) race and must be ordered by the caller.
- * ADVISOR_FP32 / ADVISOR_FP64 return ADVISOR_ERR_UNSUPPORTED. */
+/* Tensor-core scoring that allocates nothing: the computation and result
+ * of advisor_score_variants with ADVISOR_BF16 or ADVISOR_FP16 on the fused
+ * scorer (this call always runs the fused tensor-core kernel, with the
+ * model's tc_ctas, whatever layer_path the model's launch configuration
+ * sets), for callers that cannot provide device memory for a workspace
+ * (code where cudaMalloc is not allowed, e.g. host callbacks or hosts that
+ * forbid device allocations after start-up).  The paper has no
+ * counterpart: this is an interface convenience.  The 16-bit activation
+ * image lives in a fixed device array inside the library: 16,384 rows of up
+ * to 128 features (4 MiB on every GPU that loads the library, held until
+ * exit); n_rows beyond 16,384 returns ADVISOR_ERR_OUT_OF_MEMORY before
+ * anything is enqueued.  The model must be bound and loaded (set_params);
+ * its workspace is not used.  The first call on a device looks up the
+ * array's device address (once per device, with that device current, kept
+ * for the life of the process: the library must not outlive a reset of the
+ * device), so make that first call before any stream capture.  All calls on
+ * a device share the array; each call rewrites every part it reads, but
+ * calls whose kernels overlap on the GPU (e.g. on two streams) race and
+ * must be ordered by the caller.  ADVISOR_FP32 / ADVISOR_FP64 return
+ * ADVISOR_ERR_UNSUPPORTED. */
 advisor_status advisor_score_variants_noalloc(advisor_model_t m, const int32_t* d_feat_q16,
                                               const uint8_t* d_row_status, int64_t n_rows,
                                               advisor_precision precision, float* d_scores,

@@ -90,6 +90,10 @@ def lib():
         "advisor_rank_staged": (st, [P, P, P, i64, P, i64, st, f32, f32, P, P, P, P, i32, P]),
         "advisor_plan_rank_staged": (st, [P, P, P, i64, P, i64, st, f32, f32, P, P, P, P, i32, i32, P,
                                           ctypes.POINTER(P)]),
+        "advisor_rank_staged_ex": (st, [P, P, P, i64, P, i64, st, f32, f32, f32, P, P, P, P, i32, P]),
+        "advisor_plan_rank_ex": (st, [P, P, i64, P, i64, st, f32, f32, f32, P, P, P, P, i32, P, ctypes.POINTER(P)]),
+        "advisor_plan_rank_staged_ex": (st, [P, P, P, i64, P, i64, st, f32, f32, f32, P, P, P, P, i32, i32, P,
+                                             ctypes.POINTER(P)]),
         "advisor_plan_launch": (st, [P, P]),
         "advisor_plan_info": (st, [P, P, P, P]),
         "advisor_plan_destroy": (st, [P]),
@@ -193,6 +197,20 @@ def advisor_enumerate_variants(kernels: torch.Tensor, stream=None):
                                             _stream(stream)), "advisor_enumerate_variants")
     n = int(total.item())
     return out[:n], off
+
+
+def workspace_bytes(widths, max_rows: int, max_kernels: int) -> int:
+    """Device bytes of the workspace a model of these widths needs for batches of
+    up to max_rows variants and max_kernels kernels (advisor_workspace_bytes;
+    nothing is allocated)."""
+    w = (ctypes.c_int32 * len(widths))(*[int(x) for x in widths])
+    h = ctypes.c_void_p()
+    _check(lib().advisor_model_create(ctypes.cast(w, ctypes.c_void_p), len(widths), ctypes.byref(h)),
+           "advisor_model_create")
+    try:
+        return int(lib().advisor_workspace_bytes(h, int(max_rows), int(max_kernels)))
+    finally:
+        lib().advisor_model_destroy(h)
 
 
 def advisor_fit_standardizer(feat: torch.Tensor, status: torch.Tensor | None = None, stream=None):
@@ -334,28 +352,36 @@ class Model:
     def launch_config(self, c: LaunchConfig):
         _check(lib().advisor_model_set_launch_config(self.handle, ctypes.byref(c)), "set_launch_config")
 
-    def plan_rank(self, desc, offsets, precision="bf16", eps=-1.0, eps32=0.0, autotune=False, stream=None):
-        """A Plan replaying rank() on these buffers (refill desc / offsets in place between launches)."""
-        return Plan(self, desc, offsets, precision, eps, eps32, autotune, stream)
+    def plan_rank(self, desc, offsets, precision="bf16", eps=-1.0, eps32=0.0, autotune=False, stream=None,
+                  eps16=None):
+        """A Plan replaying rank() on these buffers (refill desc / offsets in place between launches);
+        with eps16, the FP16 middle tier is captured too (advisor_plan_rank_ex)."""
+        return Plan(self, desc, offsets, precision, eps, eps32, autotune, stream, eps16=eps16)
 
     def rank_staged(self, h_desc, d_desc, offsets, precision="bf16", eps=-1.0, eps32=0.0, n_stages=4,
-                    scores=None, status=None, stream=None):
+                    scores=None, status=None, stream=None, eps16=None):
         """rank() on descriptors in pinned host memory (h_desc), copied into the device buffer
-        d_desc in n_stages chunks that overlap the scoring (advisor_rank_staged)."""
+        d_desc in n_stages chunks that overlap the scoring (advisor_rank_staged[_ex])."""
         K = offsets.shape[0] - 1
         best = torch.empty(K, dtype=torch.int32, device=self.device)
         best_score = torch.empty(K, dtype=torch.float64, device=self.device)
-        _check(lib().advisor_rank_staged(self.handle, _ptr(h_desc), _ptr(d_desc), h_desc.shape[0], _ptr(offsets), K,
-                                         _prec(precision), float(eps), float(eps32), _ptr(best), _ptr(best_score),
-                                         _ptr(scores), _ptr(status), int(n_stages), _stream(stream)),
-               "advisor_rank_staged")
+        if eps16 is None:
+            _check(lib().advisor_rank_staged(self.handle, _ptr(h_desc), _ptr(d_desc), h_desc.shape[0], _ptr(offsets),
+                                             K, _prec(precision), float(eps), float(eps32), _ptr(best),
+                                             _ptr(best_score), _ptr(scores), _ptr(status), int(n_stages),
+                                             _stream(stream)), "advisor_rank_staged")
+        else:
+            _check(lib().advisor_rank_staged_ex(self.handle, _ptr(h_desc), _ptr(d_desc), h_desc.shape[0],
+                                                _ptr(offsets), K, _prec(precision), float(eps), float(eps16),
+                                                float(eps32), _ptr(best), _ptr(best_score), _ptr(scores),
+                                                _ptr(status), int(n_stages), _stream(stream)), "advisor_rank_staged_ex")
         return best, best_score
 
     def plan_rank_staged(self, h_desc, d_desc, offsets, precision="bf16", eps=-1.0, eps32=0.0, n_stages=4,
-                         autotune=False, stream=None):
+                         autotune=False, stream=None, eps16=None):
         """A Plan replaying rank_staged() (refill h_desc / offsets in place between launches)."""
         return Plan(self, d_desc, offsets, precision, eps, eps32, autotune, stream, h_desc=h_desc,
-                    n_stages=n_stages)
+                    n_stages=n_stages, eps16=eps16)
 
     def rank_topn(self, desc, offsets, top_n, precision="bf16", eps=-1.0, eps32=0.0, scores=None, status=None,
                   stream=None, eps16=None):
@@ -472,7 +498,7 @@ class Plan:
     scores / status in place."""
 
     def __init__(self, model: Model, desc, offsets, precision="bf16", eps=-1.0, eps32=0.0, autotune=False,
-                 stream=None, h_desc=None, n_stages=1):
+                 stream=None, h_desc=None, n_stages=1, eps16=None):
         self.model = model
         self.desc, self.offsets, self.h_desc = desc, offsets, h_desc
         K = offsets.shape[0] - 1
@@ -481,18 +507,20 @@ class Plan:
         self.scores = torch.empty(desc.shape[0], dtype=torch.float32, device=model.device)
         self.status = torch.empty(desc.shape[0], dtype=torch.uint8, device=model.device)
         h = ctypes.c_void_p()
+        e16 = -1.0 if eps16 is None else float(eps16)
         if h_desc is None:
-            _check(lib().advisor_plan_rank(model.handle, _ptr(desc), desc.shape[0], _ptr(offsets), K,
-                                           _prec(precision), float(eps), float(eps32), _ptr(self.best),
-                                           _ptr(self.best_score), _ptr(self.scores), _ptr(self.status),
-                                           1 if autotune else 0, _stream(stream), ctypes.byref(h)),
-                   "advisor_plan_rank")
+            _check(lib().advisor_plan_rank_ex(model.handle, _ptr(desc), desc.shape[0], _ptr(offsets), K,
+                                              _prec(precision), float(eps), e16, float(eps32), _ptr(self.best),
+                                              _ptr(self.best_score), _ptr(self.scores), _ptr(self.status),
+                                              1 if autotune else 0, _stream(stream), ctypes.byref(h)),
+                   "advisor_plan_rank_ex")
         else:
-            _check(lib().advisor_plan_rank_staged(model.handle, _ptr(h_desc), _ptr(desc), desc.shape[0],
-                                                  _ptr(offsets), K, _prec(precision), float(eps), float(eps32),
-                                                  _ptr(self.best), _ptr(self.best_score), _ptr(self.scores),
-                                                  _ptr(self.status), int(n_stages), 1 if autotune else 0,
-                                                  _stream(stream), ctypes.byref(h)), "advisor_plan_rank_staged")
+            _check(lib().advisor_plan_rank_staged_ex(model.handle, _ptr(h_desc), _ptr(desc), desc.shape[0],
+                                                     _ptr(offsets), K, _prec(precision), float(eps), e16,
+                                                     float(eps32), _ptr(self.best), _ptr(self.best_score),
+                                                     _ptr(self.scores), _ptr(self.status), int(n_stages),
+                                                     1 if autotune else 0, _stream(stream), ctypes.byref(h)),
+                   "advisor_plan_rank_staged_ex")
         self.handle = h
 
     def launch(self, stream=None):

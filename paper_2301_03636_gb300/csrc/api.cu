@@ -833,13 +833,14 @@ advisor_status advisor_rank_ex(advisor_model_t m, const advisor_variant_desc* d_
                      d_best_local, d_best_score, stream, eps_fp16 >= 0.f ? eps_fp16 : -1.f, zeroed);
 }
 
-advisor_status advisor_rank_staged(advisor_model_t m, const advisor_variant_desc* h_desc,
-                                   advisor_variant_desc* d_desc, int64_t n_rows, const int64_t* d_seg_off,
-                                   int64_t n_kernels, advisor_precision precision, float eps_scores,
-                                   float eps_fp32, int32_t* d_best_local, double* d_best_score, float* d_scores,
-                                   uint8_t* d_row_status, int32_t n_stages, cudaStream_t stream) {
+advisor_status advisor_rank_staged_ex(advisor_model_t m, const advisor_variant_desc* h_desc,
+                                      advisor_variant_desc* d_desc, int64_t n_rows, const int64_t* d_seg_off,
+                                      int64_t n_kernels, advisor_precision precision, float eps_scores,
+                                      float eps_fp16, float eps_fp32, int32_t* d_best_local, double* d_best_score,
+                                      float* d_scores, uint8_t* d_row_status, int32_t n_stages,
+                                      cudaStream_t stream) {
     if (n_stages < 1 || n_stages > ADVISOR_MAX_STAGES) return ADVISOR_ERR_INVALID_ARGUMENT;
-    advisor_status st = rank_checks(m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, -1.f,
+    advisor_status st = rank_checks(m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, eps_fp16,
                                     eps_fp32, d_best_local, d_best_score);
     if (st != ADVISOR_OK || n_kernels == 0) return st;
     if (ensure_images(m, stream) != cudaSuccess) return ADVISOR_ERR_CUDA;
@@ -885,7 +886,16 @@ advisor_status advisor_rank_staged(advisor_model_t m, const advisor_variant_desc
     if (n_rows == 0) rank_scores(m, d_desc, 0, precision, scores, status, &rs, stream);
     else if (c == 0) return ADVISOR_ERR_CUDA;
     return do_select(m, scores, n_rows, d_seg_off, n_kernels, rs, rescore && n_rows > 0, eps_scores, eps_fp32,
-                     d_best_local, d_best_score, stream, -1.f, zeroed);
+                     d_best_local, d_best_score, stream, eps_fp16 >= 0.f ? eps_fp16 : -1.f, zeroed);
+}
+
+advisor_status advisor_rank_staged(advisor_model_t m, const advisor_variant_desc* h_desc,
+                                   advisor_variant_desc* d_desc, int64_t n_rows, const int64_t* d_seg_off,
+                                   int64_t n_kernels, advisor_precision precision, float eps_scores,
+                                   float eps_fp32, int32_t* d_best_local, double* d_best_score, float* d_scores,
+                                   uint8_t* d_row_status, int32_t n_stages, cudaStream_t stream) {
+    return advisor_rank_staged_ex(m, h_desc, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, -1.f,
+                                  eps_fp32, d_best_local, d_best_score, d_scores, d_row_status, n_stages, stream);
 }
 
 advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
@@ -1111,6 +1121,7 @@ int adv_model_noalloc_view(advisor_model_t m, int fmt_idx, adv::NoallocModelView
     out->nslab0 = m->L.n_hidden > 0 ? m->L.nslab[0] : 0;
     out->tc_ok = tc_supported(m) ? 1 : 0;
     out->num_sms = m->num_sms;
+    out->tc_ctas = m->cfg.tc_ctas;
     if (!out->ready) return 1;
     out->sa = reinterpret_cast<const float*>(m->P + m->L.p_stdz_a);
     out->sc = reinterpret_cast<const float*>(m->P + m->L.p_stdz_c);

@@ -32,7 +32,10 @@ std::mutex g_noalloc_mutex;
 void* g_noalloc_addr[kMaxDevices] = {};
 
 // Device address of the scratch on the current device, looked up once per
-// device (the symbol name is only a host-side handle, not a device address).
+// device (the symbol name is only a host-side handle, not a device address)
+// and kept for the life of the process: the library must not outlive a reset
+// of the device (cudaDeviceReset or a re-created primary context), after
+// which the kept address would no longer be valid.
 cudaError_t noalloc_scratch(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -83,5 +86,5 @@ extern "C" advisor_status advisor_score_variants_noalloc(advisor_model_t m, cons
     a.status = d_row_status;
     a.scores = d_scores;
     a.fmt = precision == ADVISOR_BF16 ? 1 : 0;
-    return launch_mlp_tc(a, v.num_sms, stream) == cudaSuccess ? ADVISOR_OK : ADVISOR_ERR_CUDA;
+    return launch_mlp_tc(a, v.num_sms, stream, v.tc_ctas) == cudaSuccess ? ADVISOR_OK : ADVISOR_ERR_CUDA;
 }

@@ -13,6 +13,7 @@ struct NoallocModelView {
     const float* sc;
     TcArgs tc;   // weights, biases, output row, geometry; x_img/n_rows/scores/status filled per call
     int num_sms;
+    int tc_ctas;   // the model's CTA count for the tensor-core scorer (0: one per SM)
     int tc_ok;
     int ready;
 };

@@ -40,7 +40,7 @@ struct RankCall {
     const int64_t* off;
     int64_t n_kernels;
     advisor_precision precision;
-    float eps, eps32;
+    float eps, eps16, eps32;   // eps16 < 0: no FP16 tier
     int32_t* best;
     double* best_score;
     float* scores;
@@ -68,11 +68,11 @@ advisor_status capture(const RankCall& r, cudaStream_t cap, cudaGraph_t* g_out, 
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return ADVISOR_ERR_CUDA;
     const long long before = advisor_launch_count();
     const advisor_status st =
-        r.h_desc ? advisor_rank_staged(r.m, r.h_desc, const_cast<advisor_variant_desc*>(r.desc), r.n_rows, r.off,
-                                       r.n_kernels, r.precision, r.eps, r.eps32, r.best, r.best_score, r.scores,
-                                       r.status, r.n_stages, cap)
-                 : advisor_rank(r.m, r.desc, r.n_rows, r.off, r.n_kernels, r.precision, r.eps, r.eps32, r.best,
-                                r.best_score, r.scores, r.status, cap);
+        r.h_desc ? advisor_rank_staged_ex(r.m, r.h_desc, const_cast<advisor_variant_desc*>(r.desc), r.n_rows, r.off,
+                                          r.n_kernels, r.precision, r.eps, r.eps16, r.eps32, r.best, r.best_score,
+                                          r.scores, r.status, r.n_stages, cap)
+                 : advisor_rank_ex(r.m, r.desc, r.n_rows, r.off, r.n_kernels, r.precision, r.eps, r.eps16, r.eps32,
+                                   r.best, r.best_score, r.scores, r.status, cap);
     // the launches were only recorded; replays account for them instead
     adv_count_launch(-(int)(advisor_launch_count() - before));
     cudaGraph_t g = nullptr;
@@ -226,13 +226,35 @@ advisor_status make_plan(const RankCall& r, int32_t autotune, cudaStream_t strea
 
 extern "C" {
 
+advisor_status advisor_plan_rank_ex(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
+                                    const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
+                                    float eps_scores, float eps_fp16, float eps_fp32, int32_t* d_best_local,
+                                    double* d_best_score, float* d_scores, uint8_t* d_row_status, int32_t autotune,
+                                    cudaStream_t stream, advisor_plan_t* out) {
+    const RankCall r{m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, eps_fp16, eps_fp32,
+                     d_best_local, d_best_score, d_scores, d_row_status, nullptr, 1};
+    return make_plan(r, autotune, stream, out);
+}
+
 advisor_status advisor_plan_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
                                  const int64_t* d_seg_off, int64_t n_kernels, advisor_precision precision,
                                  float eps_scores, float eps_fp32, int32_t* d_best_local, double* d_best_score,
                                  float* d_scores, uint8_t* d_row_status, int32_t autotune, cudaStream_t stream,
                                  advisor_plan_t* out) {
-    const RankCall r{m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, eps_fp32,
-                     d_best_local, d_best_score, d_scores, d_row_status, nullptr, 1};
+    return advisor_plan_rank_ex(m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, -1.f, eps_fp32,
+                                d_best_local, d_best_score, d_scores, d_row_status, autotune, stream, out);
+}
+
+advisor_status advisor_plan_rank_staged_ex(advisor_model_t m, const advisor_variant_desc* h_desc,
+                                           advisor_variant_desc* d_desc, int64_t n_rows, const int64_t* d_seg_off,
+                                           int64_t n_kernels, advisor_precision precision, float eps_scores,
+                                           float eps_fp16, float eps_fp32, int32_t* d_best_local,
+                                           double* d_best_score, float* d_scores, uint8_t* d_row_status,
+                                           int32_t n_stages, int32_t autotune, cudaStream_t stream,
+                                           advisor_plan_t* out) {
+    if (!h_desc) return ADVISOR_ERR_INVALID_ARGUMENT;
+    const RankCall r{m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, eps_fp16, eps_fp32,
+                     d_best_local, d_best_score, d_scores, d_row_status, h_desc, n_stages};
     return make_plan(r, autotune, stream, out);
 }
 
@@ -242,10 +264,9 @@ advisor_status advisor_plan_rank_staged(advisor_model_t m, const advisor_variant
                                         float eps_fp32, int32_t* d_best_local, double* d_best_score,
                                         float* d_scores, uint8_t* d_row_status, int32_t n_stages,
                                         int32_t autotune, cudaStream_t stream, advisor_plan_t* out) {
-    if (!h_desc) return ADVISOR_ERR_INVALID_ARGUMENT;
-    const RankCall r{m, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores, eps_fp32,
-                     d_best_local, d_best_score, d_scores, d_row_status, h_desc, n_stages};
-    return make_plan(r, autotune, stream, out);
+    return advisor_plan_rank_staged_ex(m, h_desc, d_desc, n_rows, d_seg_off, n_kernels, precision, eps_scores,
+                                       -1.f, eps_fp32, d_best_local, d_best_score, d_scores, d_row_status, n_stages,
+                                       autotune, stream, out);
 }
 
 advisor_status advisor_plan_launch(advisor_plan_t p, cudaStream_t stream) {

@@ -184,3 +184,52 @@ def test_plan_rejects_what_rank_rejects(gpu_lib, setup):
     assert e.value.code == 3   # ADVISOR_ERR_OUT_OF_MEMORY
     with pytest.raises(advisor.AdvisorError):
         m.plan_rank(d, torch.from_numpy(setup["off"]).cuda(), "bf16", 0.1, -1.0)   # eps32 < 0 with re-score on
+
+
+def _direct_ex(m, d, o, precision, eps, eps16, eps32):
+    scores = torch.empty(d.shape[0], dtype=torch.float32, device="cuda")
+    status = torch.empty(d.shape[0], dtype=torch.uint8, device="cuda")
+    best, bs = m.rank(d, o, precision, eps=eps, eps32=eps32, scores=scores, status=status, eps16=eps16)
+    torch.cuda.synchronize()
+    return best.clone(), bs.clone(), scores, status
+
+
+@pytest.mark.parametrize("staged", [False, True])
+def test_plan_with_fp16_tier_matches_rank_ex(gpu_lib, setup, staged):
+    """The FP16 tensor-core tier captured into a plan (advisor_plan_rank_ex /
+    advisor_plan_rank_staged_ex): every replay equals the direct
+    advisor_rank_ex call bit for bit, leaves the same per-tier counts, ranks
+    refilled inputs, and selects what the FP64 oracle selects."""
+    m = setup["m"]
+    eps, eps16, eps32 = setup["eps"]["bf16"], setup["eps"]["fp16"], setup["eps"]["fp32"]
+    d = torch.from_numpy(setup["d_a"]).cuda()
+    o = torch.from_numpy(setup["off"]).cuda()
+    direct = _direct_ex(m, d, o, "bf16", eps, eps16, eps32)
+    counts = m.rescore_counts_ex()
+    assert counts[0] > 0 and counts[1] < counts[0]   # the FP16 tier took candidates and passed on fewer
+    if staged:
+        h = torch.from_numpy(setup["d_a"]).pin_memory()
+        dd = torch.empty_like(d)
+        plan = m.plan_rank_staged(h, dd, o, "bf16", eps, eps32, n_stages=3, eps16=eps16)
+    else:
+        plan = m.plan_rank(d, o, "bf16", eps, eps32, eps16=eps16)
+    assert plan.info()["kernels_per_replay"] > 7   # the FP16 tier adds its own kernels
+    for _ in range(2):
+        plan.launch()
+    torch.cuda.synchronize()
+    for a, b in zip((plan.best, plan.best_score, plan.scores, plan.status), direct):
+        assert torch.equal(a, b)
+    assert m.rescore_counts_ex() == counts
+    assert np.array_equal(plan.best.cpu().numpy(), setup["ref_a"])
+    # refill the bound inputs in place: the next replay ranks the new rows
+    if staged:
+        h.copy_(torch.from_numpy(setup["d_b"]))
+    else:
+        d.copy_(torch.from_numpy(setup["d_b"]).cuda())
+    plan.launch()
+    torch.cuda.synchronize()
+    assert np.array_equal(plan.best.cpu().numpy(), setup["ref_b"])
+    plan.close()
+    if not staged:
+        d.copy_(torch.from_numpy(setup["d_a"]).cuda())
+    assert m.device_status() == 0

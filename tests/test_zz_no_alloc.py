@@ -36,7 +36,10 @@ def test_noalloc_matches_workspace_path_twice(gpu_lib, precision):
     mu, sigma = oracle.fit_standardizer(fc, sc)
     m = advisor.Model(widths, max_rows=16384, max_kernels=1)
     m.set_params(W.make_weights(widths, 3, "he", 0.1), mu, sigma)
-    for call, (n, seed) in enumerate([(5003, 41), (16384, 42)]):   # two calls in a row, different inputs
+    # two calls in a row with different inputs, the larger first: the second, ragged call
+    # (5003 rows, not a multiple of the 128-row tile) must read nothing the first one left
+    # in the shared scratch; the output is poisoned with NaN before each call
+    for call, (n, seed) in enumerate([(16384, 42), (5003, 41)]):
         d = torch.from_numpy(W.make_descriptors(n, seed)).cuda()
         f, st = advisor.advisor_extract_features(d, 64)
         ref = m.score(f, st, precision)
