@@ -5,19 +5,23 @@ Continuous batching: queries arriving while earlier batches are on the GPU
 wait in a FIFO queue; whenever one of the pipelines (a model handle with its
 own workspace, CUDA stream and pinned buffers, all sharing one resident
 parameter block) is idle, the queued queries are packed into its next batch
-up to its row capacity (admission by device memory), copied host->device,
-ranked with one advisor_rank call and copied back.  Several batches are in
-flight at once on different streams.  Every kernel of the path computes each
-row and each kernel segment independently of the rest of the batch, so a
-query's answer is the same alone and in any mix.
+up to its row capacity (admission by device memory: the capacity comes from
+the pipeline's share of a device-memory budget and the library's workspace
+size), copied host->device, ranked with one advisor_rank call and copied
+back.  Each pipeline is driven by a host thread of its own, so that several
+batches are in flight at once on different streams.  Every kernel of the
+path computes each row and each kernel segment independently of the rest of
+the batch, so a query's answer is the same alone and in any mix.
 
-The host logic (Batcher) has no GPU dependency and is tested on the CPU with
-a fake executor.
+The host logic (Batcher, Server, the threaded executor) has no GPU
+dependency and is tested on the CPU with fake executors.
 """
 from __future__ import annotations
 
 import collections
 import dataclasses
+import queue
+import threading
 import time
 
 import numpy as np
@@ -179,6 +183,7 @@ class GpuPipeline:
         self.event = torch.cuda.Event()
         self.batch = None
         self.nk = 0
+        self.intervals = []   # (start, end) timing events of every batch on this pipeline's stream
 
     def idle(self) -> bool:
         return self.batch is None
@@ -186,14 +191,18 @@ class GpuPipeline:
     def launch(self, batch):
         torch = self.torch
         n, k = pack(batch, self.h_desc.numpy(), self.h_off.numpy())
+        ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(self.stream):
+            ev_a.record(self.stream)
             self.d_desc[:n].copy_(self.h_desc[:n], non_blocking=True)
             self.d_off[:k + 1].copy_(self.h_off[:k + 1], non_blocking=True)
             self.model.rank(self.d_desc[:n], self.d_off[:k + 1], self.precision, self.eps, self.eps32,
                             best=self.d_best[:k], best_score=self.d_score[:k], stream=self.stream)
             self.h_best[:k].copy_(self.d_best[:k], non_blocking=True)
             self.h_score[:k].copy_(self.d_score[:k], non_blocking=True)
+            ev_b.record(self.stream)
             self.event.record(self.stream)
+        self.intervals.append((ev_a, ev_b))
         self.batch, self.nk = batch, k
 
     def poll(self):
@@ -202,6 +211,68 @@ class GpuPipeline:
         out = [(self.batch, self.h_best[:self.nk].numpy().copy(), self.h_score[:self.nk].numpy().copy())]
         self.batch = None
         return out
+
+
+class ThreadedPipeline:
+    """A pipeline driven by a worker thread of its own: launch() hands the
+    batch to the worker, which packs it, enqueues the copies and the ranking
+    on the pipeline's stream and waits for them; poll() returns what the
+    worker finished.  The host work of different pipelines (packing,
+    launches, waits; ctypes and torch release the interpreter lock) runs in
+    parallel, so that one pipeline's batch is being enqueued while another's
+    is on the GPU -- with one host thread, launching a small batch takes
+    longer than the GPU takes to rank it, and the batches never overlap."""
+
+    def __init__(self, pipe):
+        self.pipe = pipe
+        self.inbox: queue.Queue = queue.Queue(maxsize=1)
+        self.results: collections.deque = collections.deque()
+        self.busy = False
+        self.error: BaseException | None = None
+        self.thread = threading.Thread(target=self._work, daemon=True)
+        self.thread.start()
+
+    @property
+    def intervals(self):
+        return self.pipe.intervals
+
+    @intervals.setter
+    def intervals(self, v):
+        self.pipe.intervals = v
+
+    def idle(self) -> bool:
+        return not self.busy
+
+    def launch(self, batch):
+        self.busy = True
+        self.inbox.put(batch)
+
+    def _work(self):
+        while True:
+            batch = self.inbox.get()
+            if batch is None:
+                return
+            try:
+                self.pipe.launch(batch)
+                self.pipe.event.synchronize()
+                self.results.extend(self.pipe.poll())
+            except BaseException as e:   # handed to the serving loop by poll()
+                self.error = e
+                self.results.append((batch, [-2] * len(batch), [float("nan")] * len(batch)))
+
+    def poll(self):
+        if self.error is not None:
+            raise RuntimeError("serving pipeline failed") from self.error
+        out = []
+        while self.results:
+            out.append(self.results.popleft())
+        if out:
+            self.busy = False
+        return out
+
+    def close(self):
+        self.inbox.put(None)
+        self.thread.join(timeout=10)
 
 
 def latency_stats(finished: list[Query]) -> dict:
@@ -226,11 +297,50 @@ def make_queries(n_queries: int, rate_per_s: float, seed: int) -> list[Query]:
     return out
 
 
+def max_overlap(intervals) -> int:
+    """Largest number of [start, end) intervals that contain a common instant."""
+    ev = sorted([(a, 1) for a, _ in intervals] + [(b, -1) for _, b in intervals], key=lambda x: (x[0], x[1]))
+    cur = best = 0
+    for _, d in ev:
+        cur += d
+        best = max(best, cur)
+    return best
+
+
+def rows_for_budget(widths, budget_bytes: int, max_queries: int, lo: int = 512, hi: int = 1 << 20) -> int:
+    """Admission by device memory: the largest batch (in variants) whose
+    pipeline fits `budget_bytes` of device memory -- the library's workspace
+    for that many rows (advisor_workspace_bytes) plus the pipeline's own
+    device buffers (descriptors, offsets, answers).  Raises if not even `lo`
+    rows (the largest query) fit."""
+    from . import advisor
+
+    def need(r):
+        return advisor.workspace_bytes(widths, r, max_queries) + r * 128 + (max_queries + 1) * 8 + max_queries * 12
+
+    if need(lo) > budget_bytes:
+        raise ValueError(f"a device-memory budget of {budget_bytes} B does not fit a batch of {lo} variants")
+    while lo < hi:   # need() grows with the rows
+        mid = (lo + hi + 1) // 2
+        if need(mid) <= budget_bytes:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
 def run_serving(base, params, mu, sigma, queries: list[Query], precision="bf16", eps=-1.0, eps32=0.0,
-                pipelines: int = 3, max_rows: int = 8192, max_queries: int = 128, warmup: bool = True):
+                pipelines: int = 3, max_rows: int = 8192, max_queries: int = 128, warmup: bool = True,
+                memory_budget_bytes: int | None = None, threads: bool = True):
     """Serve `queries` (open loop, real clock) with `pipelines` batches in
-    flight; returns (finished queries, stats)."""
+    flight; returns (finished queries, stats).  With memory_budget_bytes, each
+    pipeline's row capacity (the admission bound of a batch) comes from its
+    share of that device-memory budget instead of max_rows.  The stats report
+    the largest number of batches whose copy-in .. copy-out intervals
+    overlapped in device time (max_batches_in_flight)."""
     import torch
+    if memory_budget_bytes is not None:
+        max_rows = rows_for_budget(base.widths, memory_budget_bytes // pipelines, max_queries)
     pipes = [GpuPipeline(base, max_rows, max_queries, params, mu, sigma, precision, eps, eps32)
              for _ in range(pipelines)]
     if warmup:   # first launches (module load, attribute setup) outside the replay
@@ -240,14 +350,30 @@ def run_serving(base, params, mu, sigma, queries: list[Query], precision="bf16",
         torch.cuda.synchronize()
         for p in pipes:
             p.poll()
+    for p in pipes:
+        p.intervals = []
+    execs = [ThreadedPipeline(p) for p in pipes] if threads else pipes
     batcher = Batcher(max_rows, max_queries)
-    srv = Server(batcher, pipes)
+    srv = Server(batcher, execs)
+    ref = torch.cuda.Event(enable_timing=True)
+    ref.record()
     t0 = time.perf_counter()
-    done = srv.run(queries)
+    try:
+        done = srv.run(queries)
+    finally:
+        if threads:
+            for ex in execs:
+                ex.close()
     wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    iv = [(ref.elapsed_time(a), ref.elapsed_time(b)) for p in pipes for a, b in p.intervals]
     st = latency_stats(done)
+    st["batches"] = len(iv)
+    st["max_batches_in_flight"] = max_overlap(iv)
+    st["rows_per_batch_capacity"] = max_rows
     st["queries_per_s"] = len(done) / wall
     st["variants_per_s"] = sum(q.rows for q in done) / wall
     st["rejected"] = len(batcher.rejected)
     st["pipelines"] = pipelines
+    st["host_threads"] = pipelines if threads else 1
     return done, st

@@ -25,7 +25,9 @@ def served():
     eps = base.calibrate_eps(fcal, scal, "bf16")
     eps32 = base.calibrate_eps(fcal, scal, "fp32")
     queries = serving.make_queries(1500, 20000.0, W.SEEDS["serving"])
-    done, st = serving.run_serving(base, params, mu, sigma, queries, "bf16", eps, eps32, pipelines=3)
+    # admission by device memory: 3 pipelines sharing a 144 MB budget
+    done, st = serving.run_serving(base, params, mu, sigma, queries, "bf16", eps, eps32, pipelines=3,
+                                   memory_budget_bytes=144 << 20)
     print("serving stats:", st)
     return dict(base=base, done=done, st=st, eps=eps, eps32=eps32, mu=mu.cpu().numpy(),
                 sigma=sigma.cpu().numpy(), params=params, wl=wl)
@@ -37,6 +39,17 @@ def test_every_query_answered(gpu_lib, served):
     assert all(q.status == "done" and 0 <= q.best < q.rows for q in done)
     st = served["st"]
     assert st["p50_ms"] > 0 and st["p99_ms"] >= st["p50_ms"]
+
+
+def test_batches_overlap_on_the_gpu(gpu_lib, served):
+    """Continuous batching, not a queue alone: at some instant at least two
+    pipelines had a batch in flight on the GPU (copy-in .. copy-out intervals,
+    timed by events on their streams, overlapping)."""
+    st = served["st"]
+    print("batches:", st["batches"], "max in flight:", st["max_batches_in_flight"],
+          "rows per batch:", st["rows_per_batch_capacity"])
+    assert st["max_batches_in_flight"] >= 2
+    assert st["rows_per_batch_capacity"] >= 512   # the device-memory budget admits the largest query
 
 
 def test_alone_equals_mix(gpu_lib, served):

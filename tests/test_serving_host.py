@@ -105,3 +105,72 @@ def test_server_continuous_batching_with_slow_executor():
     admitted = sorted(done, key=lambda x: (x.admitted, x.arrival))
     assert [x.qid for x in admitted] == sorted(x.qid for x in done)
     assert len(order) == len(done)
+
+
+def test_max_overlap_counts_batches_in_flight():
+    assert serving.max_overlap([]) == 0
+    assert serving.max_overlap([(0, 1), (1, 2), (2, 3)]) == 1          # back to back: never two at once
+    assert serving.max_overlap([(0, 5), (1, 2), (1.5, 3), (4, 6)]) == 3
+    assert serving.max_overlap([(0, 10), (2, 3), (2, 3), (9, 11)]) == 3
+
+
+def test_rows_for_budget_follows_the_workspace_size():
+    """Admission by device memory: the row capacity is the largest batch whose
+    workspace (the library's own size function) and buffers fit the budget."""
+    from paper_2301_03636_gb300 import advisor
+    widths, q = (32, 128, 128, 1), 128
+
+    def need(r):
+        return advisor.workspace_bytes(widths, r, q) + r * 128 + (q + 1) * 8 + q * 12
+
+    for budget in (40 << 20, 64 << 20, 200 << 20):
+        r = serving.rows_for_budget(widths, budget, q)
+        assert need(r) <= budget < need(r + 1)
+    try:
+        serving.rows_for_budget(widths, 1 << 10, q)
+        raise AssertionError("a budget smaller than one query must be refused")
+    except ValueError:
+        pass
+
+
+def test_threaded_pipeline_runs_batches_on_its_worker():
+    """The threaded executor: launch() returns at once, the worker runs the
+    pipe's launch / wait / poll, poll() hands the results back and frees it."""
+    import threading
+    import time as _t
+
+    class FakePipe:
+        def __init__(self):
+            self.intervals, self.threads, self.pending = [], set(), None
+
+            class Ev:
+                def synchronize(self_inner):
+                    _t.sleep(0.01)
+            self.event = Ev()
+
+        def launch(self, batch):
+            self.threads.add(threading.get_ident())
+            self.pending = batch
+
+        def poll(self):
+            b, self.pending = self.pending, None
+            return [(b, [q.rows - 1 for q in b], [float(q.qid) for q in b])]
+
+    pipe = FakePipe()
+    ex = serving.ThreadedPipeline(pipe)
+    try:
+        qs = [serving.Query(i, np.zeros((3 + i, 16), np.int64), 0.0) for i in range(3)]
+        assert ex.idle()
+        ex.launch(qs)
+        assert not ex.idle()
+        got = []
+        for _ in range(500):
+            got = ex.poll()
+            if got:
+                break
+            _t.sleep(0.002)
+        assert got and [b for b in got[0][1]] == [2, 3, 4] and ex.idle()
+        assert pipe.threads == {ex.thread.ident}   # the GPU calls ran on the worker thread
+    finally:
+        ex.close()
+    assert not ex.thread.is_alive()
