@@ -94,6 +94,53 @@ def topn_leg(m, desc, offs, eps, eps32, n, flush, stream, top_n=10, reps=50, eps
     return out
 
 
+def tensor_peaks_leg(dev, reps=10):
+    """Dense GEMM rates measured on this GPU for the operand types the scorers
+    use beside BF16 (library GEMMs, for the roofline denominators only): FP8
+    E4M3 with per-tensor scales (torch._scaled_mm, 8192^3, BF16 output), BF16
+    at the same size in the same process (so that the FP8/BF16 ratio is
+    measured, not nominal), and FP64 (torch.matmul, 4096^3).  Best of `reps`
+    after warm-up (burst), 2 n^3 FLOP per product."""
+    import torch
+
+    def best_ms(fn, warm=3):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    out = {"method": "best of %d after warm-up; 2 n^3 FLOP per product" % reps}
+    n = 8192
+    x = torch.randn(n, n, device=dev)
+    y = torch.randn(n, n, device=dev)
+    xb, yb = x.to(torch.bfloat16), y.to(torch.bfloat16)
+    ms = best_ms(lambda: torch.matmul(xb, yb))
+    out["bf16_tflops"] = 2 * n ** 3 / (ms / 1000.0) / 1e12
+    try:
+        x8 = x.to(torch.float8_e4m3fn)
+        y8 = y.t().contiguous().to(torch.float8_e4m3fn).t()   # column-major second operand
+        one = torch.ones((), device=dev, dtype=torch.float32)
+        ms = best_ms(lambda: torch._scaled_mm(x8, y8, scale_a=one, scale_b=one, out_dtype=torch.bfloat16))
+        out["fp8_e4m3_tflops"] = 2 * n ** 3 / (ms / 1000.0) / 1e12
+        out["fp8_over_bf16"] = out["fp8_e4m3_tflops"] / out["bf16_tflops"]
+    except Exception as e:   # reported; the BF16 and FP64 figures stand
+        out["fp8_error"] = repr(e)
+    n64 = 4096
+    xd, yd = torch.randn(n64, n64, device=dev, dtype=torch.float64), torch.randn(n64, n64, device=dev,
+                                                                                 dtype=torch.float64)
+    ms = best_ms(lambda: torch.matmul(xd, yd))
+    out["fp64_tflops"] = 2 * n64 ** 3 / (ms / 1000.0) / 1e12
+    return out
+
+
 def err_stats(y, y64):
     """Max and 99th percentile of |y - y64| over the rows (y64: the FP64 scorer's values)."""
     e = (y.double() - y64.double()).abs().cpu().numpy()
@@ -156,6 +203,12 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout_s: float = 10.0):
+        """Block until nvidia-smi has printed its first sample (or the timeout)."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout_s:
+            time.sleep(0.02)
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -180,8 +233,11 @@ class ClockSampler:
             for nm, v in zip(names, parts[2:6]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if not sm:
+            out["error"] = "no nvidia-smi sample was taken during the sampled window"
+        return out
 
 
 def cpu_baseline(desc, off, params, mu, sigma, min_seconds=10.0):
@@ -259,10 +315,13 @@ def serving_leg(dev):
     for rate in (2000, 10000, 50000):
         n = int(min(4000, rate * 0.5))
         qs = serving.make_queries(n, float(rate), W.SEEDS["serving"] + rate)
-        _, st = serving.run_serving(base, params, mu, sigma, qs, "bf16", eps, eps32, pipelines=3)
+        _, st = serving.run_serving(base, params, mu, sigma, qs, "bf16", eps, eps32, pipelines=3,
+                                    memory_budget_bytes=144 << 20)
         st["rate_per_s"] = rate
         runs.append(st)
-    return {"workload": "queries of 4..512 variants, 32-128-128-1, bf16 + re-score", "runs": runs}
+    return {"workload": "queries of 4..512 variants, 32-128-128-1, bf16 + re-score",
+            "admission": "3 pipelines, row capacity each from its share of a 144 MB device-memory budget",
+            "runs": runs}
 
 
 def training_leg(dev, steps=20):
@@ -370,6 +429,10 @@ def dslash_leg(dev, reps=50):
     mu, sigma = advisor.advisor_fit_standardizer(fcal, scal)
     m = advisor.Model(wl.widths, max_rows=84 * K, max_kernels=K, device=dev)
     m.set_params(wl.weights(), mu, sigma)
+    # error bounds calibrated on the workload's own distribution: other
+    # Dslash-shaped kernels (another seed) enumerated by the same GPU enumerator
+    v_cal, _ = advisor.advisor_enumerate_variants(torch.from_numpy(W.make_dslash_kernels(256, 1023)).to(dev))
+    fcal, scal = advisor.advisor_extract_features(v_cal.contiguous(), wl.n_features)
     eps, eps32 = m.calibrate_eps(fcal, scal, "bf16"), m.calibrate_eps(fcal, scal, "fp32")
     v, off = advisor.advisor_enumerate_variants(k)
     n = v.shape[0]
@@ -404,16 +467,25 @@ def dslash_leg(dev, reps=50):
     ref = best.clone()
     ms16 = run(eps16)
     c16t, c32t, c64t = m.rescore_counts_ex()
+    # the calibrated bounds on the ranked rows themselves (the FP64 scorer's values equal
+    # the oracle's bit for bit): the tiers' exactness rests on |score - fp64| <= eps
+    f_v, st_v = advisor.advisor_extract_features(v.contiguous(), wl.n_features)
+    y64 = m.score_fp64(f_v, st_v)
+    e_bf16 = err_stats(m.score(f_v, st_v, "bf16"), y64)["max_abs_err_vs_fp64"]
+    e_fp16 = err_stats(m.score(f_v, st_v, "fp16"), y64)["max_abs_err_vs_fp64"]
+    bounds = {"calibration": "Dslash-shaped kernels of another seed, enumerated on the GPU",
+              "eps_bf16": eps, "max_abs_err_bf16": e_bf16, "eps_fp16": eps16, "max_abs_err_fp16": e_fp16,
+              "bound_held": bool(e_bf16 <= eps and e_fp16 <= eps16)}
     return {"workload": f"{K} Dslash-shaped kernels (depth 4, lattice trip counts), 84 variants each = {n}, "
                         "enumerated on the GPU and ranked with 64-256-256-256-1 (bf16 + re-score)",
             "variants": n, "ms_per_step": ms, "variants_per_s": n / (ms / 1000.0), "kernels_per_s": K / (ms / 1000.0),
-            "near_tie_fp32_rows": c32, "near_tie_fp64_rows": c64,
+            "near_tie_fp32_rows": c32, "near_tie_fp64_rows": c64, "error_bounds": bounds,
             "fp16tier": {"ms_per_step": ms16, "variants_per_s": n / (ms16 / 1000.0), "near_tie_fp16_rows": c16t,
                          "near_tie_fp32_rows": c32t, "near_tie_fp64_rows": c64t,
                          "same_selection": bool(torch.equal(best, ref))}}
 
 
-def large_sweep_leg(dev, reps=5, rows=0):
+def large_sweep_leg(dev, reps=5, rows=0, fp8_ratio=None):
     """The large sweep: 2^20 variants of 65,536 kernels (2..64 each), F = 128,
     MLP 128-1024-1024-1024-1, scored on the tensor cores one launch per hidden
     layer (BF16, FP16) and on the FP32 SIMT path, then ranked with the near-tie
@@ -462,7 +534,10 @@ def large_sweep_leg(dev, reps=5, rows=0):
                   "peak": tf, "peak_source": src + " dense bf16 (fp16 runs at the bf16 rate)",
                   **err_stats(y[:sample], y64)}
     # E4M3: static activation scales from the calibration sample; peak = the
-    # measured dense BF16 peak x the nominal FP8 / BF16 ratio (4.5 / 2.25)
+    # measured dense BF16 peak x the FP8 / BF16 ratio measured in this run
+    # (tensor_peaks_leg), else the nominal ratio (4.5 / 2.25)
+    r8 = fp8_ratio if fp8_ratio else 2.0
+    r8_src = "measured fp8/bf16 ratio" if fp8_ratio else "nominal fp8/bf16 ratio 2"
     m.calibrate_fp8(fcal)
     m.set_profile_events(*kev)
     for _ in range(2):
@@ -476,8 +551,8 @@ def large_sweep_leg(dev, reps=5, rows=0):
     m.set_profile_events(None, None)
     ms = float(np.median(tk))
     ach = n * flop_row / (ms / 1000.0) / 1e12
-    out["fp8"] = {"layers_ms": ms, "variants_per_s": n / (ms / 1000.0), "tflops": ach, "frac_of_peak": ach / (2 * tf),
-                  "peak": 2 * tf, "peak_source": src + " dense bf16 x 2 (nominal fp8 / bf16 ratio)",
+    out["fp8"] = {"layers_ms": ms, "variants_per_s": n / (ms / 1000.0), "tflops": ach, "frac_of_peak": ach / (r8 * tf),
+                  "peak": r8 * tf, "peak_source": f"{src} dense bf16 x {r8:.3f} ({r8_src})",
                   **err_stats(y[:sample], y64)}
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     y = m.score(f, st, "fp32")
@@ -664,6 +739,8 @@ def main():
     prec = args.precision
     eps = m.calibrate_eps(fcal, scal, prec) if prec != "fp32" else m.calibrate_eps(fcal, scal, "fp32")
     eps32 = m.calibrate_eps(fcal, scal, "fp32")
+    # 16-bit first tier: the FP16 tensor-core tier sits between it and the FP32 re-score
+    eps16 = m.calibrate_eps(fcal, scal, "fp16") if prec != "fp32" else None
     desc = torch.from_numpy(desc_np).to(dev)
     offs = torch.from_numpy(off).to(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -677,20 +754,61 @@ def main():
     torch.cuda.synchronize()
     m.set_profile_events(*kev)
     plan = m.plan_rank(desc, offs, prec, eps, eps32, autotune=True)
+    tier_choice = None
+    if eps16 is not None:
+        # the FP16 tensor-core tier trades FP32 re-score rows for kernels of its own:
+        # both plans are timed here (20 replays each, L2 flushed) and the faster one is
+        # the step; both times are reported
+        plan16 = m.plan_rank(desc, offs, prec, eps, eps32, autotune=True, eps16=eps16)
+
+        def replay_ms(pl, reps=20):
+            for _ in range(3):
+                pl.launch()
+            torch.cuda.synchronize()
+            tt = []
+            for i in range(reps):
+                flush.fill_(i & 0xFF)
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                pl.launch()
+                b_.record(stream)
+                tt.append((a_, b_))
+            torch.cuda.synchronize()
+            return float(np.median([x.elapsed_time(y) for x, y in tt]))
+        ms_without, ms_with = replay_ms(plan), replay_ms(plan16)
+        tier_choice = {"ms_without_fp16_tier": ms_without, "ms_with_fp16_tier": ms_with,
+                       "fp16_tier_in_step": ms_with < ms_without}
+        if ms_with < ms_without:
+            plan.close()
+            plan = plan16
+        else:
+            plan16.close()
+            eps16 = None
     m.set_profile_events(None, None)
     tuned = plan.info()
     m_eps = {prec: eps}
-    plans = {prec: plan}
+    plans = {}
     for _ in range(args.warmup):
         flush.fill_(1)
         plan.launch()
     torch.cuda.synchronize()
 
+    # ---- clocks: nvidia-smi samples from ~1.5 s of the same replays right
+    # before the timed steps through the end of the timed steps (the timed
+    # region alone is too short for nvidia-smi to sample) ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    clocks.wait_first()
+    t_end = time.time() + 1.5
+    while time.time() < t_end:
+        for i in range(50):
+            flush.fill_(i & 0xFF)
+            plan.launch()
+        torch.cuda.synchronize()
+
     # ---- timed region ----
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t_kernel = []
-    clocks = ClockSampler(local)
-    clocks.start()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -717,8 +835,18 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = n * world / (ms / 1000.0)
-    # rows the last replay sent to the FP32 and FP64 re-score tiers
-    c32, c64 = m.rescore_counts()
+    # rows the last replay sent to the FP16, FP32 and FP64 re-score tiers
+    if eps16 is not None:
+        c16, c32, c64 = m.rescore_counts_ex()
+    else:
+        c16 = None
+        c32, c64 = m.rescore_counts()
+    # accuracy of the first-tier scores against the FP64 scorer (which equals the oracle's
+    # values bit for bit): the error statement of this run's precision
+    f_all, st_all = advisor.advisor_extract_features(desc, WL.n_features)
+    y64_all = m.score_fp64(f_all, st_all)
+    head_err = err_stats(m.score(f_all, st_all, prec), y64_all)
+    head_err_fp16 = err_stats(m.score(f_all, st_all, "fp16"), y64_all) if prec != "fp32" else None
 
     # ---- end to end through the public API with host buffers ----
     desc_h = torch.from_numpy(desc_np).pin_memory()
@@ -753,7 +881,7 @@ def main():
     # the same plan bound to the pinned host descriptors: the extraction kernel
     # (and the re-score kernels, for their few rows) read them over the
     # CPU-GPU link while they compute; only the offsets are copied
-    plan_h = m.plan_rank(desc_h, offs, prec, eps, eps32, autotune=True)
+    plan_h = m.plan_rank(desc_h, offs, prec, eps, eps32, autotune=True, eps16=eps16)
 
     def e2e_host_step():
         offs.copy_(off_h, non_blocking=True)
@@ -761,32 +889,11 @@ def main():
         best_h.copy_(plan_h.best, non_blocking=True)
         bs_h.copy_(plan_h.best_score, non_blocking=True)
 
-    # the copy split over four streams (several copy engines at once)
-    side = [torch.cuda.Stream(dev) for _ in range(4)]
-    bounds = np.linspace(0, n, len(side) + 1).astype(np.int64)
-
-    def e2e_split_step():
-        ready = torch.cuda.Event()
-        ready.record(stream)
-        done = []
-        for i, st_ in enumerate(side):
-            st_.wait_event(ready)
-            with torch.cuda.stream(st_):
-                desc[bounds[i]:bounds[i + 1]].copy_(desc_h[bounds[i]:bounds[i + 1]], non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(st_)
-            done.append(ev)
-        offs.copy_(off_h, non_blocking=True)
-        for ev in done:
-            stream.wait_event(ev)
-        plan.launch()
-        best_h.copy_(plan.best, non_blocking=True)
-        bs_h.copy_(plan.best_score, non_blocking=True)
-
-    # copy-in in chunks that overlap the scoring of the chunks before them
+    # copy-in in chunks that overlap the scoring of the chunks before them: the
+    # reported end-to-end mode (advisor_plan_rank_staged_ex, 4 chunks)
     staged = {}
     for ns in (3, 4, 6):
-        ps = m.plan_rank_staged(desc_h, desc, offs, prec, eps, eps32, n_stages=ns, autotune=True)
+        ps = m.plan_rank_staged(desc_h, desc, offs, prec, eps, eps32, n_stages=ns, autotune=True, eps16=eps16)
 
         def e2e_staged_step(ps=ps):
             offs.copy_(off_h, non_blocking=True)
@@ -795,20 +902,27 @@ def main():
             bs_h.copy_(ps.best_score, non_blocking=True)
         staged[ns] = (ps, e2e_staged_step)
 
-    modes = {"descriptors and offsets copied from pinned host memory": time_e2e(e2e_copy_step),
-             "descriptors copied in four concurrent chunks, offsets copied": time_e2e(e2e_split_step),
+    def copy_only_step():
+        # the ceiling of the copy-in: the same bytes from pinned host memory, nothing else
+        desc.copy_(desc_h, non_blocking=True)
+        offs.copy_(off_h, non_blocking=True)
+
+    reported = "descriptors copied in 4 chunks overlapping the scoring (advisor_plan_rank_staged_ex), offsets copied"
+    modes = {reported: time_e2e(staged[4][1]),
+             "descriptors and offsets copied from pinned host memory, then the plan": time_e2e(e2e_copy_step),
              "descriptors read by the kernels from pinned host memory, offsets copied": time_e2e(e2e_host_step)}
-    for ns, (ps, fn) in staged.items():
-        modes[f"descriptors copied in {ns} chunks overlapping the scoring (advisor_rank_staged), offsets copied"] = \
-            time_e2e(fn)
+    for ns in (3, 6):
+        modes[f"descriptors copied in {ns} chunks overlapping the scoring, offsets copied"] = time_e2e(staged[ns][1])
+    ms_copy = time_e2e(copy_only_step)
     same = bool(torch.equal(plan_h.best, plan.best)) and all(torch.equal(ps.best, plan.best)
                                                            for ps, _ in staged.values())
-    mode = min(modes, key=modes.get)
-    ms_e2e = modes[mode]
+    ms_e2e = modes[reported]
+    h2d = int(desc_h.numel() * 8 + off_h.numel() * 8)
     e2e = {"value": n * world / (ms_e2e / 1000.0), "unit": UNIT,
-           "h2d_bytes_per_step": int(desc_h.numel() * 8 + off_h.numel() * 8),
-           "d2h_bytes_per_step": int(K * 4 + K * 8), "mode": mode, "ms_per_step": ms_e2e,
-           "ms_per_step_by_mode": modes, "same_selection": same}
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(K * 4 + K * 8), "mode": reported,
+           "ms_per_step": ms_e2e, "ms_per_step_other_modes": {k: v for k, v in modes.items() if k != reported},
+           "copy_in_only_ms": ms_copy, "copy_in_only_gbs": h2d / (ms_copy / 1000.0) / 1e9,
+           "frac_of_copy_in_only": ms_copy / ms_e2e, "same_selection": same}
 
     # ---- roofline of the dominant kernel (the tensor-core MLP) ----
     hbm, tf, src = peaks()
@@ -823,10 +937,20 @@ def main():
            "vs_baseline": None, "dtype": prec, "data": "synthetic",
            "config": {"workload": WL.name, "kernels": K, "variants": n, "features": WL.n_features,
                       "mlp": "-".join(map(str, WL.widths)), "precision": prec, "l2": "flushed (512 MB write) "
-                      "between steps", "near_tie_rescore": "fp32 then fp64", "eps": eps, "eps32": eps32,
-                      "near_tie_fp32_rows": c32, "near_tie_fp64_rows": c64, "near_tie_fraction": c32 / n,
-                      "batching": "one CUDA graph per step (advisor_plan_rank, autotuned launch shapes)",
-                      "launch_config": tuned["config"], "kernels_per_step": tuned["kernels_per_replay"]},
+                      "between steps",
+                      "near_tie_rescore": ("fp16 tensor-core tier, then fp32, then fp64" if eps16 is not None
+                                           else "fp32 then fp64"),
+                      "eps": eps, "eps16": eps16, "eps32": eps32, "near_tie_fp16_rows": c16,
+                      "near_tie_fp32_rows": c32, "near_tie_fp64_rows": c64,
+                      "near_tie_fraction": (c16 if c16 is not None else c32) / n,
+                      **{k: v for k, v in head_err.items()},
+                      "at_target_fp16": ({"precision": "fp16", "target_abs_err": 1e-2, **head_err_fp16}
+                                         if head_err_fp16 is not None else None),
+                      "fp16_tier_choice": tier_choice,
+                      "batching": "one CUDA graph per step (advisor_plan_rank_ex, autotuned launch shapes)",
+                      "launch_config": tuned["config"], "kernels_per_step": tuned["kernels_per_replay"],
+                      "clocks_window": "1.5 s of the same replays right before the timed steps, and the timed "
+                                       "steps"},
            "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clk}
 
     if rank == 0 and not args.no_extras:
@@ -869,10 +993,14 @@ def main():
         runs = out["serving"].get("runs", [])
         srv10 = [r for r in runs if r["rate_per_s"] == 10000]
         out["p99_query_ms"] = srv10[0]["p99_ms"] if srv10 else None
+        out["serving_ms_by_rate"] = {str(r["rate_per_s"]): {"p50": r["p50_ms"], "p99": r["p99_ms"],
+                                                           "max_batches_in_flight": r.get("max_batches_in_flight")}
+                                     for r in runs}
         leg("plain_512", lambda: plain_latency_leg(dev))
         leg("dslash", lambda: dslash_leg(dev))
         leg("training", lambda: training_leg(dev))
-        leg("large_sweep", lambda: large_sweep_leg(dev))
+        leg("tensor_peaks", lambda: tensor_peaks_leg(dev))
+        leg("large_sweep", lambda: large_sweep_leg(dev, fp8_ratio=out["tensor_peaks"].get("fp8_over_bf16")))
         leg("kernel_rooflines", lambda: kernel_rooflines_leg(dev, m, f, st, flush))
 
         def cpu_leg():
@@ -880,8 +1008,32 @@ def main():
             import oracle
             fc, sc = oracle.extract_features(W.calibration_descriptors(65536), WL.n_features)
             mu_o, sg_o = oracle.fit_standardizer(fc, sc)
-            return cpu_baseline(desc_np, off, params, mu_o, sg_o)
+            res = cpu_baseline(desc_np, off, params, mu_o, sg_o)
+            # oracle match of the timed path: the oracle's selection for every kernel of
+            # the timed workload, against one replay of the timed plan (same graph, same
+            # buffers) on the model with the oracle's standardiser (the oracle takes no
+            # input from the CUDA path; the weights are the seeded ones both sides use)
+            t0 = time.perf_counter()
+            best_o = oracle.rank(desc_np, off, WL.widths, params, mu_o, sg_o)[0]
+            t_full = time.perf_counter() - t0
+            mu_g, sg_g = mu.cpu().numpy(), sigma.cpu().numpy()
+            m.set_params(params, mu_o, sg_o)
+            try:
+                plan.launch()
+                torch.cuda.synchronize()
+                got = plan.best.cpu().numpy()
+            finally:
+                m.set_params(params, mu, sigma)
+            res["oracle_match"] = {
+                "kernels": int(K), "identical": bool(np.array_equal(got, best_o)),
+                "mismatches": int((got != best_o).sum()), "oracle_seconds": t_full,
+                "standardiser_max_rel_diff_gpu_vs_oracle": float(max(
+                    np.max(np.abs(mu_g - mu_o) / np.maximum(np.abs(mu_o), 1e-300)),
+                    np.max(np.abs(sg_g - sg_o) / np.maximum(np.abs(sg_o), 1e-300))))}
+            return res
         leg("cpu_baseline", cpu_leg)
+        om = out.get("cpu_baseline", {}).get("oracle_match")
+        out["config"]["oracle_match"] = om["identical"] if om else None
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
