@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libadvisor.so")
 SOURCES = ["api.cu", "extract.cu", "mlp_simt.cu", "mlp_tc.cu", "mlp_layer_tc.cu", "select.cu", "pack.cu", "train.cu",
-           "train_tc.cu", "noalloc.cu", "plan.cu", "enumerate.cu", "peak.cu",
+           "train_tc.cu", "gemm_tc.cu", "noalloc.cu", "plan.cu", "enumerate.cu", "peak.cu",
            "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -67,10 +67,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    # cuBLASLt (the 16-bit training GEMMs) from the toolkit, found at run time through the rpath
-    lib_dir = os.path.join(os.path.dirname(os.path.dirname(cc)), "lib64")
-    cmd = [cc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + [
-        "-L" + lib_dir, "-lcublasLt", "-Xlinker", "-rpath=" + lib_dir]
+    cmd = [cc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -48,7 +48,6 @@ struct advisor_model {
     adv::LaunchConfig cfg{};  // launch shapes of the hot path (a plan may set them)
     bool fp8_calibrated = false;   // activation scales stored (advisor_model_calibrate_fp8)
     int saved_fmt = 0;             // precision of the last advisor_forward_saved: 0 FP32, 1 BF16, 2 FP16
-    adv::LtContext* lt = nullptr;  // cuBLASLt handle of the 16-bit training GEMMs (created on first use)
     bool last_mid = false;         // the last re-scoring selection ran the FP16 middle tier
     // advisor_rank_staged: the stream that copies the descriptor chunks and the
     // events that hand each chunk to the scoring stream (created on first use)
@@ -58,7 +57,6 @@ struct advisor_model {
     // inference copies were last built: rebuilt before the next scoring call
     bool images_stale = false;
     ~advisor_model() {
-        adv::lt_destroy(lt);
         for (cudaEvent_t e : stage_ev)
             if (e) cudaEventDestroy(e);
         if (copy_stream) cudaStreamDestroy(copy_stream);
@@ -942,8 +940,6 @@ advisor_status advisor_rank_topn(advisor_model_t m, const advisor_variant_desc* 
 int train_fmt(advisor_model* m, advisor_precision p) {
     if (p == ADVISOR_FP32) return 0;
     if (p != ADVISOR_BF16 && p != ADVISOR_FP16) return -1;
-    if (!m->lt) m->lt = adv::lt_create();
-    if (!m->lt) return -1;
     return p == ADVISOR_BF16 ? 1 : 2;
 }
 
@@ -977,9 +973,9 @@ advisor_status advisor_train_step(advisor_model_t m, const int32_t* d_feat_q16, 
     adv::FusedFwd ff{};
     cudaError_t e = fmt == 0 ? adv::launch_train_step(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), d_feat_q16,
                                                       d_labels, n_rows, &h, step, nullptr, d_loss, m->num_sms, stream)
-                             : adv::launch_train_step_tc(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), m->lt,
-                                                         fmt, d_feat_q16, d_labels, n_rows, &h, step, nullptr, d_loss,
-                                                         stream, fused_fwd(m, fmt, &ff));
+                             : adv::launch_train_step_tc(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), fmt,
+                                                         d_feat_q16, d_labels, n_rows, &h, step, nullptr, d_loss,
+                                                         stream, status_word(m), fused_fwd(m, fmt, &ff));
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     m->adam_step = step;
     m->images_stale = true;
@@ -1004,8 +1000,8 @@ advisor_status advisor_train_step_ex(advisor_model_t m, const int32_t* d_feat_q1
     o.alpha = opt->alpha;
     const int64_t step = m->adam_step + 1;
     adv::FusedFwd ff{};
-    cudaError_t e = adv::launch_train_step_ex(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), m->lt, fmt,
-                                              d_feat_q16, d_labels, n_rows, o, step, d_loss, stream,
+    cudaError_t e = adv::launch_train_step_ex(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), fmt, d_feat_q16,
+                                              d_labels, n_rows, o, step, d_loss, stream, status_word(m),
                                               fused_fwd(m, fmt, &ff));
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     m->adam_step = step;
@@ -1023,9 +1019,9 @@ advisor_status advisor_loss_grad(advisor_model_t m, const int32_t* d_feat_q16, c
     if (fmt < 0) return ADVISOR_ERR_UNSUPPORTED;
     adv::FusedFwd ff{};
     if (fmt != 0)
-        return cuda_status(adv::launch_train_step_tc(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), m->lt, fmt,
+        return cuda_status(adv::launch_train_step_tc(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), fmt,
                                                      d_feat_q16, d_labels, n_rows, nullptr, 0, d_grad, d_loss,
-                                                     stream, fused_fwd(m, fmt, &ff)));
+                                                     stream, status_word(m), fused_fwd(m, fmt, &ff)));
     return cuda_status(adv::launch_train_step(m->L, m->T, m->P, m->WS + m->W.train, mlp_desc(m), d_feat_q16,
                                               d_labels, n_rows, nullptr, 0, d_grad, d_loss, m->num_sms, stream));
 }
@@ -1047,8 +1043,9 @@ advisor_status advisor_forward_saved(advisor_model_t m, const int32_t* d_feat_q1
     adv::FusedFwd ff{};
     cudaError_t e = fmt == 0 ? adv::launch_forward_saved(m->L, m->T, m->WS + m->W.train, mlp_desc(m), d_feat_q16,
                                                          n_rows, d_y, stream)
-                             : adv::launch_forward_saved_tc(m->L, m->T, m->WS + m->W.train, mlp_desc(m), m->lt, fmt,
-                                                            d_feat_q16, n_rows, d_y, stream, fused_fwd(m, fmt, &ff));
+                             : adv::launch_forward_saved_tc(m->L, m->T, m->WS + m->W.train, mlp_desc(m), fmt,
+                                                            d_feat_q16, n_rows, d_y, stream, status_word(m),
+                                                            fused_fwd(m, fmt, &ff));
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     m->saved_rows = n_rows;
     m->saved_fmt = fmt;
@@ -1060,8 +1057,8 @@ advisor_status advisor_backward(advisor_model_t m, const float* d_dy, int64_t n_
     if (!m || !d_dy || !d_grad || n_rows < 1) return ADVISOR_ERR_INVALID_ARGUMENT;
     if (n_rows != m->saved_rows) return ADVISOR_ERR_INVALID_ARGUMENT;
     if (m->saved_fmt != 0)
-        return cuda_status(adv::launch_backward_tc(m->L, m->T, m->WS + m->W.train, mlp_desc(m), m->lt, m->saved_fmt,
-                                                   d_dy, n_rows, d_grad, stream));
+        return cuda_status(adv::launch_backward_tc(m->L, m->T, m->WS + m->W.train, mlp_desc(m), m->saved_fmt,
+                                                   d_dy, n_rows, d_grad, stream, status_word(m)));
     return cuda_status(adv::launch_backward(m->L, m->T, m->WS + m->W.train, mlp_desc(m), d_dy, n_rows, d_grad, stream));
 }
 

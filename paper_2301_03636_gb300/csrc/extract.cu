@@ -76,7 +76,7 @@ __device__ __forceinline__ void write_x_row_e4m3(uint8_t* x_img, int nslab, int6
 template <int F, int FMT>
 __device__ __forceinline__ void write_x_row(uint8_t* x_img, int nslab, int64_t row, const int32_t (&f)[F],
                                             bool valid_row, const float* __restrict__ sa,
-                                            const float* __restrict__ sc) {
+                                            const float* __restrict__ sc, uint16_t* x_rm = nullptr) {
     const int64_t tile = row / ADV_TILE_M;
     const uint32_t r = (uint32_t)(row % ADV_TILE_M);
     uint8_t* tile_base = x_img + (size_t)tile * nslab * ADV_X_SLAB_BYTES;
@@ -93,8 +93,11 @@ __device__ __forceinline__ void write_x_row(uint8_t* x_img, int nslab, int64_t r
                                                    -__ldg(sc + (k < F ? k : 0)))
                                             : 0.f;
             }
-            *reinterpret_cast<uint4*>(tile_base + (size_t)s * ADV_X_SLAB_BYTES + sw128_offset(r, c)) =
-                pack8<FMT>(z);
+            const uint4 pk = pack8<FMT>(z);
+            *reinterpret_cast<uint4*>(tile_base + (size_t)s * ADV_X_SLAB_BYTES + sw128_offset(r, c)) = pk;
+            if constexpr (F % 8 == 0)
+                if (x_rm && valid_row && s * 64 + c * 8 < F)
+                    *reinterpret_cast<uint4*>(x_rm + (size_t)row * F + s * 64 + c * 8) = pk;
         }
     }
 }
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(128) standardize_kernel(const int32_t* __restr
                                                           int64_t n_rows_padded, uint8_t* x_img, int nslab,
                                                           const float* __restrict__ sa,
                                                           const float* __restrict__ sc,
-                                                          const float* __restrict__ x8_scale) {
+                                                          const float* __restrict__ x8_scale, uint16_t* x_rm) {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= n_rows_padded) return;
     int32_t f[F];
@@ -201,7 +204,7 @@ __global__ void __launch_bounds__(128) standardize_kernel(const int32_t* __restr
     }
     (void)status;  // invalid rows are scored +inf by the scorer's epilogue
     if constexpr (FMT == 3) write_x_row_e4m3<F>(x_img, nslab, row, f, valid, sa, sc, 1.f / __ldg(x8_scale));
-    else write_x_row<F, FMT>(x_img, nslab, row, f, valid, sa, sc);
+    else write_x_row<F, FMT>(x_img, nslab, row, f, valid, sa, sc, x_rm);
 }
 
 // Mean and population standard deviation of feature/65536 per column over
@@ -304,25 +307,29 @@ cudaError_t launch_extract(const ExtractArgs& a, int F, int fmt, cudaStream_t s,
 template <int F>
 static cudaError_t launch_standardize_f(const int32_t* feat, const uint8_t* status, int64_t n, int64_t npad,
                                         uint8_t* x_img, int nslab, const float* sa, const float* sc, int fmt,
-                                        const float* x8_scale, cudaStream_t s) {
+                                        const float* x8_scale, uint16_t* x_rm, cudaStream_t s) {
     const unsigned grid = (unsigned)((npad + 127) / 128);
     if (grid == 0) return cudaSuccess;
     if (fmt == 3 && !x8_scale) return cudaErrorInvalidValue;
-    if (fmt == 1) standardize_kernel<F, 1><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc, x8_scale);
-    else if (fmt == 3) standardize_kernel<F, 3><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc, x8_scale);
-    else standardize_kernel<F, 2><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc, x8_scale);
+    if (x_rm && (fmt == 3 || F % 8 != 0 || ((uintptr_t)x_rm & 15) != 0)) return cudaErrorInvalidValue;
+    if (fmt == 1)
+        standardize_kernel<F, 1><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc, x8_scale, x_rm);
+    else if (fmt == 3)
+        standardize_kernel<F, 3><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc, x8_scale, x_rm);
+    else
+        standardize_kernel<F, 2><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc, x8_scale, x_rm);
     adv_count_launch(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_standardize(const int32_t* feat, const uint8_t* status, int64_t n, int64_t npad, uint8_t* x_img,
                                int nslab, const float* sa, const float* sc, int F, int fmt, cudaStream_t s,
-                               const float* x8_scale) {
+                               const float* x8_scale, uint16_t* x_rm) {
     switch (F) {
-        case 32: return launch_standardize_f<32>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, s);
-        case 33: return launch_standardize_f<33>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, s);
-        case 64: return launch_standardize_f<64>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, s);
-        case 128: return launch_standardize_f<128>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, s);
+        case 32: return launch_standardize_f<32>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, x_rm, s);
+        case 33: return launch_standardize_f<33>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, x_rm, s);
+        case 64: return launch_standardize_f<64>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, x_rm, s);
+        case 128: return launch_standardize_f<128>(feat, status, n, npad, x_img, nslab, sa, sc, fmt, x8_scale, x_rm, s);
         default: return cudaErrorInvalidValue;
     }
 }

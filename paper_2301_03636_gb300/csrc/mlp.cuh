@@ -64,9 +64,11 @@ bool launch_config_valid(const LaunchConfig& c);
 
 cudaError_t launch_extract(const ExtractArgs& a, int F, int fmt, cudaStream_t s, int block = 128);
 cudaError_t launch_extract_list(const ExtractArgs& a, int F, int fmt, int num_sms, cudaStream_t s);
+// x_rm (16-bit formats, F % 8 == 0): also the standardised rows row-major
+// ([n][F], the same values as the image) for the training step's weight gradient.
 cudaError_t launch_standardize(const int32_t* feat, const uint8_t* status, int64_t n, int64_t npad, uint8_t* x_img,
                                int nslab, const float* sa, const float* sc, int F, int fmt, cudaStream_t s,
-                               const float* x8_scale = nullptr);
+                               const float* x8_scale = nullptr, uint16_t* x_rm = nullptr);
 cudaError_t launch_fit_standardizer(const int32_t* feat, const uint8_t* status, int64_t n, int F, double* mu,
                                     double* sigma, cudaStream_t s);
 

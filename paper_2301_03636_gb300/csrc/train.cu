@@ -129,11 +129,16 @@ __global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ y, 
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+// One warp: lane l sums part[l], part[l + 32], ... in order, then the lanes
+// are added in a fixed tree.
 __global__ void loss_final_kernel(const float* __restrict__ part, int nb, int64_t n, float* __restrict__ loss,
                                   float* __restrict__ loss_out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        float s = 0.f;
-        for (int i = 0; i < nb; ++i) s += part[i];
+    const int lane = threadIdx.x;
+    float s = 0.f;
+    for (int i = lane; i < nb; i += 32) s += part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
         *loss = s / (float)n;
         if (loss_out) *loss_out = s / (float)n;
     }
@@ -235,8 +240,6 @@ size_t train_layout(const ModelLayout& L, int64_t R, TrainLayout* t) {
     t->dz16[0] = take((size_t)R * wmax * 2);
     t->dz16[1] = take((size_t)R * wmax * 2);
     t->c32 = t->dB;
-    t->lt_ws_bytes = (size_t)32 << 20;
-    t->lt_ws = take(t->lt_ws_bytes);
     t->rows = R;
     t->bytes = o;
     return o;
@@ -353,13 +356,13 @@ cudaError_t launch_adam_update(const ModelLayout& L, uint8_t* P, const float* gr
 }
 
 cudaError_t launch_train_step_ex(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
-                                 const MlpDesc& md, LtContext* lt, int fmt, const int32_t* feat, const float* labels,
-                                 int64_t n, const TrainOptions& o, int64_t step, float* d_loss, cudaStream_t s,
+                                 const MlpDesc& md, int fmt, const int32_t* feat, const float* labels, int64_t n,
+                                 const TrainOptions& o, int64_t step, float* d_loss, cudaStream_t s, int* status_word,
                                  const FusedFwd* ff) {
     float* grad = reinterpret_cast<float*>(TW + T.grad);
     float* loss = reinterpret_cast<float*>(TW + T.loss);
     cudaError_t e = fmt == 0 ? launch_forward_saved(L, T, TW, md, feat, n, nullptr, s)
-                             : launch_forward_saved_tc(L, T, TW, md, lt, fmt, feat, n, nullptr, s, ff);
+                             : launch_forward_saved_tc(L, T, TW, md, fmt, feat, n, nullptr, s, status_word, ff);
     if (e != cudaSuccess) return e;
     e = launch_mse_loss(L, T, TW, labels, n, o.loss == 1 ? nullptr : d_loss, s);
     if (e != cudaSuccess) return e;
@@ -367,7 +370,8 @@ cudaError_t launch_train_step_ex(const ModelLayout& L, const TrainLayout& T, uin
         rmse_scale_kernel<<<grid1(n), 256, 0, s>>>(reinterpret_cast<float*>(TW + T.dA), n, loss, d_loss);
         adv_count_launch(1);
     }
-    e = fmt == 0 ? launch_backward_saved(L, T, TW, md, n, grad, s) : launch_backward_tc(L, T, TW, md, lt, fmt, nullptr, n, grad, s);
+    e = fmt == 0 ? launch_backward_saved(L, T, TW, md, n, grad, s)
+                 : launch_backward_tc(L, T, TW, md, fmt, nullptr, n, grad, s, status_word);
     if (e != cudaSuccess) return e;
     if (o.optimizer == 0) return launch_adam_update(L, P, grad, o.h, step, s);
     rmsprop_kernel<<<grid1(L.n_params), 256, 0, s>>>(reinterpret_cast<float*>(P + L.p_master), grad,

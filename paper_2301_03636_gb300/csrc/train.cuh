@@ -1,6 +1,8 @@
 // Training-mode kernels (train.cu): forward with saved activations, MSE loss
 // on ln runtime, hand-written backward, Adam.
 #pragma once
+#include <cuda.h>   // CUtensorMap (the encoder is reached through the runtime's driver entry point)
+
 #include "mlp.cuh"
 
 namespace adv {
@@ -18,7 +20,6 @@ struct TrainLayout {
     size_t w16[ADV_MAX_LAYERS];       // row-major 16-bit copies of the hidden layers' weights
     size_t dz16[2];                   // dZ ping-pong [R][wmax], 16-bit
     size_t c32;                       // FP32 GEMM output [R][wmax] (aliases dB)
-    size_t lt_ws, lt_ws_bytes;        // cuBLASLt workspace
     int splits;
     int64_t rows;
     size_t bytes;
@@ -70,8 +71,6 @@ struct TrainOptions {
     AdamHyper h;
     float alpha;
 };
-struct LtContext;
-
 // The 16-bit training forward through the fused tensor-core scorer (for
 // models it covers, hidden widths multiples of 8): one launch packs this
 // step's weights (the scorer's swizzled 16-bit images, the padded biases and
@@ -90,22 +89,69 @@ struct FusedFwd {
 // One training step with these options; fmt 0 FP32 SIMT, 1 BF16, 2 FP16.
 // ff (nullable): the fused forward for fmt 1 / 2.
 cudaError_t launch_train_step_ex(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
-                                 const MlpDesc& md, LtContext* lt, int fmt, const int32_t* feat, const float* labels,
-                                 int64_t n, const TrainOptions& o, int64_t step, float* d_loss, cudaStream_t s,
+                                 const MlpDesc& md, int fmt, const int32_t* feat, const float* labels, int64_t n,
+                                 const TrainOptions& o, int64_t step, float* d_loss, cudaStream_t s, int* status_word,
                                  const FusedFwd* ff = nullptr);
 
+// Dense GEMM on the tensor cores (gemm_tc.cu): C[m][n] = sum_k A(m,k) B(n,k),
+// 16-bit operands, FP32 accumulation.  A(m, k) = A[m * lda + k] (a_mn == 0,
+// K-major) or A[k * lda + m] (a_mn == 1, MN-major), likewise B.  C row-major
+// with leading dimension ldc: FP32, or the operands' 16-bit type (c16, round
+// to nearest).  splits > 1 splits K over CTAs: FP32 partials go to part
+// ([splits][M][ldc]) and are added in split order into C.
+struct TcGemm {
+    // TMA tensor maps of A and B (set by launch_gemm_tc when both operands'
+    // row strides are multiples of 16 bytes and their bases 16-byte aligned)
+    CUtensorMap tma_a, tma_b;
+    int use_tma;
+    int box_b;             // B rows per K block in the TMA path (64-multiple <= 256)
+    int stages;            // ring depth of the TMA path (2 .. 4; set by launch_gemm_tc)
+    const uint16_t* A;
+    int64_t lda;
+    int a_mn;
+    const uint16_t* B;
+    int64_t ldb;
+    int b_mn;
+    int64_t M, N, K;
+    void* C;
+    int64_t ldc;
+    int c16;
+    float* part;
+    int splits;
+    int fmt;               // 1 BF16, 0 FP16
+    int* status_word;
+    uint64_t timeout_ns;
+    // Masked form (c16 = 1, splits = 1): C[m][n] = 16-bit(acc) where
+    // mask_h[m][n] > 0, else 0 (ReLU backward; mask_h row stride ldc), and
+    // colpart[m / 128][n] = the sum over the tile's rows of the stored C
+    // (bias-gradient partials, one row per 128-row tile, row stride N).
+    const uint16_t* mask_h;
+    float* colpart;
+};
+cudaError_t launch_gemm_tc(const TcGemm& g, cudaStream_t s);
+
+// ReLU backward through a hidden layer in one persistent kernel (the masked
+// form of TcGemm, specialised): dz[r][j] = 16-bit(sum_k dza[r][k] W[k][j])
+// where h[r][j] > 0, else 0, for r < n, j < fi, k < fo; and the bias-gradient
+// partials colpart[p][j] (p < *parts) whose sum over p in order is
+// sum_r dz[r][j].  W stays in shared memory; 128-row tiles are dealt to the
+// CTAs round robin.  16-bit arrays row-major, 16-byte aligned; fo, fi
+// multiples of 8 and <= 256.  Returns cudaErrorNotSupported (nothing
+// launched) for shapes outside that, or when colpart_cap floats cannot hold
+// the partials.
+cudaError_t launch_dgrad_mask(const uint16_t* dza, int fo, const uint16_t* W, int fi, const uint16_t* h, int64_t n,
+                              uint16_t* dz, float* colpart, int64_t colpart_cap, int* parts, int fmt,
+                              int* status_word, cudaStream_t s);
+
 // 16-bit operands on the tensor cores (train_tc.cu); fmt 1 BF16, 2 FP16.
-struct LtContext;
-LtContext* lt_create();
-void lt_destroy(LtContext* c);
 cudaError_t launch_forward_saved_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
-                                    LtContext* lt, int fmt, const int32_t* feat, int64_t n, float* d_y,
-                                    cudaStream_t s, const FusedFwd* ff = nullptr);
-cudaError_t launch_backward_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
-                               LtContext* lt, int fmt, const float* d_dy, int64_t n, float* d_grad, cudaStream_t s);
+                                    int fmt, const int32_t* feat, int64_t n, float* d_y, cudaStream_t s,
+                                    int* status_word, const FusedFwd* ff = nullptr);
+cudaError_t launch_backward_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md, int fmt,
+                               const float* d_dy, int64_t n, float* d_grad, cudaStream_t s, int* status_word);
 cudaError_t launch_train_step_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
-                                 const MlpDesc& md, LtContext* lt, int fmt, const int32_t* feat, const float* labels,
-                                 int64_t n, const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss,
-                                 cudaStream_t s, const FusedFwd* ff = nullptr);
+                                 const MlpDesc& md, int fmt, const int32_t* feat, const float* labels, int64_t n,
+                                 const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss,
+                                 cudaStream_t s, int* status_word, const FusedFwd* ff = nullptr);
 
 }  // namespace adv

@@ -5,19 +5,18 @@
 //   forward   C_l = H_{l-1} W_l^T (GEMM), H_l = 16-bit(ReLU(C_l + b_l)),
 //             y = H_L w_out + b_out (FP32 dot per row);
 //   backward  dZ_L = 16-bit(dy w_out^T masked by H_L > 0),
-//             dW_l = dZ_l^T H_{l-1}  (GEMM, K = rows, straight into the FP32 gradient),
+//             dW_l = dZ_l^T H_{l-1}  (GEMM, K = rows, split over CTAs, the
+//                                     partial sums added in a fixed order),
 //             db_l = column sums of dZ_l (fixed split order),
 //             dZ_{l-1} = 16-bit(dZ_l W_l masked by H_{l-1} > 0);
 //   Adam on the FP32 master weights, then the derived copies are rebuilt.
-// The three GEMMs per layer are plain dense contractions and run through
-// cuBLASLt (tensor cores, FP32 accumulation, a workspace inside the caller's
-// buffer); every other step is a kernel of this file.  Activations are kept
-// in 16 bits between layers, so the masks use the stored 16-bit values
-// (positive iff the FP32 pre-activation rounded to a positive value).
+// The GEMMs are this library's tcgen05 kernel (gemm_tc.cu), reading the
+// row-major operands in place as K-major or MN-major; every other step is a
+// kernel of this file.  Activations are kept in 16 bits between layers, so
+// the masks use the stored 16-bit values (positive iff the FP32
+// pre-activation rounded to a positive value).
 #include <algorithm>
-#include <new>
-
-#include <cublasLt.h>
+#include <type_traits>
 
 #include "pack.cuh"
 #include "train.cuh"
@@ -223,19 +222,17 @@ __global__ void stdz16_vec_kernel(const int32_t* __restrict__ feat, int n, int F
     }
 }
 
-// dZ = 16-bit(g masked by h > 0) for a block of VEC_ROWS rows, with
-//   MODE 1: g[r][j] = dy[r] w_out[j]          (last hidden layer)
-//   MODE 2: g[r][j] = c[r][j], the dX GEMM's result in the 16-bit type (hidden
-//           layers; rounding before the mask gives the same dZ as after it)
-// plus the block's column sums in row order: part0[block][j] = sum_r dZ[r][j]
-// (the bias gradient), and in MODE 1 part1[block][j] = sum_r dy[r] h[r][j]
+// Last hidden layer, for a block of VEC_ROWS rows: dZ[r][j] = 16-bit(dy[r]
+// w_out[j]) where h[r][j] > 0, else 0; plus the block's column sums in row
+// order: part0[block][j] = sum_r dZ[r][j] (the bias gradient, of the stored
+// 16-bit dZ as the GEMMs read it) and part1[block][j] = sum_r dy[r] h[r][j]
 // (the output-row gradient).
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) dz_colsum16_kernel(const void* __restrict__ c, const float* __restrict__ dy,
-                                                          const float* __restrict__ wo, const T* __restrict__ h,
-                                                          int n, int w, T* __restrict__ dz, float* __restrict__ part0,
-                                                          float* __restrict__ part1) {
-    __shared__ float red0[256 * 8], red1[MODE == 1 ? 256 * 8 : 1];
+template <typename T>
+__global__ void __launch_bounds__(256) dz_last_colsum16_kernel(const float* __restrict__ dy,
+                                                               const float* __restrict__ wo, const T* __restrict__ h,
+                                                               int n, int w, T* __restrict__ dz,
+                                                               float* __restrict__ part0, float* __restrict__ part1) {
+    __shared__ float red0[256 * 8], red1[256 * 8];
     const int w8 = w >> 3;
     const int cg = threadIdx.x % w8;            // column group: columns 8 cg .. 8 cg + 7
     const int rl = threadIdx.x / w8;            // row lane
@@ -243,34 +240,28 @@ __global__ void __launch_bounds__(256) dz_colsum16_kernel(const void* __restrict
     const int r0 = blockIdx.x * VEC_ROWS;
     float s0[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, s1[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float wq[8];
-    if (MODE == 1) load8f(wo + 8 * cg, wq);
+    load8f(wo + 8 * cg, wq);
     for (int r = r0 + rl; r < r0 + VEC_ROWS && r < n; r += lanes) {
         const int v = r * w8 + cg;
-        float hv[8], g[8], o[8];
+        float hv[8], o[8];
         unpack8<T>(reinterpret_cast<const uint4*>(h)[v], hv);
-        if (MODE == 2) {
-            unpack8<T>(reinterpret_cast<const uint4*>(c)[v], g);
-        } else {
-            const float d = dy[r];
+        const float d = dy[r];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) g[i] = d * wq[i];
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) o[i] = hv[i] > 0.f ? g[i] : 0.f;
+        for (int i = 0; i < 8; ++i) o[i] = hv[i] > 0.f ? d * wq[i] : 0.f;
         const uint4 pk = pack8<T>(o);
         reinterpret_cast<uint4*>(dz)[v] = pk;
         float q[8];
-        unpack8<T>(pk, q);   // the bias gradient sums the stored 16-bit dZ, as the GEMMs read it
+        unpack8<T>(pk, q);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             s0[i] += q[i];
-            if (MODE == 1) s1[i] = fmaf(dy[r], hv[i], s1[i]);
+            s1[i] = fmaf(d, hv[i], s1[i]);
         }
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         red0[threadIdx.x * 8 + i] = s0[i];
-        if (MODE == 1) red1[threadIdx.x * 8 + i] = s1[i];
+        red1[threadIdx.x * 8 + i] = s1[i];
     }
     __syncthreads();
     // row lanes of each column summed in lane order
@@ -279,94 +270,14 @@ __global__ void __launch_bounds__(256) dz_colsum16_kernel(const void* __restrict
         float a0 = 0.f, a1 = 0.f;
         for (int l = 0; l < lanes; ++l) {
             a0 += red0[(l * w8 + g) * 8 + i];
-            if (MODE == 1) a1 += red1[(l * w8 + g) * 8 + i];
+            a1 += red1[(l * w8 + g) * 8 + i];
         }
         part0[(size_t)blockIdx.x * w + t] = a0;
-        if (MODE == 1) part1[(size_t)blockIdx.x * w + t] = a1;
+        part1[(size_t)blockIdx.x * w + t] = a1;
     }
 }
 
 }  // namespace
-
-// ---- cuBLASLt ------------------------------------------------------------------
-struct LtContext {
-    cublasLtHandle_t h = nullptr;
-    struct Entry {
-        int key[10];
-        cublasLtMatmulAlgo_t algo;
-        bool used = false;
-    };
-    Entry cache[64];
-};
-
-LtContext* lt_create() {
-    LtContext* c = new (std::nothrow) LtContext();
-    if (!c) return nullptr;
-    if (cublasLtCreate(&c->h) != CUBLAS_STATUS_SUCCESS) {
-        delete c;
-        return nullptr;
-    }
-    return c;
-}
-
-void lt_destroy(LtContext* c) {
-    if (!c) return;
-    if (c->h) cublasLtDestroy(c->h);
-    delete c;
-}
-
-// Column-major D[m x n] (FP32, ld ldd) = op(A) op(B) with 16-bit A (stored
-// ta ? k x m : m x k, ld lda) and B (stored tb ? n x k : k x n, ld ldb).
-// D = op(A) op(B) in FP32 accumulation, D stored as dt (FP32, or the operands'
-// 16-bit type, rounded to nearest).
-static cudaError_t lt_gemm(LtContext* c, bool ta, bool tb, int m, int n, int k, const void* A, int lda, const void* B,
-                           int ldb, void* D, int ldd, cudaDataType_t ab, void* ws, size_t ws_bytes, cudaStream_t s,
-                           cudaDataType_t dt = CUDA_R_32F) {
-    if (!c) return cudaErrorInvalidValue;
-    const int key[10] = {ta, tb, m, n, k, lda, ldb, ldd, (int)ab, (int)dt};
-    cublasLtMatmulDesc_t op = nullptr;
-    cublasLtMatrixLayout_t la = nullptr, lb = nullptr, ld = nullptr;
-    cublasStatus_t st = cublasLtMatmulDescCreate(&op, CUBLAS_COMPUTE_32F, CUDA_R_32F);
-    const cublasOperation_t opa = ta ? CUBLAS_OP_T : CUBLAS_OP_N, opb = tb ? CUBLAS_OP_T : CUBLAS_OP_N;
-    if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSA, &opa, sizeof(opa));
-    if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatmulDescSetAttribute(op, CUBLASLT_MATMUL_DESC_TRANSB, &opb, sizeof(opb));
-    if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatrixLayoutCreate(&la, ab, ta ? k : m, ta ? m : k, lda);
-    if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatrixLayoutCreate(&lb, ab, tb ? n : k, tb ? k : n, ldb);
-    if (st == CUBLAS_STATUS_SUCCESS) st = cublasLtMatrixLayoutCreate(&ld, dt, m, n, ldd);
-    LtContext::Entry* hit = nullptr;
-    for (auto& e : c->cache)
-        if (e.used && std::equal(key, key + 10, e.key)) { hit = &e; break; }
-    if (st == CUBLAS_STATUS_SUCCESS && !hit) {
-        cublasLtMatmulPreference_t pref = nullptr;
-        st = cublasLtMatmulPreferenceCreate(&pref);
-        if (st == CUBLAS_STATUS_SUCCESS)
-            st = cublasLtMatmulPreferenceSetAttribute(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &ws_bytes,
-                                                      sizeof(ws_bytes));
-        cublasLtMatmulHeuristicResult_t res{};
-        int found = 0;
-        if (st == CUBLAS_STATUS_SUCCESS)
-            st = cublasLtMatmulAlgoGetHeuristic(c->h, op, la, lb, ld, ld, pref, 1, &res, &found);
-        if (pref) cublasLtMatmulPreferenceDestroy(pref);
-        if (st == CUBLAS_STATUS_SUCCESS && found > 0) {
-            for (auto& e : c->cache)
-                if (!e.used) { hit = &e; break; }
-            if (!hit) hit = &c->cache[0];   // full: replace the first entry
-            std::copy(key, key + 10, hit->key);
-            hit->algo = res.algo;
-            hit->used = true;
-        } else if (st == CUBLAS_STATUS_SUCCESS) {
-            st = CUBLAS_STATUS_NOT_SUPPORTED;
-        }
-    }
-    const float one = 1.f, zero = 0.f;
-    if (st == CUBLAS_STATUS_SUCCESS)
-        st = cublasLtMatmul(c->h, op, &one, A, la, B, lb, &zero, D, ld, D, ld, &hit->algo, ws, ws_bytes, s);
-    if (ld) cublasLtMatrixLayoutDestroy(ld);
-    if (lb) cublasLtMatrixLayoutDestroy(lb);
-    if (la) cublasLtMatrixLayoutDestroy(la);
-    if (op) cublasLtMatmulDescDestroy(op);
-    return st == CUBLAS_STATUS_SUCCESS ? cudaSuccess : cudaErrorUnknown;
-}
 
 // ---- the 16-bit training step -------------------------------------------------
 namespace {
@@ -377,8 +288,8 @@ struct Tc {
     const TrainLayout& T_;
     uint8_t* TW;
     const MlpDesc& md;
-    LtContext* lt;
-    cudaDataType_t ab;
+    int* status_word;
+    static constexpr int fmt = std::is_same<T, __nv_bfloat16>::value ? 1 : 0;   // instruction-descriptor code
 
     T* x16() const { return reinterpret_cast<T*>(TW + T_.x16); }
     T* h16(int l) const { return reinterpret_cast<T*>(TW + T_.h16[l]); }
@@ -388,7 +299,61 @@ struct Tc {
     float* part() const { return reinterpret_cast<float*>(TW + T_.part); }
     float* y() const { return reinterpret_cast<float*>(TW + T_.act[L.n_layers]); }
     float* dy() const { return reinterpret_cast<float*>(TW + T_.dA); }
-    void* ws() const { return TW + T_.lt_ws; }
+
+    // C[M][N] = sum_k A(m,k) B(n,k) on the tensor cores (see TcGemm)
+    cudaError_t gemm(const T* A, int64_t lda, int a_mn, const T* B, int64_t ldb, int b_mn, int64_t M, int64_t N,
+                     int64_t K, void* C, int64_t ldc, int c16, int splits, cudaStream_t s) const {
+        TcGemm g{};
+        g.A = reinterpret_cast<const uint16_t*>(A);
+        g.lda = lda;
+        g.a_mn = a_mn;
+        g.B = reinterpret_cast<const uint16_t*>(B);
+        g.ldb = ldb;
+        g.b_mn = b_mn;
+        g.M = M;
+        g.N = N;
+        g.K = K;
+        g.C = C;
+        g.ldc = ldc;
+        g.c16 = c16;
+        g.part = part();
+        g.splits = splits;
+        g.fmt = fmt;
+        g.status_word = status_word;
+        g.timeout_ns = 2000000000ull;
+        return launch_gemm_tc(g, s);
+    }
+    // dZ[n][fi] = 16-bit(dZ_above W) masked by h > 0 (ReLU backward), plus the
+    // bias-gradient partials colpart[tile][fi] of the stored dZ, 128-row tiles
+    cudaError_t gemm_mask(const T* dz_above, int fo, const T* W, int fi, const T* h, int64_t n, T* dz, float* colpart,
+                          cudaStream_t s) const {
+        TcGemm g{};
+        g.A = reinterpret_cast<const uint16_t*>(dz_above);
+        g.lda = fo;
+        g.a_mn = 0;
+        g.B = reinterpret_cast<const uint16_t*>(W);
+        g.ldb = fi;
+        g.b_mn = 1;
+        g.M = n;
+        g.N = fi;
+        g.K = fo;
+        g.C = dz;
+        g.ldc = fi;
+        g.c16 = 1;
+        g.splits = 1;
+        g.fmt = fmt;
+        g.status_word = status_word;
+        g.timeout_ns = 2000000000ull;
+        g.mask_h = reinterpret_cast<const uint16_t*>(h);
+        g.colpart = colpart;
+        return launch_gemm_tc(g, s);
+    }
+    // split-K factor of the weight-gradient GEMMs: about 1,024 rows per split, at
+    // most the partial-sum buffer's splits
+    int dw_splits(int64_t n) const {
+        const int64_t sp = (n + 1023) / 1024;
+        return (int)(sp < 1 ? 1 : (sp > T_.splits ? T_.splits : sp));
+    }
     // input of hidden layer l: the standardised features or the previous layer's output
     const T* in16(int l) const { return l == 0 ? x16() : h16(l - 1); }
 
@@ -404,9 +369,8 @@ struct Tc {
         adv_count_launch(L.n_hidden + 1);
         for (int l = 0; l < L.n_hidden; ++l) {
             const int fi = L.widths[l], fo = L.widths[l + 1];
-            // row-major C[n][fo] = In[n][fi] W^T, i.e. column-major C^T = W In^T
-            cudaError_t e = lt_gemm(lt, true, false, fo, (int)n, fi, w16(l), fi, in16(l), fi, c32(), fo, ab, ws(),
-                                    T_.lt_ws_bytes, s);
+            // C[n][fo] = In[n][fi] W[fo][fi]^T: A = In (K-major), B = W (K-major)
+            cudaError_t e = gemm(in16(l), fi, 0, w16(l), fi, 0, n, fo, fi, c32(), fo, 0, 1, s);
             if (e != cudaSuccess) return e;
             if (vec_ok(n, fo))
                 bias_relu16_vec_kernel<T><<<grid_n(n * fo / 8), 256, 0, s>>>(c32(), (int)n, fo, md.b[l], h16(l));
@@ -430,7 +394,8 @@ struct Tc {
             wmax = std::max<int64_t>(wmax, L.widths[l + 1]);
         }
         for (int l = 0; l < L.n_hidden; ++l) vec = vec && vec_ok(n, L.widths[l + 1]);
-        // the fused reductions keep two [blocks][w] partial arrays in the split-sum buffer
+        // the fused reductions keep two [blocks][w] partial arrays in the split-sum buffer (the
+        // masked GEMMs one [n / 128][w] array, no larger)
         vec = vec && 2 * ((n + VEC_ROWS - 1) / VEC_ROWS) * wmax <= (int64_t)T_.splits * lmax;
         if (vec) return backward_vec(n, grad, s);
         const int splits = (int)((n + TC_SPLIT_ROWS - 1) / TC_SPLIT_ROWS);
@@ -447,18 +412,17 @@ struct Tc {
         int cur = 0;
         for (int l = H - 1; l >= 0; --l) {
             const int fi = L.widths[l], fo = L.widths[l + 1];
-            // dW[fo][fi] = dZ^T In: column-major dW^T[fi x fo] = In^T[fi x n] dZ[n x fo]
-            cudaError_t e = lt_gemm(lt, false, true, fi, fo, (int)n, in16(l), fi, dz16(cur), fo,
-                                    grad + L.layer_w_off[l], fi, ab, ws(), T_.lt_ws_bytes, s);
+            // dW[fo][fi] = dZ[n][fo]^T In[n][fi]: A = dZ, B = In, both MN-major (K = the rows)
+            cudaError_t e = gemm(dz16(cur), fo, 1, in16(l), fi, 1, fo, fi, n, grad + L.layer_w_off[l], fi, 0,
+                                 dw_splits(n), s);
             if (e != cudaSuccess) return e;
             dim3 bg((unsigned)((fo + 127) / 128), (unsigned)splits);
             colsum16_kernel<T><<<bg, 128, 0, s>>>(dz16(cur), nullptr, n, fo, part());
             splitsum(part(), splits, fo, grad + L.layer_b_off[l], s);
             adv_count_launch(2);
             if (l == 0) break;
-            // dIn[n][fi] = dZ[n][fo] W[fo][fi]: column-major dIn^T = W^T dZ^T
-            e = lt_gemm(lt, false, false, fi, (int)n, fo, w16(l), fi, dz16(cur), fo, c32(), fi, ab, ws(),
-                        T_.lt_ws_bytes, s);
+            // dIn[n][fi] = dZ[n][fo] W[fo][fi]: A = dZ (K-major), B = W (MN-major)
+            e = gemm(dz16(cur), fo, 0, w16(l), fi, 1, n, fi, fo, c32(), fi, 0, 1, s);
             if (e != cudaSuccess) return e;
             mask16_kernel<T><<<grid_n(n * fi), 256, 0, s>>>(c32(), h16(l - 1), n, fi, dz16(cur ^ 1));
             adv_count_launch(1);
@@ -471,12 +435,13 @@ struct Tc {
     // output-row) gradients per 256-row block.
     cudaError_t backward_vec(int64_t n, float* grad, cudaStream_t s) const {
         const int blocks = (int)((n + VEC_ROWS - 1) / VEC_ROWS);
+        int64_t lmax_ = 0;   // the split-sum buffer holds T_.splits x lmax_ floats
+        for (int l = 0; l < L.n_layers; ++l) lmax_ = std::max<int64_t>(lmax_, (int64_t)L.widths[l] * L.widths[l + 1]);
         const int H = L.n_hidden;
         const int wl = L.widths[H];
         float* p0 = part();
         float* p1 = part() + (size_t)blocks * wl;
-        dz_colsum16_kernel<T, 1><<<blocks, 256, 0, s>>>(nullptr, dy(), md.W[H], h16(H - 1), (int)n, wl, dz16(0), p0,
-                                                        p1);
+        dz_last_colsum16_kernel<T><<<blocks, 256, 0, s>>>(dy(), md.W[H], h16(H - 1), (int)n, wl, dz16(0), p0, p1);
         splitsum(p1, blocks, wl, grad + L.layer_w_off[H], s);
         rowsum_kernel<<<(int)((n + TC_SPLIT_ROWS - 1) / TC_SPLIT_ROWS), 256, 0, s>>>(dy(), n, p1);
         splitsum(p1, (int)((n + TC_SPLIT_ROWS - 1) / TC_SPLIT_ROWS), 1,
@@ -486,18 +451,25 @@ struct Tc {
         int cur = 0;
         for (int l = H - 1; l >= 0; --l) {
             const int fi = L.widths[l], fo = L.widths[l + 1];
-            cudaError_t e = lt_gemm(lt, false, true, fi, fo, (int)n, in16(l), fi, dz16(cur), fo,
-                                    grad + L.layer_w_off[l], fi, ab, ws(), T_.lt_ws_bytes, s);
+            cudaError_t e = gemm(dz16(cur), fo, 1, in16(l), fi, 1, fo, fi, n, grad + L.layer_w_off[l], fi, 0,
+                                 dw_splits(n), s);
             if (e != cudaSuccess) return e;
             if (l == 0) break;
-            // dX in the 16-bit type: the masked dZ is stored in 16 bits anyway
-            e = lt_gemm(lt, false, false, fi, (int)n, fo, w16(l), fi, dz16(cur), fo, c32(), fi, ab, ws(),
-                        T_.lt_ws_bytes, s, ab);
+            // dZ of layer l - 1 = (dZ W) masked by h > 0, rounded to 16 bits in the
+            // GEMM's epilogue, with the bias gradient's per-tile column sums
+            int parts = 0;
+            e = launch_dgrad_mask(reinterpret_cast<const uint16_t*>(dz16(cur)), fo,
+                                  reinterpret_cast<const uint16_t*>(w16(l)), fi,
+                                  reinterpret_cast<const uint16_t*>(h16(l - 1)), n,
+                                  reinterpret_cast<uint16_t*>(dz16(cur ^ 1)), p0, (int64_t)T_.splits * lmax_,
+                                  &parts, fmt, status_word, s);
+            if (e == cudaErrorNotSupported) {   // shapes outside the persistent kernel: the generic GEMM
+                e = gemm_mask(dz16(cur), fo, w16(l), fi, h16(l - 1), n, dz16(cur ^ 1), p0, s);
+                parts = (int)((n + 127) / 128);
+            }
             if (e != cudaSuccess) return e;
-            dz_colsum16_kernel<T, 2><<<blocks, 256, 0, s>>>(c32(), nullptr, nullptr, h16(l - 1), (int)n, fi,
-                                                            dz16(cur ^ 1), p0, nullptr);
-            splitsum(p0, blocks, fi, grad + L.layer_b_off[l - 1], s);
-            adv_count_launch(2);
+            splitsum(p0, parts, fi, grad + L.layer_b_off[l - 1], s);
+            adv_count_launch(1);
             cur ^= 1;
         }
         return cudaGetLastError();
@@ -600,14 +572,18 @@ static cudaError_t forward_fused(const ModelLayout& L, const TrainLayout& Tl, ui
     const int64_t total = at + p.w_out_pad_n;
     pack_train_kernel<T><<<grid_n(total), 256, 0, s>>>(p);
     T* x16 = reinterpret_cast<T*>(TW + Tl.x16);
-    if (vec_ok(n, L.F) && L.F % 8 == 0)
-        stdz16_vec_kernel<T><<<grid_n(n * L.F / 8), 256, 0, s>>>(feat, (int)n, L.F, md.sa, md.sc, x16);
-    else
-        stdz16_kernel<T><<<grid_n(n * L.F), 256, 0, s>>>(feat, n, L.F, md.sa, md.sc, x16);
-    adv_count_launch(2);
+    adv_count_launch(1);
     const int64_t npad_rows = ((n + ADV_TILE_M - 1) / ADV_TILE_M) * ADV_TILE_M;
+    // the scorer's input image and, when F allows 16-byte rows, the row-major
+    // copy that the first layer's weight gradient reads, in one pass
+    const bool rm_fused = L.F % 8 == 0 && (Tl.x16 % 16) == 0;
+    if (!rm_fused) {
+        stdz16_kernel<T><<<grid_n(n * L.F), 256, 0, s>>>(feat, n, L.F, md.sa, md.sc, x16);
+        adv_count_launch(1);
+    }
     cudaError_t e = launch_standardize(feat, nullptr, n, npad_rows, ff.x_img, L.nslab[0], md.sa, md.sc, L.F,
-                                       fmt == 1 ? 1 : 2, s);
+                                       fmt == 1 ? 1 : 2, s, nullptr,
+                                       rm_fused ? reinterpret_cast<uint16_t*>(x16) : nullptr);
     if (e != cudaSuccess) return e;
     TcArgs a = ff.tc;
     a.x_img = ff.x_img;
@@ -634,38 +610,38 @@ static bool fused_forward_ok(const ModelLayout& L) {
 }
 
 cudaError_t launch_forward_saved_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
-                                    LtContext* lt, int fmt, const int32_t* feat, int64_t n, float* d_y,
-                                    cudaStream_t s, const FusedFwd* ff) {
+                                    int fmt, const int32_t* feat, int64_t n, float* d_y, cudaStream_t s,
+                                    int* status_word, const FusedFwd* ff) {
     cudaError_t e;
     if (ff && fused_forward_ok(L))
         e = fmt == 1 ? forward_fused<__nv_bfloat16>(L, T, TW, md, fmt, feat, n, *ff, s)
                      : forward_fused<__half>(L, T, TW, md, fmt, feat, n, *ff, s);
-    else if (fmt == 1) e = Tc<__nv_bfloat16>{L, T, TW, md, lt, CUDA_R_16BF}.forward(feat, n, s);
-    else e = Tc<__half>{L, T, TW, md, lt, CUDA_R_16F}.forward(feat, n, s);
+    else if (fmt == 1) e = Tc<__nv_bfloat16>{L, T, TW, md, status_word}.forward(feat, n, s);
+    else e = Tc<__half>{L, T, TW, md, status_word}.forward(feat, n, s);
     if (e != cudaSuccess || !d_y) return e;
     return launch_copy_f32(reinterpret_cast<const float*>(TW + T.act[L.n_layers]), d_y, n, s);
 }
 
-cudaError_t launch_backward_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
-                               LtContext* lt, int fmt, const float* d_dy, int64_t n, float* d_grad, cudaStream_t s) {
+cudaError_t launch_backward_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md, int fmt,
+                               const float* d_dy, int64_t n, float* d_grad, cudaStream_t s, int* status_word) {
     if (d_dy) {
         cudaError_t e = launch_copy_f32(d_dy, reinterpret_cast<float*>(TW + T.dA), n, s);
         if (e != cudaSuccess) return e;
     }
-    if (fmt == 1) return Tc<__nv_bfloat16>{L, T, TW, md, lt, CUDA_R_16BF}.backward(n, d_grad, s);
-    return Tc<__half>{L, T, TW, md, lt, CUDA_R_16F}.backward(n, d_grad, s);
+    if (fmt == 1) return Tc<__nv_bfloat16>{L, T, TW, md, status_word}.backward(n, d_grad, s);
+    return Tc<__half>{L, T, TW, md, status_word}.backward(n, d_grad, s);
 }
 
 cudaError_t launch_train_step_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
-                                 const MlpDesc& md, LtContext* lt, int fmt, const int32_t* feat, const float* labels,
-                                 int64_t n, const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss,
-                                 cudaStream_t s, const FusedFwd* ff) {
+                                 const MlpDesc& md, int fmt, const int32_t* feat, const float* labels, int64_t n,
+                                 const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss,
+                                 cudaStream_t s, int* status_word, const FusedFwd* ff) {
     float* grad = d_grad_out ? d_grad_out : reinterpret_cast<float*>(TW + T.grad);
-    cudaError_t e = launch_forward_saved_tc(L, T, TW, md, lt, fmt, feat, n, nullptr, s, ff);
+    cudaError_t e = launch_forward_saved_tc(L, T, TW, md, fmt, feat, n, nullptr, s, status_word, ff);
     if (e != cudaSuccess) return e;
     e = launch_mse_loss(L, T, TW, labels, n, d_loss, s);
     if (e != cudaSuccess) return e;
-    e = launch_backward_tc(L, T, TW, md, lt, fmt, nullptr, n, grad, s);
+    e = launch_backward_tc(L, T, TW, md, fmt, nullptr, n, grad, s, status_word);
     if (e != cudaSuccess || !adam) return e;
     return launch_adam_update(L, P, grad, *adam, step, s);
 }

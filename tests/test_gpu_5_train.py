@@ -209,3 +209,30 @@ def test_scoring_after_training_uses_the_updated_weights(gpu_lib):
     torch.cuda.synchronize()
     ref.set_params(m.get_params().cpu().numpy(), mu, sg)
     assert torch.equal(plan.scores, ref.score(f, st, "bf16"))
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_tensor_core_gradient_ragged_shapes(gpu_lib, precision):
+    """The hand-written tensor-core GEMMs of the 16-bit step on ragged shapes:
+    widths that are not multiples of 8 (rows not 16-byte aligned, the
+    element-wise loader path and padded MMA widths) and 3,001 rows (a partial
+    128-row tile, a partial 64-row K block and a short last K split of the
+    weight-gradient GEMM).  Gradient against the FP64 oracle."""
+    widths = (33, 66, 132, 40, 1)
+    n = 3001
+    d = W.make_descriptors(n, 77)
+    f, st = oracle.extract_features(d, widths[0])
+    t = W.make_labels(d, 77)
+    mu, sg = oracle.fit_standardizer(f, st)
+    p = W.make_weights(widths, 78, "glorot", 0.05)
+    loss_ref, g_ref = oracle.loss_grad(f, t, widths, p, mu, sg)
+    m = advisor.Model(widths, max_rows=n, max_kernels=1)
+    m.set_params(p, mu, sg)
+    loss, g = m.loss_grad(torch.from_numpy(f).cuda(), torch.from_numpy(t).cuda(), precision)
+    g = g.cpu().numpy().astype(np.float64)
+    rel = _split_rel(g, g_ref, widths)
+    cos = float(g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref)))
+    print(precision, "ragged: per-tensor rel-L2", np.array2string(rel, precision=4), "cos", cos)
+    assert abs(float(loss.item()) - loss_ref) <= 1e-2 * abs(loss_ref)
+    assert rel.max() < 2e-2 and cos > 0.999
+    assert m.device_status() == 0
