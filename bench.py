@@ -367,7 +367,8 @@ def training_leg(dev, steps=20):
         ach = flop / (ms / 1000.0) / 1e12
         out[p] = {"ms_per_step": ms, "steps_per_s": 1000.0 / ms, "tflops": ach, "frac_of_peak": ach / tf,
                   "peak_source": src + " dense bf16", "loss_after": float(loss.item()),
-                  "gemms": p.upper() + " tensor cores (cuBLASLt), FP32 accumulation"}
+                  "gemms": p.upper() + " tensor cores, hand-written tcgen05 kernels (fused forward scorer, "
+                           "TMA-fed weight-gradient GEMMs, persistent ReLU-backward GEMM), FP32 accumulation"}
     return out
 
 

@@ -635,15 +635,16 @@ __global__ void gemm_split_sum_kernel(const float* __restrict__ part, int splits
 // Warp 0 lane 0 loads W once (KB x NA MN-major atoms: K block kb of fo, 64
 // columns a of fi) and streams the 128-row K-major blocks of dza through a
 // DG_SA-deep ring; warp 1 lane 0 issues the MMAs into one of two TMEM
-// accumulators (tile i into buffer i % 2); warps 2..5 drain them, one TMEM
-// lane quadrant q = warp % 4 (rows 32 q .. 32 q + 31 of the tile) each.  A
-// drain warp keeps its 32 rows of h in shared memory as NA TMA boxes {64, 32}
-// (128-byte swizzle), overwrites them in place with dz and stores each box
-// back with TMA, then loads the next tile's h into the box as soon as the
-// store has read it.  Column sums of the stored dz accumulate in registers
+// accumulators (tile i into buffer i % 2); warps 2..9 drain them: TMEM lane
+// quadrant q = warp % 4 (rows 32 q .. 32 q + 31 of the tile), and of the
+// 64-column boxes a of those rows the even ones (warps 2..5) or the odd ones
+// (warps 6..9).  Rows 32 q .. 32 q + 31 of h sit in shared memory as NA TMA
+// boxes {64, 32} (128-byte swizzle); a drain warp overwrites its boxes in
+// place with dz and stores each back with TMA, then loads the next tile's h
+// into the box as soon as the store has read it.  Column sums of the stored dz accumulate in registers
 // over the CTA's tiles: lane 2u holds column 8 b4 + 4 b3 + 2 b2 + b1 of each
 // 16-column chunk (b_i the bits of 2u).
-constexpr int DG_THREADS = 192;
+constexpr int DG_THREADS = 320;
 constexpr int DG_SA = 2;                  // ring depth of the dza blocks (16 KB each)
 
 struct DgradArgs {
@@ -682,7 +683,7 @@ __global__ void __launch_bounds__(DG_THREADS, 1) dgrad_mask_kernel(const __grid_
     uint64_t* a_full = bars + 1;                             // [DG_SA] a dza block has landed
     uint64_t* a_empty = a_full + DG_SA;                      // [DG_SA] its MMAs are done
     uint64_t* acc_full = a_empty + DG_SA;                    // [2] an accumulator holds a finished tile
-    uint64_t* acc_empty = acc_full + 2;                      // [2] the four drain warps have read it
+    uint64_t* acc_empty = acc_full + 2;                      // [2] the eight drain warps have read it
     uint64_t* h_full = acc_empty + 2;                        // [4 x 4] box a of quadrant q has landed
     uint64_t* fin = h_full + 16;                             // every MMA issued has completed
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(fin + 1);
@@ -700,7 +701,7 @@ __global__ void __launch_bounds__(DG_THREADS, 1) dgrad_mask_kernel(const __grid_
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4);
+            mbar_init(&acc_empty[b], 8);
         }
         for (int i = 0; i < 16; ++i) mbar_init(&h_full[i], 1);
         mbar_init(fin, 1);
@@ -784,22 +785,22 @@ __global__ void __launch_bounds__(DG_THREADS, 1) dgrad_mask_kernel(const __grid_
         __syncwarp();
     } else {
         // ---- drain warps
-        const int q = warp & 3;
+        const int q = warp & 3, half = (warp - 2) >> 2;   // TMEM quadrant; even or odd boxes
         uint8_t* hq = h_s + (size_t)q * NA * 4096;
         uint64_t* hf = h_full + 4 * q;
         const int colid = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
         uint32_t pend = 0, par = 0;   // boxes with a load in flight, and the parity it completes
-        if (lane == 0 && my_tiles > 0) {
-            const int32_t r0 = (int32_t)(blockIdx.x * 128 + 32 * q);
-            for (int a = 0; a < NA; ++a) {
-                mbar_expect_tx(&hf[a], 4096u);
-                tma_load_2d(hq + (size_t)a * 4096, &g.tm_h, 64 * a, r0, &hf[a]);
-                pend |= 1u << a;
-            }
-        }
-        float csum[16];
+        auto load_h = [&](int a, int32_t row, int tile_i) {
+            mbar_expect_tx(&hf[a], 4096u);
+            tma_load_2d(hq + (size_t)a * 4096, &g.tm_h, 64 * a, row, &hf[a]);
+            pend |= 1u << a;
+            par = (par & ~(1u << a)) | ((uint32_t)(tile_i & 1) << a);
+        };
+        if (lane == 0 && my_tiles > 0)
+            for (int a = half; a < NA; a += 2) load_h(a, (int32_t)(blockIdx.x * 128 + 32 * q), 0);
+        float csum[8];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) csum[e] = 0.f;
+        for (int e = 0; e < 8; ++e) csum[e] = 0.f;
         bool ok = true;
         for (int i = 0; i < my_tiles && ok; ++i) {
             const int64_t t = blockIdx.x + (int64_t)i * gridDim.x;
@@ -812,8 +813,10 @@ __global__ void __launch_bounds__(DG_THREADS, 1) dgrad_mask_kernel(const __grid_
             if (!ok) break;
             tc_fence_after();
             const uint32_t tl = tmem + (uint32_t)b * acc_cols + ((uint32_t)(32 * q) << 16);
+            int prev = -1;   // the box stored before this one
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
+            for (int ai = 0; ai < 2; ++ai) {
+                const int a = 2 * ai + half;
                 if (a >= NA) break;
                 ok = __all_sync(0xffffffffu,
                                 mbar_wait_bounded(&hf[a], (uint32_t)i & 1u, g.status_word, abort_flag, lim));
@@ -848,50 +851,45 @@ __global__ void __launch_bounds__(DG_THREADS, 1) dgrad_mask_kernel(const __grid_
                     }
                     *p0 = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     *p1 = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                    csum[4 * a + c] += warp_colsum16(qv, lane);
+                    csum[4 * ai + c] += warp_colsum16(qv, lane);
                 }
                 fence_proxy_async_smem();   // the writes above, before the TMA store reads them
                 __syncwarp();
                 if (lane == 0) {
                     if (r0 < g.n) tma_store_2d(&g.tm_dz, hq + (size_t)a * 4096, 64 * a, r0);   // rows past n are clipped
                     bulk_commit();
-                    if (a >= 1 && more) {   // box a - 1 has been stored: load the next tile's h into it
+                    if (prev >= 0 && more) {   // the previous box has been stored: the next tile's h into it
                         bulk_wait_read<1>();
-                        mbar_expect_tx(&hf[a - 1], 4096u);
-                        tma_load_2d(hq + (size_t)(a - 1) * 4096, &g.tm_h, 64 * (a - 1), r0_next, &hf[a - 1]);
-                        pend |= 1u << (a - 1);
-                        par = (par & ~(1u << (a - 1))) | ((uint32_t)((i + 1) & 1) << (a - 1));
+                        load_h(prev, r0_next, i + 1);
                     }
                 }
+                prev = a;
             }
             if (!ok) break;
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&acc_empty[b]);
-                if (more) {
+                if (prev >= 0 && more) {
                     bulk_wait_read<0>();
-                    mbar_expect_tx(&hf[NA - 1], 4096u);
-                    tma_load_2d(hq + (size_t)(NA - 1) * 4096, &g.tm_h, 64 * (NA - 1), r0_next, &hf[NA - 1]);
-                    pend |= 1u << (NA - 1);
-                    par = (par & ~(1u << (NA - 1))) | ((uint32_t)((i + 1) & 1) << (NA - 1));
+                    load_h(prev, r0_next, i + 1);
                 }
             }
         }
         if (lane == 0) {
             bulk_wait_all();   // the dz stores are complete
-            for (int a = 0; a < NA; ++a)   // loads still in flight land (only after an abort)
+            for (int a = half; a < NA; a += 2)   // loads still in flight land (only after an abort)
                 if ((pend >> a) & 1u)
                     if (!mbar_wait_drain(&hf[a], (par >> a) & 1u, lim)) atomicOr(g.status_word, ADV_DEV_TIMEOUT);
         }
         if (ok) {
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int ai = 0; ai < 2; ++ai)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const int col = 64 * a + 16 * c + colid;
+                    const int a = 2 * ai + half, col = 64 * a + 16 * c + colid;
                     if ((lane & 1) == 0 && a < NA && col < g.fi)
-                        g.colpart[((size_t)blockIdx.x * 4 + q) * g.fi + col] = csum[4 * a + c];
+                        g.colpart[((size_t)blockIdx.x * 4 + q) * g.fi + col] = csum[4 * ai + c];
                 }
         }
     }

@@ -137,25 +137,34 @@ __global__ void rowsum_kernel(const float* __restrict__ v, int64_t n, float* __r
 // out[j] = sum over s of part[s][j]: eight interleaved split sequences per
 // column (s = y, y + 8, ...) summed in split order, then combined in y order.
 // Block (32, 8), one block per 32 columns.
-__global__ void __launch_bounds__(256) splitsum16_kernel(const float* __restrict__ part, int splits, int w,
-                                                         float* __restrict__ out) {
-    __shared__ float red[8][33];
+__global__ void __launch_bounds__(1024) splitsum16_kernel(const float* __restrict__ part, int splits, int w,
+                                                          float* __restrict__ out) {
+    // 32 columns x 32 split lanes: lane y sums splits y, y + 32, ... in order,
+    // then the lanes are added in order
+    __shared__ float red[32][33];
     const int j = blockIdx.x * 32 + threadIdx.x;
     float s = 0.f;
-    if (j < w)
-        for (int i = threadIdx.y; i < splits; i += 8) s += part[(size_t)i * w + j];
+    if (j < w) {
+        int i = threadIdx.y;
+        for (; i + 96 < splits; i += 128) {
+            const float a0 = part[(size_t)i * w + j], a1 = part[(size_t)(i + 32) * w + j];
+            const float a2 = part[(size_t)(i + 64) * w + j], a3 = part[(size_t)(i + 96) * w + j];
+            s = (((s + a0) + a1) + a2) + a3;
+        }
+        for (; i < splits; i += 32) s += part[(size_t)i * w + j];
+    }
     red[threadIdx.y][threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.y == 0 && j < w) {
         float t = 0.f;
-#pragma unroll
-        for (int y = 0; y < 8; ++y) t += red[y][threadIdx.x];
+#pragma unroll 8
+        for (int y = 0; y < 32; ++y) t += red[y][threadIdx.x];
         out[j] = t;
     }
 }
 
 void splitsum(const float* part, int splits, int w, float* out, cudaStream_t s) {
-    splitsum16_kernel<<<(w + 31) / 32, dim3(32, 8), 0, s>>>(part, splits, w, out);
+    splitsum16_kernel<<<(w + 31) / 32, dim3(32, 32), 0, s>>>(part, splits, w, out);
 }
 
 // ---- vectorised forms: 8 consecutive columns (16 bytes of 16-bit values) per

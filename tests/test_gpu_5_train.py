@@ -211,14 +211,17 @@ def test_scoring_after_training_uses_the_updated_weights(gpu_lib):
     assert torch.equal(plan.scores, ref.score(f, st, "bf16"))
 
 
+@pytest.mark.parametrize("widths", [(33, 66, 132, 40, 1), (64, 128, 32, 64, 1)])
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
-def test_tensor_core_gradient_ragged_shapes(gpu_lib, precision):
-    """The hand-written tensor-core GEMMs of the 16-bit step on ragged shapes:
+def test_tensor_core_gradient_ragged_shapes(gpu_lib, precision, widths):
+    """The hand-written tensor-core GEMMs of the 16-bit step on ragged shapes
+    and 3,001 rows (a partial 128-row tile, a partial 64-row K block and a
+    short last K split of the weight-gradient GEMM).  (33, 66, 132, 40):
     widths that are not multiples of 8 (rows not 16-byte aligned, the
-    element-wise loader path and padded MMA widths) and 3,001 rows (a partial
-    128-row tile, a partial 64-row K block and a short last K split of the
-    weight-gradient GEMM).  Gradient against the FP64 oracle."""
-    widths = (33, 66, 132, 40, 1)
+    element-wise loader path and padded MMA widths).  (64, 128, 32, 64):
+    16-byte rows, so the ReLU backward runs in the persistent kernel, with a
+    32-column layer (half a 64-column box, a partial K block of 32).
+    Gradient against the FP64 oracle."""
     n = 3001
     d = W.make_descriptors(n, 77)
     f, st = oracle.extract_features(d, widths[0])
