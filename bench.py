@@ -562,8 +562,11 @@ def large_sweep_leg(dev, reps=5, rows=0, fp8_ratio=None):
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
-    out["fp32"] = {"ms": ms, "variants_per_s": n / (ms / 1000.0), "tflops": n * flop_row / (ms / 1000.0) / 1e12,
-                   **err_stats(y[:sample], y64)}
+    fma = advisor.advisor_measure_fp32_fma_peak()
+    ach = n * flop_row / (ms / 1000.0) / 1e12
+    out["fp32"] = {"kernel": "adv::mlp_fp32_w16_kernel", "ms": ms, "variants_per_s": n / (ms / 1000.0),
+                   "tflops": ach, "frac_of_fma_peak": ach / fma, "fma_peak": fma,
+                   "peak_source": "measured (advisor_measure_fp32_fma_peak)", **err_stats(y[:sample], y64)}
     eps32 = m.calibrate_eps(fcal, scal, "fp32")
     eps16 = m.calibrate_eps(fcal, scal, "fp16")
     best = torch.empty(K, dtype=torch.int32, device=dev)
@@ -627,7 +630,7 @@ def kernel_rooflines_leg(dev, m, f, st, flush, reps=5):
     n = f.shape[0]
     ms = timed(lambda: m.score(f, st, "fp32"))
     ach = n * FLOP_PER_ROW / (ms / 1000.0) / 1e12
-    out["fp32_scorer"] = {"kernel": "adv::mlp_fp32_kernel", "rows": n, "ms": ms, "bound": "fp32 fma",
+    out["fp32_scorer"] = {"kernel": "adv::mlp_fp32_t64_kernel", "rows": n, "ms": ms, "bound": "fp32 fma",
                           "achieved": ach, "peak": fma, "unit": "TFLOP/s", "frac": ach / fma,
                           "peak_source": "measured (advisor_measure_fp32_fma_peak)"}
 

@@ -329,6 +329,149 @@ __global__ void __launch_bounds__(256, 1) mlp_fp32_t64_kernel(MlpDesc m, RowSrc 
     }
 }
 
+// The plain FP32 scorer for hidden widths up to 1,024 (the column-block loop
+// would carry wider layers in 1,024-column blocks): 16-row tiles, thread t computes rows 8 (t / 128) .. + 7
+// and output neurons cb + 8 (t % 128) .. + 7 of column block cb.  The
+// transposed weights WT[k][j] of the block come into shared memory W16_KC
+// input rows at a time with asynchronous 16-byte copies, double-buffered; per
+// 4 input indices a thread reads its 8 rows' activations (the same for every
+// lane of a warp: broadcasts) and 4 x 8 weights (one contiguous 1 KB row
+// piece per warp) as 16-byte shared loads feeding 256 FMAs.  Each output
+// neuron is summed over the input index in order with FMA, as in the other
+// FP32 scorers (same values).
+constexpr int W16_KC = 8;
+
+template <int F, bool FROM_DESC>
+__global__ void __launch_bounds__(256, 1) mlp_fp32_w16_kernel(MlpDesc m, RowSrc src, float* __restrict__ out, int ws) {
+    constexpr int TM = 16, KC = W16_KC, CW = 1024;
+    extern __shared__ __align__(16) float smem_w[];
+    float* act0 = smem_w;                  // [TM][ws] row-major
+    float* act1 = act0 + TM * ws;
+    float* wst = act1 + TM * ws;           // [2][KC][CW]
+    __shared__ int row_ok[TM];
+    const int tid = threadIdx.x;
+    const int rg = tid >> 7, cq = tid & 127;   // rows 8 rg .. + 7, neurons cb + 8 cq .. + 7
+    const int64_t count = src.count_dev ? (int64_t)*src.count_dev : src.count;
+    const int64_t ntiles = (count + TM - 1) / TM;
+    for (int i = tid; i < 2 * TM * ws; i += 256) act0[i] = 0.f;
+
+    // chunk kc0 of layer l, column block cb, into buffer buf: WT rows kc0 .. kc0 + KC - 1
+    auto stage = [&](int l, int cb, int kc0, int buf) {
+        const int fi = m.widths[l], ld = m.wt_ld[l];
+        const float* wt = m.WT[l];
+        float* dst = wst + buf * KC * CW;
+#pragma unroll
+        for (int q = 0; q < KC * CW / 4 / 256; ++q) {
+            const int piece = tid + 256 * q;           // 16-byte piece
+            const int kk = piece / (CW / 4), n4 = (piece % (CW / 4)) * 4;
+            const bool in = kc0 + kk < fi && cb + n4 < ld;
+            cp_async16(dst + kk * CW + n4, in ? wt + (size_t)(kc0 + kk) * ld + cb + n4 : wt, in ? 16 : 0);
+        }
+        cp_async_commit();
+    };
+
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        __syncthreads();
+        float* in = act0;
+        float* outb = act1;
+        if (tid < TM) {
+            const int64_t pos = tile * TM + tid;
+            int64_t row = -1;
+            if (pos < count) row = src.rows ? src.rows[pos] : pos;
+            int ok = 0;
+            if (row >= 0) {
+                int32_t f[F];
+                ok = fetch_row_features<F, FROM_DESC>(src, row, f) ? 1 : 0;
+#pragma unroll
+                for (int k = 0; k < F; ++k) in[tid * ws + k] = fmaf((float)f[k], __ldg(m.sa + k), -__ldg(m.sc + k));
+            } else {
+#pragma unroll
+                for (int k = 0; k < F; ++k) in[tid * ws + k] = 0.f;
+            }
+            row_ok[tid] = ok;
+        }
+        __syncthreads();
+        for (int l = 0; l + 2 < m.nw; ++l) {
+            const int fi = m.widths[l], fo = m.widths[l + 1];
+            const int nck = (fi + KC - 1) / KC;
+            for (int cb = 0; cb < fo; cb += CW) {
+                float acc[8][8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+                stage(l, cb, 0, 0);
+                for (int c = 0; c < nck; ++c) {
+                    if (c + 1 < nck) {
+                        stage(l, cb, (c + 1) * KC, (c + 1) & 1);
+                        cp_async_wait<1>();
+                    } else {
+                        cp_async_wait<0>();
+                    }
+                    __syncthreads();
+                    const float* w = wst + (c & 1) * KC * CW + 8 * cq;
+                    const float* a = in + (8 * rg) * ws + c * KC;
+#pragma unroll
+                    for (int k4 = 0; k4 < KC; k4 += 4) {
+                        float av[8][4];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float4 t = *reinterpret_cast<const float4*>(a + i * ws + k4);
+                            av[i][0] = t.x; av[i][1] = t.y; av[i][2] = t.z; av[i][3] = t.w;
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const float4 w0 = *reinterpret_cast<const float4*>(w + (k4 + kk) * CW);
+                            const float4 w1 = *reinterpret_cast<const float4*>(w + (k4 + kk) * CW + 4);
+                            const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i][kk], wv[j], acc[i][j]);
+                        }
+                    }
+                    __syncthreads();   // buffer c & 1 is refilled two chunks later
+                }
+                // bias + ReLU; columns past fo are never read by the next layer
+                const int c0 = cb + 8 * cq;
+                if (c0 < fo) {
+                    float bb[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) bb[j] = c0 + j < fo ? __ldg(m.b[l] + c0 + j) : 0.f;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        float* o = outb + (8 * rg + i) * ws + c0;
+                        *reinterpret_cast<float4*>(o) =
+                            make_float4(fmaxf(acc[i][0] + bb[0], 0.f), fmaxf(acc[i][1] + bb[1], 0.f),
+                                        fmaxf(acc[i][2] + bb[2], 0.f), fmaxf(acc[i][3] + bb[3], 0.f));
+                        *reinterpret_cast<float4*>(o + 4) =
+                            make_float4(fmaxf(acc[i][4] + bb[4], 0.f), fmaxf(acc[i][5] + bb[5], 0.f),
+                                        fmaxf(acc[i][6] + bb[6], 0.f), fmaxf(acc[i][7] + bb[7], 0.f));
+                    }
+                }
+            }
+            __syncthreads();
+            float* t = in; in = outb; outb = t;
+        }
+        {
+            const int L = m.nw - 2;
+            const int fi = m.widths[L];
+            const float* __restrict__ wl = m.W[L];
+            const int warp = tid >> 5, lane = tid & 31;
+            for (int r = warp; r < TM; r += 8) {
+                float s = 0.f;
+                for (int k = lane; k < fi; k += 32) s = fmaf(in[r * ws + k], __ldg(wl + k), s);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) {
+                    const int64_t pos = tile * TM + r;
+                    if (pos < count) out[pos] = row_ok[r] ? s + __ldg(m.b[L]) : INFINITY;
+                }
+            }
+        }
+    }
+}
+
 // FP32 scorer for short row lists (the near-tie re-score).  A block takes
 // LIST_RB = 16 rows as two groups of 8 (threads 0-127 and 128-255); each
 // thread computes two adjacent output neurons of its group (JP pairs, 256
@@ -574,6 +717,29 @@ static cudaError_t launch_fp32_t64_f(const MlpDesc& m, const RowSrc& src, float*
     }
 }
 
+template <int F, bool FD>
+static cudaError_t launch_fp32_w16(const MlpDesc& m, const RowSrc& src, float* out, int grid, cudaStream_t s) {
+    const int ws = act_stride(m);
+    const size_t smem = (size_t)(2 * 16 * ws + 2 * W16_KC * 1024) * sizeof(float);
+    auto k = mlp_fp32_w16_kernel<F, FD>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, 256, smem, s>>>(m, src, out, ws);
+    adv_count_launch(1);
+    return cudaGetLastError();
+}
+
+template <bool FD>
+static cudaError_t launch_fp32_w16_f(const MlpDesc& m, const RowSrc& src, float* out, int grid, cudaStream_t s) {
+    switch (m.widths[0]) {
+        case 32: return launch_fp32_w16<32, FD>(m, src, out, grid, s);
+        case 33: return launch_fp32_w16<33, FD>(m, src, out, grid, s);
+        case 64: return launch_fp32_w16<64, FD>(m, src, out, grid, s);
+        case 128: return launch_fp32_w16<128, FD>(m, src, out, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int TM, int RPT, bool FD>
 static cudaError_t launch_fp32_f(const MlpDesc& m, const RowSrc& src, float* out, int grid, cudaStream_t s) {
     switch (m.widths[0]) {
@@ -640,6 +806,13 @@ cudaError_t launch_mlp_fp32(const MlpDesc& m, const RowSrc& src, float* out, int
     }
     if (for_list && status_word)
         return launch_fp32_list(m, src, out, num_sms, status_word, list_blocks_per_sm, list_chunk_kb, s);
+    // wider models: 16-row tiles in 1,024-column blocks while the activations fit
+    // (two 16-row buffers and the weight ring in 227 KB of shared memory)
+    if (!for_list && (size_t)(2 * 16 * act_stride(m) + 2 * W16_KC * 1024) * sizeof(float) <= 227 * 1024) {
+        const int64_t tiles = (src.count + 15) / 16;
+        const int grid = (int)(tiles < 1 ? 1 : tiles);
+        return fd ? launch_fp32_w16_f<true>(m, src, out, grid, s) : launch_fp32_w16_f<false>(m, src, out, grid, s);
+    }
     int grid = num_sms * 2;
     if (!for_list) {
         const int64_t tiles = (src.count + 15) / 16;

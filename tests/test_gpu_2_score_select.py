@@ -13,8 +13,8 @@ from tests._cases import mixed_descriptors
 
 pytestmark = pytest.mark.gpu
 
-# FP32 with FP32 accumulation over <= 256 terms per layer: |y - y64| stays
-# below ~1e-5 relative; the bound below leaves two decades of margin.
+# FP32 with FP32 accumulation over <= 1,024 terms per layer: |y - y64| stays
+# below ~1e-5 relative; the bound below leaves over a decade of margin.
 FP32_ATOL, FP32_RTOL = 2e-4, 2e-4
 
 
@@ -29,7 +29,11 @@ def setup_model(widths, n_rows, n_kernels, seed, bias_scale=0.2, max_depth=3):
 
 
 @pytest.mark.parametrize("widths,n", [((32, 128, 128, 1), 512), ((64, 256, 256, 256, 1), 3001),
-                                      ((128, 96, 200, 1), 777), ((32, 33, 66, 132, 66, 33, 1), 1000)])
+                                      ((128, 96, 200, 1), 777), ((32, 33, 66, 132, 66, 33, 1), 1000),
+                                      # wider than 256 (up to the library's 1,024): the 16-row
+                                      # scorer with a full or a partial 1,024-column block
+                                      ((128, 1024, 1024, 1024, 1), 1000), ((64, 600, 300, 1), 777),
+                                      ((32, 1000, 64, 1), 333)])
 def test_fp32_and_fp64_scores(gpu_lib, widths, n):
     m, p, mu, sg = setup_model(widths, n, 1, 11)
     d = mixed_descriptors(n, 77 + n)
