@@ -400,6 +400,12 @@ advisor_status advisor_model_calibrate_fp8(advisor_model_t m, const int32_t* d_f
     return ADVISOR_OK;
 }
 
+// Internal hooks for plans (plan.cu): which re-score tiers the last selection ran.
+extern "C" int adv_model_last_mid(advisor_model_t m) { return m && m->last_mid ? 1 : 0; }
+extern "C" void adv_model_set_last_mid(advisor_model_t m, int mid) {
+    if (m) m->last_mid = mid != 0;
+}
+
 advisor_status advisor_get_rescore_counts_ex(advisor_model_t m, int64_t* h_counts, cudaStream_t stream) {
     if (!m || !h_counts || !m->WS) return ADVISOR_ERR_INVALID_ARGUMENT;
     int c[4] = {0, 0, 0, 0};

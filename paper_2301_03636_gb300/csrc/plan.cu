@@ -11,7 +11,10 @@
 // the shapes never change the selections (the layer-by-layer path changes
 // the last bits of the 16-bit scores, within their error bound).
 //
-// Only public entry points of the library are used here.
+// Besides the library's public entry points, two internal hooks are used:
+// the launch counter and the model's record of which re-score tiers the
+// last selection ran (where advisor_get_rescore_counts finds each tier's
+// count), which every replay sets to its own plan's.
 #include <algorithm>
 #include <new>
 #include <vector>
@@ -21,6 +24,8 @@
 #include "advisor.h"
 
 extern "C" void adv_count_launch(int n);
+extern "C" int adv_model_last_mid(advisor_model_t m);
+extern "C" void adv_model_set_last_mid(advisor_model_t m, int mid);
 
 struct advisor_plan {
     advisor_model_t model = nullptr;
@@ -29,6 +34,7 @@ struct advisor_plan {
     advisor_launch_config cfg{};
     float replay_us = 0.f;
     int32_t kernels = 0;
+    int mid = 0;   // the captured selection runs the FP16 middle tier
 };
 
 namespace {
@@ -216,6 +222,7 @@ advisor_status make_plan(const RankCall& r, int32_t autotune, cudaStream_t strea
         return st;
     }
     p->model = m;
+    p->mid = adv_model_last_mid(m);   // set by the capture's selection
     p->cfg = best;
     p->replay_us = autotune ? best_us : 0.f;
     *out = p;
@@ -275,6 +282,7 @@ advisor_status advisor_plan_launch(advisor_plan_t p, cudaStream_t stream) {
     const advisor_status st = advisor_model_refresh(p->model, stream);
     if (st != ADVISOR_OK) return st;
     if (cudaGraphLaunch(p->exec, stream) != cudaSuccess) return ADVISOR_ERR_CUDA;
+    adv_model_set_last_mid(p->model, p->mid);
     adv_count_launch(p->kernels);
     return ADVISOR_OK;
 }

@@ -115,10 +115,19 @@ class Server:
         self.executors = executors
         self.clock = clock
         self.finished: list[Query] = []
+        # set by executors that finish batches on threads of their own, so that
+        # the loop sleeps (releasing the interpreter lock) instead of spinning
+        self.wake = threading.Event()
+        for ex in executors:
+            if hasattr(ex, "attach_wake"):
+                ex.attach_wake(self.wake)
 
-    def step(self, now: float):
+    def step(self, now: float) -> bool:
+        """Collect finished batches and launch new ones; whether anything happened."""
+        progressed = False
         for ex in self.executors:
             for batch, best, score in ex.poll():
+                progressed = True
                 t = self.clock() - self.t0
                 for q, b, s in zip(batch, best, score):
                     q.best, q.score, q.done, q.status = int(b), float(s), t, "done"
@@ -131,6 +140,8 @@ class Server:
                 for q in batch:
                     q.admitted, q.status = now, "running"
                 ex.launch(batch)
+                progressed = True
+        return progressed
 
     def run(self, queries: list[Query], cancel_at: dict | None = None, timeout_s: float = 60.0):
         """Open-loop replay: query i becomes visible at its arrival time."""
@@ -148,12 +159,20 @@ class Server:
                 if now >= t:
                     self.batcher.cancel(qid)
                     del cancel_at[qid]
-            self.step(now)
+            progressed = self.step(now)
             settled = len(self.finished) + len(self.batcher.rejected) + len(self.batcher.cancelled)
             if i >= total and settled >= total:
                 break
             if now > timeout_s:
                 raise TimeoutError("serving replay did not finish in time")
+            if not progressed:
+                # nothing to do until the next arrival, a finished batch or a cancellation
+                # (polled executors are checked again after at most 100 us)
+                nxt = pending[i].arrival - now if i < total else 1e-3
+                if cancel_at:
+                    nxt = min(nxt, min(cancel_at.values()) - now)
+                self.wake.wait(timeout=max(0.0, min(nxt, 1e-4)))
+                self.wake.clear()
         return self.finished
 
 
@@ -228,6 +247,7 @@ class ThreadedPipeline:
         self.inbox: queue.Queue = queue.Queue(maxsize=1)
         self.results: collections.deque = collections.deque()
         self.busy = False
+        self.wake: threading.Event | None = None
         self.error: BaseException | None = None
         self.thread = threading.Thread(target=self._work, daemon=True)
         self.thread.start()
@@ -242,6 +262,9 @@ class ThreadedPipeline:
 
     def idle(self) -> bool:
         return not self.busy
+
+    def attach_wake(self, ev: threading.Event):
+        self.wake = ev
 
     def launch(self, batch):
         self.busy = True
@@ -259,6 +282,8 @@ class ThreadedPipeline:
             except BaseException as e:   # handed to the serving loop by poll()
                 self.error = e
                 self.results.append((batch, [-2] * len(batch), [float("nan")] * len(batch)))
+            if self.wake is not None:
+                self.wake.set()
 
     def poll(self):
         if self.error is not None:

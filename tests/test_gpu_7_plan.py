@@ -233,3 +233,32 @@ def test_plan_with_fp16_tier_matches_rank_ex(gpu_lib, setup, staged):
     if not staged:
         d.copy_(torch.from_numpy(setup["d_a"]).cuda())
     assert m.device_status() == 0
+
+
+def test_rescore_counts_follow_the_replayed_plan(gpu_lib, setup):
+    """Two plans of one model, with and without the FP16 tier: the per-tier
+    counts after a replay are the replayed plan's, whichever was captured
+    last."""
+    m = setup["m"]
+    eps, eps16, eps32 = setup["eps"]["bf16"], setup["eps"]["fp16"], setup["eps"]["fp32"]
+    d = torch.from_numpy(setup["d_a"]).cuda()
+    o = torch.from_numpy(setup["off"]).cuda()
+    m.rank(d, o, "bf16", eps, eps32)
+    plain_counts = m.rescore_counts_ex()
+    assert plain_counts[0] == 0 and plain_counts[1] > 0
+    _direct_ex(m, d, o, "bf16", eps, eps16, eps32)
+    tier_counts = m.rescore_counts_ex()
+    plain = m.plan_rank(d, o, "bf16", eps, eps32)
+    tiered = m.plan_rank(d, o, "bf16", eps, eps32, eps16=eps16)   # captured last
+    plain.launch()
+    torch.cuda.synchronize()
+    assert m.rescore_counts_ex() == plain_counts
+    tiered.launch()
+    torch.cuda.synchronize()
+    assert m.rescore_counts_ex() == tier_counts
+    plain.launch()
+    torch.cuda.synchronize()
+    assert m.rescore_counts_ex() == plain_counts
+    plain.close()
+    tiered.close()
+
