@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the precision comparison, serving, training and CPU baseline legs")
+    ap.add_argument("--training-only", action="store_true",
+                    help="run only the training leg and print its JSON (for profiling its kernels)")
     ap.add_argument("--sweep-only", action="store_true",
                     help="run only the large-sweep leg and print its JSON (for profiling its kernels)")
     ap.add_argument("--sweep-rows", type=int, default=0,
@@ -358,10 +360,12 @@ def training_leg(dev, steps=20):
         for _ in range(3):
             m.train_step(f, t, p, loss=loss)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("training_" + p)   # lets ncu capture just these steps
         a.record()
         for _ in range(steps):
             m.train_step(f, t, p, loss=loss)
         b.record()
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / steps
         ach = flop / (ms / 1000.0) / 1e12
@@ -727,6 +731,9 @@ def main():
 
     if args.sweep_only:
         print(json.dumps(large_sweep_leg(dev, rows=args.sweep_rows)), flush=True)
+        return
+    if args.training_only:
+        print(json.dumps(training_leg(dev)), flush=True)
         return
 
     # ---- setup (untimed): workload, model, standardiser, error bounds ----
