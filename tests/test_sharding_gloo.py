@@ -3,6 +3,7 @@ kernels (here with the oracle standing in for the per-GPU ranking) and the
 gathered answers equal the unsharded answer; shards partition the kernels."""
 import os
 import socket
+import sys
 
 import numpy as np
 import torch
@@ -11,6 +12,8 @@ import torch.multiprocessing as mp
 
 from paper_2301_03636_gb300 import sharding
 from paper_2301_03636_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _free_port():
@@ -69,3 +72,21 @@ def test_shards_partition_kernels():
     # balanced by rows within one kernel's size
     sizes = [sharding.shard_segments(off, r, 4)[3] - sharding.shard_segments(off, r, 4)[2] for r in range(4)]
     assert max(sizes) - min(sizes) <= 2 * 64
+
+
+def test_bench_job_is_sharded_by_the_library():
+    """bench.py's multi-GPU job: `world` seeded batches split by
+    sharding.shard_segments; rank r gets batch r whole, and one rank alone gets
+    the single-GPU workload."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2301_03636_gb300 import workloads as W
+    off1 = bench.WL.offsets()
+    n1 = int(off1[-1])
+    off, desc, n_g = bench.global_job_shard(1, 0)
+    assert n_g == n1 and np.array_equal(off, off1)
+    assert np.array_equal(desc, W.make_descriptors(n1, bench.WL.seed))
+    for r in range(3):
+        off, desc, n_g = bench.global_job_shard(3, r)
+        assert n_g == 3 * n1 and np.array_equal(off, off1)
+        assert np.array_equal(desc, W.make_descriptors(n1, bench.WL.seed + 1000 * r))
