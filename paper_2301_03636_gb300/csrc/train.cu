@@ -240,6 +240,14 @@ size_t train_layout(const ModelLayout& L, int64_t R, TrainLayout* t) {
     t->dz16[0] = take((size_t)R * wmax * 2);
     t->dz16[1] = take((size_t)R * wmax * 2);
     t->c32 = t->dB;
+    // partials of the 16-bit backward's column sums: the last hidden layer's
+    // (bias and output row, per 256-row block), the output bias (per 1,024
+    // rows), and per lower hidden layer the ReLU-backward kernel's (four per
+    // CTA of up to 256 CTAs, or one per 128-row tile in the generic form)
+    const int64_t tiles = (R + 127) / 128;
+    t->bias_part_floats = 2 * ((R + 255) / 256) * wmax + (R + 1023) / 1024 +
+                          (int64_t)L.n_hidden * (tiles > 1024 ? tiles : 1024) * wmax;
+    t->bias_part = take((size_t)t->bias_part_floats * 4);
     t->rows = R;
     t->bytes = o;
     return o;

@@ -20,6 +20,8 @@ struct TrainLayout {
     size_t w16[ADV_MAX_LAYERS];       // row-major 16-bit copies of the hidden layers' weights
     size_t dz16[2];                   // dZ ping-pong [R][wmax], 16-bit
     size_t c32;                       // FP32 GEMM output [R][wmax] (aliases dB)
+    size_t bias_part;                 // bias / output-row gradient partials of the 16-bit backward
+    int64_t bias_part_floats;         //   (kept apart from `part`, summed in one launch at its end)
     int splits;
     int64_t rows;
     size_t bytes;

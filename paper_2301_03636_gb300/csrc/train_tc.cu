@@ -163,6 +163,61 @@ __global__ void __launch_bounds__(1024) splitsum16_kernel(const float* __restric
     }
 }
 
+// Several split sums in one launch: job j sums parts[j][i][c] over i < splits[j]
+// into out[j][c] for c < w[j], in the order of splitsum16_kernel.
+constexpr int SS_MAX_JOBS = ADV_MAX_LAYERS + 2;
+struct SplitSumJobs {
+    const float* part[SS_MAX_JOBS];
+    float* out[SS_MAX_JOBS];
+    int splits[SS_MAX_JOBS], w[SS_MAX_JOBS];
+    int first_block[SS_MAX_JOBS + 1];   // blocks of job j: first_block[j] .. first_block[j + 1] - 1
+    int n;
+};
+
+__global__ void __launch_bounds__(1024) splitsum_jobs_kernel(const __grid_constant__ SplitSumJobs jb) {
+    __shared__ float red[32][33];
+    int j = 0;
+    while (j + 1 < jb.n && (int)blockIdx.x >= jb.first_block[j + 1]) ++j;
+    const int w = jb.w[j], splits = jb.splits[j];
+    const float* __restrict__ part = jb.part[j];
+    const int c = ((int)blockIdx.x - jb.first_block[j]) * 32 + threadIdx.x;
+    float s = 0.f;
+    if (c < w) {
+        int i = threadIdx.y;
+        for (; i + 96 < splits; i += 128) {
+            const float a0 = part[(size_t)i * w + c], a1 = part[(size_t)(i + 32) * w + c];
+            const float a2 = part[(size_t)(i + 64) * w + c], a3 = part[(size_t)(i + 96) * w + c];
+            s = (((s + a0) + a1) + a2) + a3;
+        }
+        for (; i < splits; i += 32) s += part[(size_t)i * w + c];
+    }
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < w) {
+        float t = 0.f;
+#pragma unroll 8
+        for (int y = 0; y < 32; ++y) t += red[y][threadIdx.x];
+        jb.out[j][c] = t;
+    }
+}
+
+struct SplitSums {
+    SplitSumJobs jb{};
+    void add(const float* part, int splits, int w, float* out) {
+        jb.part[jb.n] = part;
+        jb.out[jb.n] = out;
+        jb.splits[jb.n] = splits;
+        jb.w[jb.n] = w;
+        jb.first_block[jb.n + 1] = jb.first_block[jb.n] + (w + 31) / 32;
+        ++jb.n;
+    }
+    void launch(cudaStream_t s) const {
+        if (jb.n == 0) return;
+        splitsum_jobs_kernel<<<jb.first_block[jb.n], dim3(32, 32), 0, s>>>(jb);
+        adv_count_launch(1);
+    }
+};
+
 void splitsum(const float* part, int splits, int w, float* out, cudaStream_t s) {
     splitsum16_kernel<<<(w + 31) / 32, dim3(32, 32), 0, s>>>(part, splits, w, out);
 }
@@ -306,6 +361,7 @@ struct Tc {
     T* dz16(int i) const { return reinterpret_cast<T*>(TW + T_.dz16[i]); }
     float* c32() const { return reinterpret_cast<float*>(TW + T_.c32); }
     float* part() const { return reinterpret_cast<float*>(TW + T_.part); }
+    float* bias_part() const { return reinterpret_cast<float*>(TW + T_.bias_part); }
     float* y() const { return reinterpret_cast<float*>(TW + T_.act[L.n_layers]); }
     float* dy() const { return reinterpret_cast<float*>(TW + T_.dA); }
 
@@ -397,15 +453,9 @@ struct Tc {
     // dL/dy in dy(); gradient (master layout) into grad
     cudaError_t backward(int64_t n, float* grad, cudaStream_t s) const {
         bool vec = true;
-        int64_t lmax = 0, wmax = 0;
-        for (int l = 0; l < L.n_layers; ++l) {
-            lmax = std::max<int64_t>(lmax, (int64_t)L.widths[l] * L.widths[l + 1]);
-            wmax = std::max<int64_t>(wmax, L.widths[l + 1]);
-        }
         for (int l = 0; l < L.n_hidden; ++l) vec = vec && vec_ok(n, L.widths[l + 1]);
-        // the fused reductions keep two [blocks][w] partial arrays in the split-sum buffer (the
-        // masked GEMMs one [n / 128][w] array, no larger)
-        vec = vec && 2 * ((n + VEC_ROWS - 1) / VEC_ROWS) * wmax <= (int64_t)T_.splits * lmax;
+        // the fused reductions' partials fit the bias-partial region (sized for the workspace's rows)
+        vec = vec && n <= T_.rows;
         if (vec) return backward_vec(n, grad, s);
         const int splits = (int)((n + TC_SPLIT_ROWS - 1) / TC_SPLIT_ROWS);
         const int H = L.n_hidden;
@@ -444,19 +494,24 @@ struct Tc {
     // output-row) gradients per 256-row block.
     cudaError_t backward_vec(int64_t n, float* grad, cudaStream_t s) const {
         const int blocks = (int)((n + VEC_ROWS - 1) / VEC_ROWS);
-        int64_t lmax_ = 0;   // the split-sum buffer holds T_.splits x lmax_ floats
-        for (int l = 0; l < L.n_layers; ++l) lmax_ = std::max<int64_t>(lmax_, (int64_t)L.widths[l] * L.widths[l + 1]);
+        const int nsplit = (int)((n + TC_SPLIT_ROWS - 1) / TC_SPLIT_ROWS);
         const int H = L.n_hidden;
         const int wl = L.widths[H];
-        float* p0 = part();
-        float* p1 = part() + (size_t)blocks * wl;
+        // the column-sum partials live in their own region and are summed in one
+        // launch at the end: the last hidden layer's (bias p0, output row p1), the
+        // output bias's (p2), then one array per lower hidden layer
+        float* p0 = bias_part();
+        float* p1 = p0 + (size_t)blocks * wl;
+        float* p2 = p1 + (size_t)blocks * wl;
+        float* pl = p2 + nsplit;
+        const int64_t per_layer_rows = std::max<int64_t>((n + 127) / 128, 1024);
+        SplitSums sums;
         dz_last_colsum16_kernel<T><<<blocks, 256, 0, s>>>(dy(), md.W[H], h16(H - 1), (int)n, wl, dz16(0), p0, p1);
-        splitsum(p1, blocks, wl, grad + L.layer_w_off[H], s);
-        rowsum_kernel<<<(int)((n + TC_SPLIT_ROWS - 1) / TC_SPLIT_ROWS), 256, 0, s>>>(dy(), n, p1);
-        splitsum(p1, (int)((n + TC_SPLIT_ROWS - 1) / TC_SPLIT_ROWS), 1,
-                                           grad + L.layer_b_off[H], s);
-        splitsum(p0, blocks, wl, grad + L.layer_b_off[H - 1], s);
-        adv_count_launch(5);
+        rowsum_kernel<<<nsplit, 256, 0, s>>>(dy(), n, p2);
+        adv_count_launch(2);
+        sums.add(p1, blocks, wl, grad + L.layer_w_off[H]);
+        sums.add(p2, nsplit, 1, grad + L.layer_b_off[H]);
+        sums.add(p0, blocks, wl, grad + L.layer_b_off[H - 1]);
         int cur = 0;
         for (int l = H - 1; l >= 0; --l) {
             const int fi = L.widths[l], fo = L.widths[l + 1];
@@ -470,17 +525,18 @@ struct Tc {
             e = launch_dgrad_mask(reinterpret_cast<const uint16_t*>(dz16(cur)), fo,
                                   reinterpret_cast<const uint16_t*>(w16(l)), fi,
                                   reinterpret_cast<const uint16_t*>(h16(l - 1)), n,
-                                  reinterpret_cast<uint16_t*>(dz16(cur ^ 1)), p0, (int64_t)T_.splits * lmax_,
-                                  &parts, fmt, status_word, s);
+                                  reinterpret_cast<uint16_t*>(dz16(cur ^ 1)), pl, per_layer_rows * fi, &parts, fmt,
+                                  status_word, s);
             if (e == cudaErrorNotSupported) {   // shapes outside the persistent kernel: the generic GEMM
-                e = gemm_mask(dz16(cur), fo, w16(l), fi, h16(l - 1), n, dz16(cur ^ 1), p0, s);
+                e = gemm_mask(dz16(cur), fo, w16(l), fi, h16(l - 1), n, dz16(cur ^ 1), pl, s);
                 parts = (int)((n + 127) / 128);
             }
             if (e != cudaSuccess) return e;
-            splitsum(p0, parts, fi, grad + L.layer_b_off[l - 1], s);
-            adv_count_launch(1);
+            sums.add(pl, parts, fi, grad + L.layer_b_off[l - 1]);
+            pl += (size_t)per_layer_rows * fi;
             cur ^= 1;
         }
+        sums.launch(s);
         return cudaGetLastError();
     }
 };
