@@ -1030,7 +1030,10 @@ cudaError_t launch_dgrad_mask(const uint16_t* dza, int fo, const uint16_t* W, in
     a.colpart = colpart;
     a.status_word = status_word;
     a.timeout_ns = 2000000000ull;
-    const size_t smem = dg_smem_bytes(fo, fi);
+    // a CTA holding all 512 TMEM columns gets an SM of its own: a second CTA on
+    // the SM would wait in tcgen05.alloc until the first finished
+    size_t smem = dg_smem_bytes(fo, fi);
+    if (2 * dg_acc_cols(fi) == 512 && smem < 120 * 1024) smem = 120 * 1024;
     auto kern = fmt == 1 ? dgrad_mask_kernel<1> : dgrad_mask_kernel<0>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
