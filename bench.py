@@ -338,6 +338,8 @@ def serving_leg(dev):
         runs.append(st)
     return {"workload": "queries of 4..512 variants, 32-128-128-1, bf16 + re-score",
             "admission": "3 pipelines, row capacity each from its share of a 144 MB device-memory budget",
+            "io": "one advisor_rank call per batch: the kernels read the batch's descriptors and offsets from "
+                  "pinned host memory and write the answers there",
             "runs": runs}
 
 

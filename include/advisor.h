@@ -240,8 +240,12 @@ advisor_status advisor_select_best(advisor_model_t m, const float* d_scores, int
  * cudaHostRegister, accessible from the device through unified addressing):
  * the kernels then read the descriptors over the CPU-GPU link while they
  * compute, instead of the caller copying them first; the host must not
- * change them until the call has completed on `stream`.  Any other pointer
- * the device cannot read (e.g. pageable host memory) returns
+ * change them until the call has completed on `stream`.  d_seg_off,
+ * d_best_local and d_best_score may likewise be page-locked host memory: the
+ * kernels read the offsets and write the answers there directly, and the host
+ * reads the answers once the call has completed on `stream` (a serving batch
+ * then needs no copy around the call).  Any of these pointers that the device
+ * cannot access (e.g. pageable host memory) returns
  * ADVISOR_ERR_INVALID_ARGUMENT. */
 advisor_status advisor_rank(advisor_model_t m, const advisor_variant_desc* d_desc, int64_t n_rows,
                             const int64_t* d_seg_off, int64_t n_kernels,

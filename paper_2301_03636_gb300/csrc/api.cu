@@ -800,6 +800,9 @@ advisor_status rank_checks(advisor_model_t m, const advisor_variant_desc* d_desc
     if (n_kernels == 0) return ADVISOR_OK;
     if (!d_seg_off || (n_rows > 0 && (!d_desc || !aligned(d_desc, 16) || !device_readable(d_desc))))
         return ADVISOR_ERR_INVALID_ARGUMENT;
+    // offsets and answers: device memory or mapped page-locked host memory
+    if (!device_readable(d_seg_off) || !device_readable(d_best_local) || !device_readable(d_best_score))
+        return ADVISOR_ERR_INVALID_ARGUMENT;
     advisor_status st = check_ready(m, n_rows);
     if (st != ADVISOR_OK) return st;
     if (n_kernels > m->max_kernels) return ADVISOR_ERR_OUT_OF_MEMORY;

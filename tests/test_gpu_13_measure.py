@@ -99,16 +99,40 @@ def test_descriptors_in_pinned_host_memory(gpu_lib):
     assert torch.equal(b_plan, b_dev) and torch.equal(s_plan, s_dev)
 
 
-def test_pageable_host_descriptors_rejected(gpu_lib):
-    """A pointer the device cannot read is refused before any launch."""
+@pytest.mark.parametrize("which", ["desc", "offsets", "best", "best_score"])
+def test_pageable_host_pointers_rejected(gpu_lib, which):
+    """A descriptor, offset or answer pointer the device cannot access is
+    refused before any launch."""
     widths = (32, 16, 1)
     m = advisor.Model(widths, max_rows=64, max_kernels=1)
     m.set_params(W.make_weights(widths, 1), np.zeros(32), np.ones(32))
-    d = torch.from_numpy(W.make_descriptors(64, 1))          # ordinary (pageable) host memory
-    o = torch.tensor([0, 64], dtype=torch.int64, device="cuda")
+    args = {"desc": torch.from_numpy(W.make_descriptors(64, 1)).cuda(),
+            "offsets": torch.tensor([0, 64], dtype=torch.int64, device="cuda"),
+            "best": torch.empty(1, dtype=torch.int32, device="cuda"),
+            "best_score": torch.empty(1, dtype=torch.float64, device="cuda")}
+    args[which] = args[which].cpu()                           # ordinary (pageable) host memory
     with pytest.raises(advisor.AdvisorError) as e:
-        m.rank(d, o, "bf16")
+        m.rank(args["desc"], args["offsets"], "bf16", best=args["best"], best_score=args["best_score"])
     assert e.value.code == 1
+
+
+def test_pinned_host_offsets_and_answers(gpu_lib):
+    """Descriptors and offsets read from, and answers written to, page-locked
+    host memory (the serving pipelines' form): the same answers as with
+    device buffers."""
+    widths = (32, 128, 128, 1)
+    off = W.make_segments(100, 4, 64, seed=8)
+    n = int(off[-1])
+    d = W.make_descriptors(n, 8)
+    m = advisor.Model(widths, max_rows=n, max_kernels=100)
+    m.set_params(W.make_weights(widths, 8), np.zeros(32), np.full(32, 8.0))
+    b_dev, s_dev = m.rank(torch.from_numpy(d).cuda(), torch.from_numpy(off).cuda(), "bf16", 0.05, 1e-4)
+    hb = torch.empty(100, dtype=torch.int32).pin_memory()
+    hs = torch.empty(100, dtype=torch.float64).pin_memory()
+    m.rank(torch.from_numpy(d).pin_memory(), torch.from_numpy(off).pin_memory(), "bf16", 0.05, 1e-4,
+           best=hb, best_score=hs)
+    torch.cuda.synchronize()
+    assert torch.equal(hb, b_dev.cpu()) and torch.equal(hs, s_dev.cpu())
 
 
 @pytest.mark.parametrize("n_stages", [1, 3, 8])
