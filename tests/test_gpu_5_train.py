@@ -211,18 +211,23 @@ def test_scoring_after_training_uses_the_updated_weights(gpu_lib):
     assert torch.equal(plan.scores, ref.score(f, st, "bf16"))
 
 
-@pytest.mark.parametrize("widths", [(33, 66, 132, 40, 1), (64, 128, 32, 64, 1)])
+@pytest.mark.parametrize("widths,n", [((33, 66, 132, 40, 1), 3001), ((64, 128, 32, 64, 1), 3001),
+                                      ((64, 128, 32, 64, 1), 100)])
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
-def test_tensor_core_gradient_ragged_shapes(gpu_lib, precision, widths):
+def test_tensor_core_gradient_ragged_shapes(gpu_lib, precision, widths, n):
     """The hand-written tensor-core GEMMs of the 16-bit step on ragged shapes
     and 3,001 rows (a partial 128-row tile, a partial 64-row K block and a
     short last K split of the weight-gradient GEMM).  (33, 66, 132, 40):
     widths that are not multiples of 8 (rows not 16-byte aligned, the
     element-wise loader path and padded MMA widths).  (64, 128, 32, 64):
     16-byte rows, so the ReLU backward runs in the persistent kernel, with a
-    32-column layer (half a 64-column box, a partial K block of 32).
-    Gradient against the FP64 oracle."""
-    n = 3001
+    32-column layer (half a 64-column box, a partial K block of 32); at 100
+    rows, one CTA on a single partial tile and a single partial K split.
+    Gradient against the FP64 oracle.  The gradient averages the rows' 16-bit
+    rounding errors, so its relative error grows as 1/sqrt(n): the bound is
+    2e-2 at 3,001 rows scaled by sqrt(3001 / n) (measured at 100 rows: 3.7e-2
+    BF16, 8.2e-3 FP16, five times the 3,001-row figures); the cosine bound,
+    which any wrong tile or index would break, stays 0.999."""
     d = W.make_descriptors(n, 77)
     f, st = oracle.extract_features(d, widths[0])
     t = W.make_labels(d, 77)
@@ -237,5 +242,5 @@ def test_tensor_core_gradient_ragged_shapes(gpu_lib, precision, widths):
     cos = float(g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref)))
     print(precision, "ragged: per-tensor rel-L2", np.array2string(rel, precision=4), "cos", cos)
     assert abs(float(loss.item()) - loss_ref) <= 1e-2 * abs(loss_ref)
-    assert rel.max() < 2e-2 and cos > 0.999
+    assert rel.max() < 2e-2 * np.sqrt(3001 / n) and cos > 0.999
     assert m.device_status() == 0
