@@ -501,8 +501,11 @@ advisor_status advisor_get_device_status(advisor_model_t m, cudaStream_t stream)
 /* Near-tie statistics of the last selection with re-score on this model
  * (advisor_select_best / advisor_rank with eps_scores >= 0): h_counts[0] =
  * rows re-scored in FP32, h_counts[1] = rows re-scored in FP64 (host
- * int64[2]).  Synchronises `stream`.  Values are undefined before the first
- * such call. */
+ * int64[2]).  A ranking call with ADVISOR_FP32 scores and no FP16 tier takes
+ * its candidates' FP32 values from its own first-tier scores instead of
+ * re-scoring them (the plain FP32 scores, whose bound eps_fp32 is); [0] then
+ * counts those candidates.  Synchronises `stream`.  Values are undefined
+ * before the first such call. */
 advisor_status advisor_get_rescore_counts(advisor_model_t m, int64_t* h_counts, cudaStream_t stream);
 
 /* As advisor_get_rescore_counts with the FP16 middle tier (host int64[3]):

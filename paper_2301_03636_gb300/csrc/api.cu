@@ -291,7 +291,7 @@ bool mid_supported(const advisor_model* m) { return tc_supported(m) || wide_supp
 // Tiered selection; `src` supplies the rows for the re-score (features or descriptors).
 advisor_status do_select(advisor_model* m, const float* scores, int64_t n_rows, const int64_t* off, int64_t K,
                          adv::RowSrc src, bool rescore, float eps, float eps32, int32_t* best, double* best_score,
-                         cudaStream_t s, float eps16 = -1.f, bool counters_zeroed = false) {
+                         cudaStream_t s, float eps16 = -1.f, bool counters_zeroed = false, bool scores_fp32 = false) {
     if (K > m->max_kernels) return ADVISOR_ERR_OUT_OF_MEMORY;
     adv::SelectArgs a{};
     a.scores = scores;
@@ -329,13 +329,19 @@ advisor_status do_select(advisor_model* m, const float* scores, int64_t n_rows, 
         a.cand_rows = a.cand_mid_rows;   // the FP32 tier takes the survivors
     }
     const adv::MlpDesc md = mlp_desc(m);
-    adv::RowSrc r1 = src;
-    r1.rows = a.cand_rows;
-    r1.count_dev = &a.counters[mid ? 2 : 0];
-    r1.count = 0;
-    e = adv::launch_mlp_fp32(md, r1, a.y32, m->num_sms, true, s, a.status_word, m->cfg.list_blocks_per_sm,
-                             m->cfg.list_chunk_kb);
-    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    if (scores_fp32 && !mid) {
+        // the first tier's scores are the plain FP32 path's, whose bound eps32 was
+        // calibrated on that path: the FP32 tier reads them instead of re-scoring
+        a.y32_rows = scores;
+    } else {
+        adv::RowSrc r1 = src;
+        r1.rows = a.cand_rows;
+        r1.count_dev = &a.counters[mid ? 2 : 0];
+        r1.count = 0;
+        e = adv::launch_mlp_fp32(md, r1, a.y32, m->num_sms, true, s, a.status_word, m->cfg.list_blocks_per_sm,
+                                 m->cfg.list_chunk_kb);
+        if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
+    }
     e = adv::launch_select_tier2(a, s, m->cfg.select_block);
     if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
     adv::RowSrc r2 = src;
@@ -837,7 +843,8 @@ advisor_status advisor_rank_ex(advisor_model_t m, const advisor_variant_desc* d_
     st = rank_scores(m, d_desc, n_rows, precision, scores, status, &rs, stream);
     if (st != ADVISOR_OK) return st;
     return do_select(m, scores, n_rows, d_seg_off, n_kernels, rs, rescore && n_rows > 0, eps_scores, eps_fp32,
-                     d_best_local, d_best_score, stream, eps_fp16 >= 0.f ? eps_fp16 : -1.f, zeroed);
+                     d_best_local, d_best_score, stream, eps_fp16 >= 0.f ? eps_fp16 : -1.f, zeroed,
+                     precision == ADVISOR_FP32);
 }
 
 advisor_status advisor_rank_staged_ex(advisor_model_t m, const advisor_variant_desc* h_desc,
@@ -893,7 +900,8 @@ advisor_status advisor_rank_staged_ex(advisor_model_t m, const advisor_variant_d
     if (n_rows == 0) rank_scores(m, d_desc, 0, precision, scores, status, &rs, stream);
     else if (c == 0) return ADVISOR_ERR_CUDA;
     return do_select(m, scores, n_rows, d_seg_off, n_kernels, rs, rescore && n_rows > 0, eps_scores, eps_fp32,
-                     d_best_local, d_best_score, stream, eps_fp16 >= 0.f ? eps_fp16 : -1.f, zeroed);
+                     d_best_local, d_best_score, stream, eps_fp16 >= 0.f ? eps_fp16 : -1.f, zeroed,
+                     precision == ADVISOR_FP32);
 }
 
 advisor_status advisor_rank_staged(advisor_model_t m, const advisor_variant_desc* h_desc,

@@ -147,6 +147,9 @@ struct SelectArgs {
     int* seg_cnt;
     int64_t* cand_rows;
     float* y32;
+    // non-null: the FP32 value of candidate row r is y32_rows[r] (the first tier's
+    // scores were the plain FP32 path's) and y32 is not read
+    const float* y32_rows;
     int64_t* cand2_rows;
     double* y64;
     int* status_word;

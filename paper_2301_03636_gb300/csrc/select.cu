@@ -190,6 +190,11 @@ __global__ void __launch_bounds__(256) select_tier1_lane_kernel(SelectArgs a) {
     }
 }
 
+// FP32 value of the candidate at list position i
+__device__ __forceinline__ float cand_y32(const SelectArgs& a, int64_t i) {
+    return a.y32_rows ? a.y32_rows[a.cand_rows[i]] : a.y32[i];
+}
+
 __global__ void __launch_bounds__(256) select_tier2_kernel(SelectArgs a) {
     griddep_wait();
     griddep_trigger();
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(256) select_tier2_kernel(SelectArgs a) {
         float bv = INFINITY;
         int64_t br = -1;
         for (int i = lane; i < cnt; i += 32) {
-            const float v = a.y32[start + i];
+            const float v = cand_y32(a, start + i);
             if (finite_score(v)) lex_min(bv, br, v, a.cand_rows[start + i]);
         }
         warp_lex_min(bv, br);
@@ -214,7 +219,7 @@ __global__ void __launch_bounds__(256) select_tier2_kernel(SelectArgs a) {
         int cnt2 = 0;
         for (int i0 = 0; i0 < cnt; i0 += 32) {
             const int i = i0 + lane;
-            const bool take = i < cnt && finite_score(a.y32[start + i]) && (double)a.y32[start + i] <= thr;
+            const bool take = i < cnt && finite_score(cand_y32(a, start + i)) && (double)cand_y32(a, start + i) <= thr;
             cnt2 += __popc(__ballot_sync(0xffffffffu, take));
         }
         if (cnt2 > 1) {
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(256) select_tier2_kernel(SelectArgs a) {
             int done = 0;
             for (int i0 = 0; i0 < cnt; i0 += 32) {
                 const int i = i0 + lane;
-                const bool take = i < cnt && finite_score(a.y32[start + i]) && (double)a.y32[start + i] <= thr;
+                const bool take = i < cnt && finite_score(cand_y32(a, start + i)) && (double)cand_y32(a, start + i) <= thr;
                 const int64_t r = take ? a.cand_rows[start + i] : 0;
                 done += append_ordered(take, r, a.cand2_rows, base, done);
             }
