@@ -57,20 +57,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-// 2-D TMA store of box {x, y} from shared memory (bulk group of this thread).
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int32_t x, int32_t y) {
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(smem_addr(src)), "r"(x), "r"(y)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// all but the newest N bulk groups of this thread have finished reading shared memory
-template <int N>
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory"); }
-// all bulk groups of this thread are complete
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
 // UMMA shared-memory descriptor of an MN-major operand with the 128-byte
 // swizzle: atoms of 64 M/N values (128 B) x 8 K rows; M/N atoms `lbo` bytes
 // apart, 8-row K groups `sbo` bytes apart.
@@ -942,6 +928,10 @@ bool make_map(CUtensorMap* map, const uint16_t* p, int64_t ld, int mn, int64_t r
 }
 
 }  // namespace
+
+bool encode_rows_map(CUtensorMap* map, const void* p, int64_t cols, int64_t rows, int box_rows, int fmt) {
+    return make_map(map, reinterpret_cast<const uint16_t*>(p), cols, 0, rows, cols, box_rows, fmt);
+}
 
 // Dynamic shared memory: 1 KB of alignment slack, the ring, the barriers and
 // TMEM holder (2 GT_STAGES + 2 words of 8 bytes), the masked epilogue's sums.

@@ -101,6 +101,12 @@ struct TcArgs {
     // activations, row-major [n_rows][save_ld[l]] (save_ld[l] a multiple of 8)
     void* save_act[ADV_MAX_LAYERS];
     int save_ld[ADV_MAX_LAYERS];
+    // with use_tma_save, tm_save[l] maps save_act[l] (dims {save_ld[l], n_rows},
+    // box 64 columns x 128 rows, 128-byte swizzle: one slab of the shared-memory
+    // image) and every hidden layer but the last is stored from that image by TMA
+    // instead of row by row from the epilogue's registers
+    CUtensorMap tm_save[ADV_MAX_LAYERS];
+    int use_tma_save;
 };
 cudaError_t launch_mlp_tc(const TcArgs& a, int num_sms, cudaStream_t s, int ctas = 0);
 

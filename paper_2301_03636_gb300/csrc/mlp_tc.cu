@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
             uint32_t stage = 0, phase = 0;
             uint32_t xph[2] = {0, 0}, aph[2] = {0, 0};
             bool ok = true, any = false;
+            bool stores = false;   // TMA stores of saved activations issued (training forward)
             for (int p = 0; p < n_pairs && ok; ++p) {
                 const int ns = (2 * p + 1 < n_my) ? 2 : 1;
                 for (int l = 0; l < a.n_hidden && ok; ++l) {
@@ -171,6 +172,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                         }
                         if (!ok) break;
                         tc_fence_after();
+                        if constexpr (SAVE) {
+                            // layer l - 1's output is complete in act[s]: store it for the backward
+                            if (l >= 1 && a.use_tma_save && a.save_act[l - 1]) {
+                                const int32_t row0 = (int32_t)((int64_t)(b + (2 * p + s) * G) * ADV_TILE_M);
+                                for (int k = 0; k < a.nslab[l]; ++k)
+                                    tma_store_2d(&a.tm_save[l - 1], act[s] + (size_t)k * ADV_X_SLAB_BYTES, 64 * k,
+                                                 row0);
+                                bulk_commit();
+                                stores = true;
+                            }
+                        }
                         const uint32_t d_tmem = tmem + (uint32_t)(s * a.nmax);
                         for (int k = 0; k < a.nslab[l]; ++k) {
                             if (!mbar_wait_bounded(&w_full[stage], phase, a.status_word, abort_flag, lim)) {
@@ -188,6 +200,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                             if (++stage == TC_STAGES) { stage = 0; phase ^= 1u; }
                         }
                         if (!ok) break;
+                        // the epilogue (or the next X load) writes act[s] once the accumulator is
+                        // ready: the stores above must have read it first
+                        if (SAVE && stores) bulk_wait_read<0>();
                         umma_commit(&acc_full[s]);
                     }
                 }
@@ -196,6 +211,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                 umma_commit(drain);
                 mbar_wait_bounded(drain, 0, a.status_word, abort_flag, lim);
             }
+            if (SAVE && stores) bulk_wait_all();   // the saved activations are written before the CTA ends
         }
     } else {
         // ---------------- epilogue warps ----------------
@@ -275,7 +291,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_tc_kernel(const __grid_cons
                                     const uint32_t chunk = (uint32_t)(((c & 63) >> 3) + q);
                                     *reinterpret_cast<uint4*>(slab + sw128_offset(r, chunk)) =
                                         make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                                    if (SAVE && save && c + 8 * q < a.save_ld[l])
+                                    if (SAVE && save && !a.use_tma_save && c + 8 * q < a.save_ld[l])
                                         *reinterpret_cast<uint4*>(save + (size_t)(c + 8 * q) * 2) =
                                             make_uint4(pk[0], pk[1], pk[2], pk[3]);
                                 }

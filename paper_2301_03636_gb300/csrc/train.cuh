@@ -132,6 +132,11 @@ struct TcGemm {
 };
 cudaError_t launch_gemm_tc(const TcGemm& g, cudaStream_t s);
 
+// TMA tensor map of a row-major 16-bit array [rows][cols] (cols * 2 a multiple
+// of 16 bytes, 16-byte aligned base): box 64 columns x box_rows rows with the
+// 128-byte swizzle; fmt 1 BF16, else FP16.  False when it cannot be made.
+bool encode_rows_map(CUtensorMap* map, const void* p, int64_t cols, int64_t rows, int box_rows, int fmt);
+
 // ReLU backward through a hidden layer in one persistent kernel (the masked
 // form of TcGemm, specialised): dz[r][j] = 16-bit(sum_k dza[r][k] W[k][j])
 // where h[r][j] > 0, else 0, for r < n, j < fi, k < fo; and the bias-gradient

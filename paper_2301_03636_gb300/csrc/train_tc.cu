@@ -657,10 +657,15 @@ static cudaError_t forward_fused(const ModelLayout& L, const TrainLayout& Tl, ui
     a.status = nullptr;
     a.scores = reinterpret_cast<float*>(TW + Tl.act[L.n_layers]);
     a.fmt = fmt == 1 ? 1 : 0;   // instruction-descriptor code
+    a.use_tma_save = 1;
     for (int l = 0; l < L.n_hidden; ++l) {
         a.w_img[l] = ff.img16[fmt == 1 ? 0 : 1][l];
         a.save_act[l] = TW + Tl.h16[l];
         a.save_ld[l] = L.widths[l + 1];
+        // the layers before the last are stored from the scorer's shared-memory image by TMA
+        if (l + 1 < L.n_hidden &&
+            !encode_rows_map(&a.tm_save[l], a.save_act[l], a.save_ld[l], n, ADV_TILE_M, fmt == 1 ? 1 : 2))
+            a.use_tma_save = 0;
     }
     return launch_mlp_tc(a, ff.num_sms, s, ff.ctas);
 }
