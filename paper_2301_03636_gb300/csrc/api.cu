@@ -348,9 +348,8 @@ advisor_status do_select(advisor_model* m, const float* scores, int64_t n_rows, 
     r2.rows = a.cand2_rows;
     r2.count_dev = &a.counters[1];
     r2.count = 0;
-    e = adv::launch_mlp_fp64(md, r2, a.y64, m->num_sms, s);
-    if (e != cudaSuccess) return ADVISOR_ERR_CUDA;
-    return cuda_status(adv::launch_select_final(a, s, m->cfg.select_block));
+    // the FP64 scorer's last block makes the final selection (no launch of its own)
+    return cuda_status(adv::launch_mlp_fp64(md, r2, a.y64, m->num_sms, s, &a));
 }
 
 }  // namespace

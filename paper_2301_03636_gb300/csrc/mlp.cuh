@@ -76,7 +76,11 @@ cudaError_t launch_fit_standardizer(const int32_t* feat, const uint8_t* status, 
 cudaError_t launch_mlp_fp32(const MlpDesc& m, const RowSrc& src, float* out, int num_sms, bool for_list,
                             cudaStream_t s, int* status_word = nullptr, int list_blocks_per_sm = 1,
                             int list_chunk_kb = 32);
-cudaError_t launch_mlp_fp64(const MlpDesc& m, const RowSrc& src, double* out, int num_sms, cudaStream_t s);
+struct SelectArgs;
+// fin (nullable): the argmin's selection state; the last block then makes the
+// final selection (see mlp_fp64_kernel), with fin->counters[3] zeroed beforehand
+cudaError_t launch_mlp_fp64(const MlpDesc& m, const RowSrc& src, double* out, int num_sms, cudaStream_t s,
+                            const SelectArgs* fin = nullptr);
 
 // mlp_tc.cu
 struct TcArgs {
@@ -147,7 +151,8 @@ struct SelectArgs {
     double* best_score;
     float eps;                 // < 0: plain argmin
     float eps32;
-    int* counters;             // [0] tier-1 candidates, [1] tier-2 candidates, [2] FP16-tier survivors
+    int* counters;             // [0] tier-1 candidates, [1] tier-2 candidates, [2] FP16-tier survivors,
+                               // [3] FP64 scorer blocks done (its last block makes the final selection)
     int* seg_state;
     int* seg_start;
     int* seg_cnt;
@@ -174,7 +179,6 @@ cudaError_t launch_topn_tier1(const SelectArgs& a, cudaStream_t s, int block = 2
 cudaError_t launch_topn_tier2(const SelectArgs& a, cudaStream_t s, int block = 256);
 cudaError_t launch_topn_final(const SelectArgs& a, cudaStream_t s, int block = 256);
 cudaError_t launch_select_tier2(const SelectArgs& a, cudaStream_t s, int block = 256);
-cudaError_t launch_select_final(const SelectArgs& a, cudaStream_t s, int block = 256);
 cudaError_t launch_select_mid(const SelectArgs& a, cudaStream_t s, int block = 256);
 cudaError_t launch_topn_mid(const SelectArgs& a, cudaStream_t s, int block = 256);
 

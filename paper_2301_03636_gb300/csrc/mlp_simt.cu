@@ -624,9 +624,13 @@ __global__ void __launch_bounds__(256, 1) mlp_fp32_list_kernel(MlpDesc m, RowSrc
     }
 }
 
-// FP64 reference-order scorer: one block per listed row.
-template <int F, bool FROM_DESC>
-__global__ void __launch_bounds__(256) mlp_fp64_kernel(MlpDesc m, RowSrc src, double* __restrict__ out, int wmax) {
+// FP64 reference-order scorer: one block per listed row.  With FIN (the
+// argmin's last tier), the block that finishes last also makes the final
+// selection: every kernel whose FP64 candidates these are (seg_state 2) takes
+// the smallest (FP64 value, row) among them, as select_final_kernel would.
+template <int F, bool FROM_DESC, bool FIN>
+__global__ void __launch_bounds__(256) mlp_fp64_kernel(MlpDesc m, RowSrc src, double* __restrict__ out, int wmax,
+                                                       SelectArgs fin) {
     extern __shared__ double smem_d[];
     double* h0 = smem_d;
     double* h1 = h0 + wmax;
@@ -671,6 +675,42 @@ __global__ void __launch_bounds__(256) mlp_fp64_kernel(MlpDesc m, RowSrc src, do
             double* t = in; in = ob; ob = t;
         }
         if (threadIdx.x == 0) out[pos] = in[0];
+    }
+    if constexpr (FIN) {
+        __shared__ int last_s;
+        __threadfence();   // this block's FP64 values are visible before it is counted
+        __syncthreads();
+        if (threadIdx.x == 0) last_s = atomicAdd(&fin.counters[3], 1) == (int)gridDim.x - 1;
+        __syncthreads();
+        if (!last_s) return;
+        __threadfence();
+        // candidate i of kernel k: the thread at k's first candidate decides k
+        for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {
+            const int64_t row = fin.cand2_rows[i];
+            int64_t lo = 0, hi = fin.n_kernels - 1;   // the last kernel whose first row is <= row
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (fin.off[mid] <= row) lo = mid;
+                else hi = mid - 1;
+            }
+            const int64_t k = lo;
+            if (fin.seg_state[k] != 2 || fin.seg_start[k] != i) continue;
+            double bv = INFINITY;
+            int64_t br = -1;
+            for (int t = 0; t < fin.seg_cnt[k]; ++t) {
+                const double v = out[i + t];
+                const int64_t r = fin.cand2_rows[i + t];
+                if (v < (double)INFINITY && (br < 0 || v < bv || (v == bv && r < br))) {
+                    bv = v;
+                    br = r;
+                }
+            }
+            if (br >= 0) {
+                fin.best[k] = (int32_t)(br - fin.off[k]);
+                fin.best_score[k] = bv;
+            }
+            fin.seg_state[k] = 0;
+        }
     }
 }
 
@@ -822,28 +862,31 @@ cudaError_t launch_mlp_fp32(const MlpDesc& m, const RowSrc& src, float* out, int
 }
 
 template <int F, bool FD>
-static cudaError_t launch_fp64_t(const MlpDesc& m, const RowSrc& src, double* out, int grid, cudaStream_t s) {
+static cudaError_t launch_fp64_t(const MlpDesc& m, const RowSrc& src, double* out, int grid, cudaStream_t s,
+                                 const SelectArgs* fin) {
     int wmax = 0;
     for (int i = 0; i < m.nw; ++i) wmax = wmax > m.widths[i] ? wmax : m.widths[i];
     const size_t smem = (size_t)2 * wmax * sizeof(double);
-    auto k = mlp_fp64_kernel<F, FD>;
+    auto k = fin ? mlp_fp64_kernel<F, FD, true> : mlp_fp64_kernel<F, FD, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(k, dim3(grid), dim3(256), smem, s, m, src, out, wmax);
+    const SelectArgs none{};
+    e = launch_pdl(k, dim3(grid), dim3(256), smem, s, m, src, out, wmax, fin ? *fin : none);
     if (e != cudaSuccess) return e;
     adv_count_launch(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_fp64(const MlpDesc& m, const RowSrc& src, double* out, int num_sms, cudaStream_t s) {
+cudaError_t launch_mlp_fp64(const MlpDesc& m, const RowSrc& src, double* out, int num_sms, cudaStream_t s,
+                            const SelectArgs* fin) {
     int grid = num_sms * 4;
     if (!src.count_dev) grid = (int)(src.count < grid ? (src.count < 1 ? 1 : src.count) : grid);
     const bool fd = (src.feat == nullptr);
     switch (m.widths[0]) {
-        case 32: return fd ? launch_fp64_t<32, true>(m, src, out, grid, s) : launch_fp64_t<32, false>(m, src, out, grid, s);
-        case 33: return fd ? launch_fp64_t<33, true>(m, src, out, grid, s) : launch_fp64_t<33, false>(m, src, out, grid, s);
-        case 64: return fd ? launch_fp64_t<64, true>(m, src, out, grid, s) : launch_fp64_t<64, false>(m, src, out, grid, s);
-        case 128: return fd ? launch_fp64_t<128, true>(m, src, out, grid, s) : launch_fp64_t<128, false>(m, src, out, grid, s);
+        case 32: return fd ? launch_fp64_t<32, true>(m, src, out, grid, s, fin) : launch_fp64_t<32, false>(m, src, out, grid, s, fin);
+        case 33: return fd ? launch_fp64_t<33, true>(m, src, out, grid, s, fin) : launch_fp64_t<33, false>(m, src, out, grid, s, fin);
+        case 64: return fd ? launch_fp64_t<64, true>(m, src, out, grid, s, fin) : launch_fp64_t<64, false>(m, src, out, grid, s, fin);
+        case 128: return fd ? launch_fp64_t<128, true>(m, src, out, grid, s, fin) : launch_fp64_t<128, false>(m, src, out, grid, s, fin);
         default: return cudaErrorInvalidValue;
     }
 }

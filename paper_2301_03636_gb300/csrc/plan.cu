@@ -3,7 +3,7 @@
 //
 // Fig. 2 of arXiv 2301.03636 runs every generated variant of a kernel
 // through feature extraction, the cost model and a selection; batching many
-// kernels' variants into one pass makes that a fixed sequence of seven
+// kernels' variants into one pass makes that a fixed sequence of six
 // kernels and a memset whose shapes depend only on the batch size.  Replaying
 // the sequence as one graph removes the per-launch host overhead and the
 // gaps between kernels.  The autotuner measures a small set of launch shapes

@@ -304,32 +304,6 @@ __global__ void __launch_bounds__(256) select_mid_kernel(SelectArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(256) select_final_kernel(SelectArgs a) {
-    griddep_wait();
-    griddep_trigger();
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < a.n_kernels; k += nwarps) {
-        if (a.seg_state[k] != 2) continue;
-        const int64_t lo = a.off[k];
-        const int start = a.seg_start[k], cnt = a.seg_cnt[k];
-        double bv = INFINITY;
-        int64_t br = -1;
-        for (int i = lane; i < cnt; i += 32) {
-            const double v = a.y64[start + i];
-            if (v < (double)INFINITY) lex_min_d(bv, br, v, a.cand2_rows[start + i]);
-        }
-        warp_lex_min_d(bv, br);
-        if (lane == 0) {
-            if (br >= 0) {
-                a.best[k] = (int32_t)(br - lo);
-                a.best_score[k] = bv;
-            }
-            a.seg_state[k] = 0;
-        }
-    }
-}
-
 // ---- top N per kernel (Fig. 2: "sort codes based on cost and select top N") ----
 //
 // Exact against the FP64 ordering under the same error bounds as the argmin:
@@ -598,10 +572,6 @@ cudaError_t launch_select_tier1(const SelectArgs& a, cudaStream_t s, int block) 
 cudaError_t launch_select_tier2(const SelectArgs& a, cudaStream_t s, int block) {
     if (!select_block_ok(block)) return cudaErrorInvalidValue;
     return counted(launch_pdl(select_tier2_kernel, dim3(select_grid(a.n_kernels, block)), dim3(block), 0, s, a));
-}
-cudaError_t launch_select_final(const SelectArgs& a, cudaStream_t s, int block) {
-    if (!select_block_ok(block)) return cudaErrorInvalidValue;
-    return counted(launch_pdl(select_final_kernel, dim3(select_grid(a.n_kernels, block)), dim3(block), 0, s, a));
 }
 
 cudaError_t launch_select_mid(const SelectArgs& a, cudaStream_t s, int block) {

@@ -106,7 +106,7 @@ def test_plan_replays_match_direct_and_read_refilled_inputs(gpu_lib, setup):
     assert counts_a[0] > 0   # near ties exist on this workload
     plan = m.plan_rank(d, o, "bf16", eps, eps32, autotune=False)
     info = plan.info()
-    assert info["kernels_per_replay"] == 7   # extract, scorer, tier 1, FP32, tier 2, FP64, final
+    assert info["kernels_per_replay"] == 6   # extract, scorer, tier 1, FP32, tier 2, FP64 (+ final selection)
     assert info["replay_us"] == 0.0
     n0 = advisor.launch_count()
     for _ in range(3):
