@@ -182,6 +182,8 @@ class GpuPipeline:
 
     def __init__(self, base, max_rows: int, max_queries: int, params, mu, sigma, precision="bf16",
                  eps=-1.0, eps32=0.0, host_io: bool = True):
+        import ctypes
+
         import torch
         from . import advisor
         self.torch = torch
@@ -195,6 +197,9 @@ class GpuPipeline:
         self.h_off = torch.empty(max_queries + 1, dtype=torch.int64).pin_memory()
         self.h_best = torch.empty(max_queries, dtype=torch.int32).pin_memory()
         self.h_score = torch.empty(max_queries, dtype=torch.float64).pin_memory()
+        # numpy views of the pinned buffers (packing and reading the answers)
+        self.np_desc, self.np_off = self.h_desc.numpy(), self.h_off.numpy()
+        self.np_best, self.np_score = self.h_best.numpy(), self.h_score.numpy()
         if not host_io:   # device copies of the batch's inputs and answers
             self.d_desc = torch.empty((max_rows, 16), dtype=torch.int64, device=dev)
             self.d_off = torch.empty(max_queries + 1, dtype=torch.int64, device=dev)
@@ -204,46 +209,76 @@ class GpuPipeline:
         # host_io: the kernels read the batch's descriptors and offsets from the pinned
         # host buffers and write the answers into pinned host memory (one library call
         # per batch instead of four copies around it: half the host time and half the
-        # device time of a small batch); otherwise copies to and from device buffers
+        # device time of a small batch); otherwise copies to and from device buffers.
+        # The call goes straight to advisor_rank with the buffers' addresses (every
+        # batch starts at their first element), so a batch costs no tensor views.
         self.host_io = host_io
+        self._rank = advisor.lib().advisor_rank
+        self._args = (self.model.handle, ctypes.c_void_p(self.h_desc.data_ptr()),
+                      ctypes.c_void_p(self.h_off.data_ptr()), advisor._prec(precision), float(eps), float(eps32),
+                      ctypes.c_void_p(self.h_best.data_ptr()), ctypes.c_void_p(self.h_score.data_ptr()),
+                      ctypes.c_void_p(self.stream.cuda_stream))
+        self._check = advisor._check
         self.batch = None
         self.nk = 0
-        self.intervals = []   # (start, end) timing events of every batch on this pipeline's stream
+        # batch timing: with `ref` set (an event recorded before the first timed batch),
+        # every batch's start and end on this stream in ms after ref, read when the
+        # batch has finished; its two events then go back to the pool
+        self.ref = None
+        self.intervals = []
+        self._pool = []
+        self._ev = None
 
     def idle(self) -> bool:
         return self.batch is None
 
-    def launch(self, batch):
+    def _events(self):
+        if self.ref is None:
+            return None
+        if self._pool:
+            return self._pool.pop()
         torch = self.torch
-        n, k = pack(batch, self.h_desc.numpy(), self.h_off.numpy())
-        ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def launch(self, batch):
+        n, k = pack(batch, self.np_desc, self.np_off)
+        ev = self._events()
         if self.host_io:
-            ev_a.record(self.stream)
-            self.model.rank(self.h_desc[:n], self.h_off[:k + 1], self.precision, self.eps, self.eps32,
-                            best=self.h_best[:k], best_score=self.h_score[:k], stream=self.stream)
-            ev_b.record(self.stream)
+            if ev:
+                ev[0].record(self.stream)
+            h, desc, off, prec, eps, eps32, best, score, stream = self._args
+            self._check(self._rank(h, desc, n, off, k, prec, eps, eps32, best, score, None, None, stream),
+                        "advisor_rank")
+            if ev:
+                ev[1].record(self.stream)
             self.event.record(self.stream)
-            self.intervals.append((ev_a, ev_b))
-            self.batch, self.nk = batch, k
+            self._ev, self.batch, self.nk = ev, batch, k
             return
+        torch = self.torch
         with torch.cuda.stream(self.stream):
-            ev_a.record(self.stream)
+            if ev:
+                ev[0].record(self.stream)
             self.d_desc[:n].copy_(self.h_desc[:n], non_blocking=True)
             self.d_off[:k + 1].copy_(self.h_off[:k + 1], non_blocking=True)
             self.model.rank(self.d_desc[:n], self.d_off[:k + 1], self.precision, self.eps, self.eps32,
                             best=self.d_best[:k], best_score=self.d_score[:k], stream=self.stream)
             self.h_best[:k].copy_(self.d_best[:k], non_blocking=True)
             self.h_score[:k].copy_(self.d_score[:k], non_blocking=True)
-            ev_b.record(self.stream)
+            if ev:
+                ev[1].record(self.stream)
             self.event.record(self.stream)
-        self.intervals.append((ev_a, ev_b))
-        self.batch, self.nk = batch, k
+        self._ev, self.batch, self.nk = ev, batch, k
 
     def poll(self):
         if self.batch is None or not self.event.query():
             return []
-        out = [(self.batch, self.h_best[:self.nk].numpy().copy(), self.h_score[:self.nk].numpy().copy())]
-        self.batch = None
+        k = self.nk
+        out = [(self.batch, self.np_best[:k].copy(), self.np_score[:k].copy())]
+        if self._ev:
+            a, b = self._ev
+            self.intervals.append((self.ref.elapsed_time(a), self.ref.elapsed_time(b)))
+            self._pool.append(self._ev)
+        self._ev, self.batch = None, None
         return out
 
 
@@ -390,13 +425,14 @@ def run_serving(base, params, mu, sigma, queries: list[Query], precision="bf16",
         torch.cuda.synchronize()
         for p in pipes:
             p.poll()
+    ref = torch.cuda.Event(enable_timing=True)
+    ref.record()
     for p in pipes:
         p.intervals = []
+        p.ref = ref
     execs = [ThreadedPipeline(p) for p in pipes] if threads else pipes
     batcher = Batcher(max_rows, max_queries)
     srv = Server(batcher, execs)
-    ref = torch.cuda.Event(enable_timing=True)
-    ref.record()
     t0 = time.perf_counter()
     try:
         done = srv.run(queries)
@@ -406,7 +442,7 @@ def run_serving(base, params, mu, sigma, queries: list[Query], precision="bf16",
                 ex.close()
     wall = time.perf_counter() - t0
     torch.cuda.synchronize()
-    iv = [(ref.elapsed_time(a), ref.elapsed_time(b)) for p in pipes for a, b in p.intervals]
+    iv = [x for p in pipes for x in p.intervals]
     st = latency_stats(done)
     st["batches"] = len(iv)
     st["max_batches_in_flight"] = max_overlap(iv)
