@@ -207,6 +207,44 @@ __global__ void __launch_bounds__(128) standardize_kernel(const int32_t* __restr
     else write_x_row<F, FMT>(x_img, nslab, row, f, valid, sa, sc, x_rm);
 }
 
+// The same image (and the optional row-major copy), one 16-byte chunk of 8
+// features per thread: the 8 * nslab chunks of a row are consecutive threads,
+// so that a warp's loads and stores cover whole rows (a thread per row would
+// touch 32 rows with every access).  16-bit formats, F % 8 == 0, 16-byte
+// aligned feat.  Same values as write_x_row.
+template <int F, int FMT>
+__global__ void __launch_bounds__(256) standardize_chunks_kernel(const int32_t* __restrict__ feat, int64_t n_rows,
+                                                                 int64_t n_rows_padded, uint8_t* x_img, int nslab,
+                                                                 const float* __restrict__ sa,
+                                                                 const float* __restrict__ sc, uint16_t* x_rm) {
+    static_assert(F % 8 == 0, "whole 8-feature chunks");
+    const int cpr = nslab * 8;   // 16-byte chunks per image row
+    const int64_t total = n_rows_padded * cpr;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = t / cpr;
+        const int c = (int)(t - row * cpr);   // features 8c .. 8c + 7
+        const int k0 = 8 * c;
+        const bool live = row < n_rows && k0 < F;
+        float z[8];
+        if (live) {
+            const int4* src = reinterpret_cast<const int4*>(feat + (size_t)row * F + k0);
+            const int4 u = __ldg(src), v = __ldg(src + 1);
+            const int32_t q[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) z[e] = fmaf((float)q[e], __ldg(sa + k0 + e), -__ldg(sc + k0 + e));
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) z[e] = 0.f;
+        }
+        const uint4 pk = pack8<FMT>(z);
+        const int64_t tile = row / ADV_TILE_M;
+        const uint32_t r = (uint32_t)(row % ADV_TILE_M);
+        *reinterpret_cast<uint4*>(x_img + ((size_t)tile * nslab + (c >> 3)) * ADV_X_SLAB_BYTES +
+                                  sw128_offset(r, (uint32_t)(c & 7))) = pk;
+        if (x_rm && live) *reinterpret_cast<uint4*>(x_rm + (size_t)row * F + k0) = pk;
+    }
+}
+
 // Mean and population standard deviation of feature/65536 per column over
 // the valid rows, in FP64, with a fixed reduction order.
 __global__ void __launch_bounds__(256) fit_standardizer_kernel(const int32_t* __restrict__ feat,
@@ -312,6 +350,18 @@ static cudaError_t launch_standardize_f(const int32_t* feat, const uint8_t* stat
     if (grid == 0) return cudaSuccess;
     if (fmt == 3 && !x8_scale) return cudaErrorInvalidValue;
     if (x_rm && (fmt == 3 || F % 8 != 0 || ((uintptr_t)x_rm & 15) != 0)) return cudaErrorInvalidValue;
+    if constexpr (F % 8 == 0) {
+        if (fmt != 3 && ((uintptr_t)feat & 15) == 0) {   // a lane per 16-byte chunk
+            const int64_t total = npad * nslab * 8;
+            const unsigned g2 = (unsigned)((total + 255) / 256 < 65535 * 16 ? (total + 255) / 256 : 65535 * 16);
+            if (fmt == 1)
+                standardize_chunks_kernel<F, 1><<<g2, 256, 0, s>>>(feat, n, npad, x_img, nslab, sa, sc, x_rm);
+            else
+                standardize_chunks_kernel<F, 2><<<g2, 256, 0, s>>>(feat, n, npad, x_img, nslab, sa, sc, x_rm);
+            adv_count_launch(1);
+            return cudaGetLastError();
+        }
+    }
     if (fmt == 1)
         standardize_kernel<F, 1><<<grid, 128, 0, s>>>(feat, status, n, npad, x_img, nslab, sa, sc, x8_scale, x_rm);
     else if (fmt == 3)
