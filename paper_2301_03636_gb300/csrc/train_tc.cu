@@ -10,11 +10,15 @@
 //             db_l = column sums of dZ_l (fixed split order),
 //             dZ_{l-1} = 16-bit(dZ_l W_l masked by H_{l-1} > 0);
 //   Adam on the FP32 master weights, then the derived copies are rebuilt.
-// The GEMMs are this library's tcgen05 kernel (gemm_tc.cu), reading the
-// row-major operands in place as K-major or MN-major; every other step is a
-// kernel of this file.  Activations are kept in 16 bits between layers, so
-// the masks use the stored 16-bit values (positive iff the FP32
-// pre-activation rounded to a positive value).
+// The GEMMs are this library's tcgen05 kernels (gemm_tc.cu): the generic
+// TMA-fed GEMM, reading the row-major operands in place as K-major or
+// MN-major, for the weight gradients; the persistent ReLU-backward kernel for
+// dZ_{l-1} with the bias-gradient column sums in its epilogue.  For models
+// the fused scorer covers, the forward is that scorer (mlp_tc.cu) saving the
+// 16-bit activations.  The bias and output-row gradient partials are summed in
+// one launch at the end of the backward.  Activations are kept in 16 bits
+// between layers, so the masks use the stored 16-bit values (positive iff the
+// FP32 pre-activation rounded to a positive value).
 #include <algorithm>
 #include <type_traits>
 
