@@ -242,10 +242,11 @@ size_t train_layout(const ModelLayout& L, int64_t R, TrainLayout* t) {
     t->c32 = t->dB;
     // partials of the 16-bit backward's column sums: the last hidden layer's
     // (bias and output row, per 256-row block), the output bias (per 1,024
-    // rows), and per lower hidden layer the ReLU-backward kernel's (four per
-    // CTA of up to 256 CTAs, or one per 128-row tile in the generic form)
+    // rows, or per 256-row block with the loss fused in, which adds the loss's
+    // per block), and per lower hidden layer the ReLU-backward kernel's (four
+    // per CTA of up to 256 CTAs, or one per 128-row tile in the generic form)
     const int64_t tiles = (R + 127) / 128;
-    t->bias_part_floats = 2 * ((R + 255) / 256) * wmax + (R + 1023) / 1024 +
+    t->bias_part_floats = 2 * ((R + 255) / 256) * wmax + (R + 1023) / 1024 + 2 * ((R + 255) / 256) +
                           (int64_t)L.n_hidden * (tiles > 1024 ? tiles : 1024) * wmax;
     t->bias_part = take((size_t)t->bias_part_floats * 4);
     t->rows = R;
@@ -372,6 +373,16 @@ cudaError_t launch_train_step_ex(const ModelLayout& L, const TrainLayout& T, uin
     cudaError_t e = fmt == 0 ? launch_forward_saved(L, T, TW, md, feat, n, nullptr, s)
                              : launch_forward_saved_tc(L, T, TW, md, fmt, feat, n, nullptr, s, status_word, ff);
     if (e != cudaSuccess) return e;
+    if (fmt != 0 && o.loss == 0) {   // MSE on the tensor cores: the loss goes with the backward
+        e = launch_loss_backward_tc(L, T, TW, md, fmt, labels, n, grad, d_loss, s, status_word);
+        if (e != cudaSuccess) return e;
+        if (o.optimizer == 0) return launch_adam_update(L, P, grad, o.h, step, s);
+        rmsprop_kernel<<<grid1(L.n_params), 256, 0, s>>>(reinterpret_cast<float*>(P + L.p_master), grad,
+                                                         reinterpret_cast<float*>(P + L.p_adam_v), L.n_params,
+                                                         o.h.lr, o.alpha, o.h.eps, o.h.weight_decay);
+        adv_count_launch(1);
+        return cudaGetLastError();
+    }
     e = launch_mse_loss(L, T, TW, labels, n, o.loss == 1 ? nullptr : d_loss, s);
     if (e != cudaSuccess) return e;
     if (o.loss == 1) {

@@ -154,6 +154,12 @@ cudaError_t launch_dgrad_mask(const uint16_t* dza, int fo, const uint16_t* W, in
 cudaError_t launch_forward_saved_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
                                     int fmt, const int32_t* feat, int64_t n, float* d_y, cudaStream_t s,
                                     int* status_word, const FusedFwd* ff = nullptr);
+// MSE loss and backward of the saved 16-bit forward (y in the training region):
+// the loss (to the loss buffer and d_loss, nullable) and the gradient; where the
+// vectorised backward applies, dL/dy is computed inside it.
+cudaError_t launch_loss_backward_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
+                                    int fmt, const float* labels, int64_t n, float* d_grad, float* d_loss,
+                                    cudaStream_t s, int* status_word);
 cudaError_t launch_backward_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md, int fmt,
                                const float* d_dy, int64_t n, float* d_grad, cudaStream_t s, int* status_word);
 cudaError_t launch_train_step_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,

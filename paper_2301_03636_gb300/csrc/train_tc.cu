@@ -173,6 +173,8 @@ constexpr int SS_MAX_JOBS = ADV_MAX_LAYERS + 2;
 struct SplitSumJobs {
     const float* part[SS_MAX_JOBS];
     float* out[SS_MAX_JOBS];
+    float* out2[SS_MAX_JOBS];   // nullable: a second copy of the result
+    float div[SS_MAX_JOBS];     // the sum is divided by this
     int splits[SS_MAX_JOBS], w[SS_MAX_JOBS];
     int first_block[SS_MAX_JOBS + 1];   // blocks of job j: first_block[j] .. first_block[j + 1] - 1
     int n;
@@ -201,15 +203,19 @@ __global__ void __launch_bounds__(1024) splitsum_jobs_kernel(const __grid_consta
         float t = 0.f;
 #pragma unroll 8
         for (int y = 0; y < 32; ++y) t += red[y][threadIdx.x];
+        t = t / jb.div[j];
         jb.out[j][c] = t;
+        if (jb.out2[j]) jb.out2[j][c] = t;
     }
 }
 
 struct SplitSums {
     SplitSumJobs jb{};
-    void add(const float* part, int splits, int w, float* out) {
+    void add(const float* part, int splits, int w, float* out, float div = 1.f, float* out2 = nullptr) {
         jb.part[jb.n] = part;
         jb.out[jb.n] = out;
+        jb.out2[jb.n] = out2;
+        jb.div[jb.n] = div;
         jb.splits[jb.n] = splits;
         jb.w[jb.n] = w;
         jb.first_block[jb.n + 1] = jb.first_block[jb.n] + (w + 31) / 32;
@@ -294,26 +300,45 @@ __global__ void stdz16_vec_kernel(const int32_t* __restrict__ feat, int n, int F
 // w_out[j]) where h[r][j] > 0, else 0; plus the block's column sums in row
 // order: part0[block][j] = sum_r dZ[r][j] (the bias gradient, of the stored
 // 16-bit dZ as the GEMMs read it) and part1[block][j] = sum_r dy[r] h[r][j]
-// (the output-row gradient).
+// (the output-row gradient).  With labels (the MSE loss fused in), dy[r] =
+// (y[r] - t[r]) / n is computed here instead of read, and the block also
+// writes part_loss[block] = sum_r (y[r] - t[r])^2 / 2 and part_dsum[block] =
+// sum_r dy[r] (the output bias's gradient), rows in order.
 template <typename T>
 __global__ void __launch_bounds__(256) dz_last_colsum16_kernel(const float* __restrict__ dy,
                                                                const float* __restrict__ wo, const T* __restrict__ h,
                                                                int n, int w, T* __restrict__ dz,
-                                                               float* __restrict__ part0, float* __restrict__ part1) {
+                                                               float* __restrict__ part0, float* __restrict__ part1,
+                                                               const float* __restrict__ y,
+                                                               const float* __restrict__ labels,
+                                                               float* __restrict__ part_loss,
+                                                               float* __restrict__ part_dsum) {
     __shared__ float red0[256 * 8], red1[256 * 8];
+    __shared__ float redl[256], redd[256];
     const int w8 = w >> 3;
     const int cg = threadIdx.x % w8;            // column group: columns 8 cg .. 8 cg + 7
     const int rl = threadIdx.x / w8;            // row lane
     const int lanes = 256 / w8;                 // rows per pass
     const int r0 = blockIdx.x * VEC_ROWS;
     float s0[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, s1[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float sl = 0.f, sd = 0.f;                   // this row lane's loss and dy sums (column group 0)
     float wq[8];
     load8f(wo + 8 * cg, wq);
     for (int r = r0 + rl; r < r0 + VEC_ROWS && r < n; r += lanes) {
         const int v = r * w8 + cg;
         float hv[8], o[8];
         unpack8<T>(reinterpret_cast<const uint4*>(h)[v], hv);
-        const float d = dy[r];
+        float d;
+        if (labels) {
+            const float e = y[r] - labels[r];
+            d = e / (float)n;
+            if (cg == 0) {
+                sl += 0.5f * e * e;
+                sd += d;
+            }
+        } else {
+            d = dy[r];
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) o[i] = hv[i] > 0.f ? d * wq[i] : 0.f;
         const uint4 pk = pack8<T>(o);
@@ -331,6 +356,8 @@ __global__ void __launch_bounds__(256) dz_last_colsum16_kernel(const float* __re
         red0[threadIdx.x * 8 + i] = s0[i];
         red1[threadIdx.x * 8 + i] = s1[i];
     }
+    redl[threadIdx.x] = sl;
+    redd[threadIdx.x] = sd;
     __syncthreads();
     // row lanes of each column summed in lane order
     for (int t = threadIdx.x; t < w; t += 256) {
@@ -342,6 +369,15 @@ __global__ void __launch_bounds__(256) dz_last_colsum16_kernel(const float* __re
         }
         part0[(size_t)blockIdx.x * w + t] = a0;
         part1[(size_t)blockIdx.x * w + t] = a1;
+    }
+    if (labels && threadIdx.x == 0) {   // the row lanes' sums (column group 0 threads) in lane order
+        float al = 0.f, ad = 0.f;
+        for (int l = 0; l < lanes; ++l) {
+            al += redl[l * w8];
+            ad += redd[l * w8];
+        }
+        part_loss[blockIdx.x] = al;
+        part_dsum[blockIdx.x] = ad;
     }
 }
 
@@ -455,7 +491,19 @@ struct Tc {
     }
 
     // dL/dy in dy(); gradient (master layout) into grad
-    cudaError_t backward(int64_t n, float* grad, cudaStream_t s) const {
+    // Whether backward() takes the vectorised path, which can fuse the MSE loss in.
+    bool vec_path(int64_t n) const {
+        bool vec = n <= T_.rows;
+        for (int l = 0; l < L.n_hidden; ++l) vec = vec && vec_ok(n, L.widths[l + 1]);
+        return vec;
+    }
+
+    // dL/dy in dy(); gradient (master layout) into grad.  With labels (vectorised
+    // path only), dL/dy of the MSE loss is computed from y() and the labels inside
+    // the backward, and the loss goes to the loss buffer (and d_loss).
+    cudaError_t backward(int64_t n, float* grad, cudaStream_t s, const float* labels = nullptr,
+                         float* loss = nullptr, float* d_loss = nullptr) const {
+        if (labels) return vec_path(n) ? backward_vec(n, grad, s, labels, loss, d_loss) : cudaErrorInvalidValue;
         bool vec = true;
         for (int l = 0; l < L.n_hidden; ++l) vec = vec && vec_ok(n, L.widths[l + 1]);
         // the fused reductions' partials fit the bias-partial region (sized for the workspace's rows)
@@ -496,7 +544,8 @@ struct Tc {
 
     // The same backward with the dZ producers also reducing the bias (and
     // output-row) gradients per 256-row block.
-    cudaError_t backward_vec(int64_t n, float* grad, cudaStream_t s) const {
+    cudaError_t backward_vec(int64_t n, float* grad, cudaStream_t s, const float* labels = nullptr,
+                             float* loss = nullptr, float* d_loss = nullptr) const {
         const int blocks = (int)((n + VEC_ROWS - 1) / VEC_ROWS);
         const int nsplit = (int)((n + TC_SPLIT_ROWS - 1) / TC_SPLIT_ROWS);
         const int H = L.n_hidden;
@@ -506,15 +555,26 @@ struct Tc {
         // output bias's (p2), then one array per lower hidden layer
         float* p0 = bias_part();
         float* p1 = p0 + (size_t)blocks * wl;
-        float* p2 = p1 + (size_t)blocks * wl;
-        float* pl = p2 + nsplit;
+        float* p2 = p1 + (size_t)blocks * wl;   // output bias: nsplit partials, or blocks with labels
+        float* pls = p2 + std::max<int64_t>(nsplit, blocks);   // the loss's partials (labels)
+        float* pl = pls + blocks;
         const int64_t per_layer_rows = std::max<int64_t>((n + 127) / 128, 1024);
         SplitSums sums;
-        dz_last_colsum16_kernel<T><<<blocks, 256, 0, s>>>(dy(), md.W[H], h16(H - 1), (int)n, wl, dz16(0), p0, p1);
-        rowsum_kernel<<<nsplit, 256, 0, s>>>(dy(), n, p2);
-        adv_count_launch(2);
-        sums.add(p1, blocks, wl, grad + L.layer_w_off[H]);
-        sums.add(p2, nsplit, 1, grad + L.layer_b_off[H]);
+        if (labels) {
+            dz_last_colsum16_kernel<T><<<blocks, 256, 0, s>>>(nullptr, md.W[H], h16(H - 1), (int)n, wl, dz16(0), p0,
+                                                              p1, y(), labels, pls, p2);
+            adv_count_launch(1);
+            sums.add(p1, blocks, wl, grad + L.layer_w_off[H]);
+            sums.add(p2, blocks, 1, grad + L.layer_b_off[H]);
+            sums.add(pls, blocks, 1, loss, (float)n, d_loss);
+        } else {
+            dz_last_colsum16_kernel<T><<<blocks, 256, 0, s>>>(dy(), md.W[H], h16(H - 1), (int)n, wl, dz16(0), p0, p1,
+                                                              nullptr, nullptr, nullptr, nullptr);
+            rowsum_kernel<<<nsplit, 256, 0, s>>>(dy(), n, p2);
+            adv_count_launch(2);
+            sums.add(p1, blocks, wl, grad + L.layer_w_off[H]);
+            sums.add(p2, nsplit, 1, grad + L.layer_b_off[H]);
+        }
         sums.add(p0, blocks, wl, grad + L.layer_b_off[H - 1]);
         int cur = 0;
         for (int l = H - 1; l >= 0; --l) {
@@ -706,6 +766,23 @@ cudaError_t launch_backward_tc(const ModelLayout& L, const TrainLayout& T, uint8
     return Tc<__half>{L, T, TW, md, status_word}.backward(n, d_grad, s);
 }
 
+template <typename X>
+static cudaError_t loss_backward(const Tc<X>& tc, const ModelLayout& L, const TrainLayout& T, uint8_t* TW,
+                                 const float* labels, int64_t n, float* grad, float* d_loss, cudaStream_t s) {
+    if (tc.vec_path(n)) return tc.backward(n, grad, s, labels, reinterpret_cast<float*>(TW + T.loss), d_loss);
+    const cudaError_t e = launch_mse_loss(L, T, TW, labels, n, d_loss, s);
+    if (e != cudaSuccess) return e;
+    return tc.backward(n, grad, s);
+}
+
+cudaError_t launch_loss_backward_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* TW, const MlpDesc& md,
+                                    int fmt, const float* labels, int64_t n, float* d_grad, float* d_loss,
+                                    cudaStream_t s, int* status_word) {
+    if (fmt == 1)
+        return loss_backward(Tc<__nv_bfloat16>{L, T, TW, md, status_word}, L, T, TW, labels, n, d_grad, d_loss, s);
+    return loss_backward(Tc<__half>{L, T, TW, md, status_word}, L, T, TW, labels, n, d_grad, d_loss, s);
+}
+
 cudaError_t launch_train_step_tc(const ModelLayout& L, const TrainLayout& T, uint8_t* P, uint8_t* TW,
                                  const MlpDesc& md, int fmt, const int32_t* feat, const float* labels, int64_t n,
                                  const AdamHyper* adam, int64_t step, float* d_grad_out, float* d_loss,
@@ -713,9 +790,7 @@ cudaError_t launch_train_step_tc(const ModelLayout& L, const TrainLayout& T, uin
     float* grad = d_grad_out ? d_grad_out : reinterpret_cast<float*>(TW + T.grad);
     cudaError_t e = launch_forward_saved_tc(L, T, TW, md, fmt, feat, n, nullptr, s, status_word, ff);
     if (e != cudaSuccess) return e;
-    e = launch_mse_loss(L, T, TW, labels, n, d_loss, s);
-    if (e != cudaSuccess) return e;
-    e = launch_backward_tc(L, T, TW, md, fmt, nullptr, n, grad, s, status_word);
+    e = launch_loss_backward_tc(L, T, TW, md, fmt, labels, n, grad, d_loss, s, status_word);
     if (e != cudaSuccess || !adam) return e;
     return launch_adam_update(L, P, grad, *adam, step, s);
 }
