@@ -100,6 +100,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Packed FP32 pairs (sm_100 and later): one instruction computes two
+// independent FMAs, each rounded as a scalar fmaf.  A pair lives in a 64-bit
+// register: the low half is the first element.
+__device__ __forceinline__ uint64_t f32x2_dup(float v) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(d) : "f"(v));
+    return d;
+}
+__device__ __forceinline__ void f32x2_fma(uint64_t& c, uint64_t a, uint64_t b) {   // c = a * b + c
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ void f32x2_unpack(uint64_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// Request the 128-byte line holding `p` into L2 (no data returned; the
+// address must lie inside an allocation).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ uint64_t global_timer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));

@@ -497,11 +497,24 @@ __global__ void __launch_bounds__(256, 1) mlp_fp32_list_kernel(MlpDesc m, RowSrc
     __shared__ int row_ok[RB];
     __shared__ int abort_s;
     const int tid = threadIdx.x;
+    const int nh = m.nw - 2;
+    {
+        // Every block streams all of the transposed weights, tile after tile,
+        // and the FP64 re-score after this kernel reads them again.  Their
+        // lines are requested into L2 all at once here (one line per thread
+        // of the grid), while the selection kernel before is still running,
+        // instead of one ring chunk after another from DRAM.
+        const int64_t gt = (int64_t)blockIdx.x * blockDim.x + tid, gs = (int64_t)gridDim.x * blockDim.x;
+        for (int l = 0; l < nh; ++l) {
+            const char* p = reinterpret_cast<const char*>(m.WT[l]);
+            const int64_t lines = ((int64_t)m.widths[l] * m.wt_ld[l] * 4 + 127) / 128;
+            for (int64_t i = gt; i < lines; i += gs) prefetch_l2(p + i * 128);
+        }
+    }
     griddep_wait();   // the candidate list and its count come from the selection kernel before
     griddep_trigger();
     const int64_t count = src.count_dev ? (int64_t)*src.count_dev : src.count;
     const int64_t ntiles = (count + RB - 1) / RB;
-    const int nh = m.nw - 2;
     int nchunks = 0;
     for (int l = 0; l < nh; ++l) nchunks += (m.widths[l] + kc - 1) / kc;
     if (tid == 0) {
@@ -551,11 +564,12 @@ __global__ void __launch_bounds__(256, 1) mlp_fp32_list_kernel(MlpDesc m, RowSrc
         int c = 0;
         for (int l = 0; l < nh; ++l) {
             const int fi = m.widths[l], fo = m.widths[l + 1], ld = m.wt_ld[l];
-            float acc[JP][2][8];
+            // acc[p][e][i]: neuron 2 cp + 256 p + e, rows 2 i and 2 i + 1 of the group (FP32 pair)
+            uint64_t acc[JP][2][4];
 #pragma unroll
             for (int p = 0; p < JP; ++p)
 #pragma unroll
-                for (int r = 0; r < 8; ++r) acc[p][0][r] = acc[p][1][r] = 0.f;
+                for (int i = 0; i < 4; ++i) acc[p][0][i] = acc[p][1][i] = 0ull;
             for (int k0 = 0; k0 < fi; k0 += kc, ++c) {
                 const int stage = (int)((used + c) % stages);
                 const uint32_t par = ((used + c) / stages) & 1u;
@@ -563,18 +577,21 @@ __global__ void __launch_bounds__(256, 1) mlp_fp32_list_kernel(MlpDesc m, RowSrc
                 const float* wk = wbuf + (size_t)stage * kc * wmax4;
                 const int nk = fi - k0 < kc ? fi - k0 : kc;
                 auto step = [&](int kk) {
-                    const float4* hv = reinterpret_cast<const float4*>(in + (k0 + kk) * RB + 8 * rg);
-                    const float4 ha = hv[0], hb = hv[1];
-                    const float hr[8] = {ha.x, ha.y, ha.z, ha.w, hb.x, hb.y, hb.z, hb.w};
+                    // the 8 activations as row pairs (0,1) (2,3) (4,5) (6,7)
+                    const ulonglong2* hv = reinterpret_cast<const ulonglong2*>(in + (k0 + kk) * RB + 8 * rg);
+                    const ulonglong2 ha = hv[0], hb = hv[1];
+                    const uint64_t hp[4] = {ha.x, ha.y, hb.x, hb.y};
 #pragma unroll
                     for (int p = 0; p < JP; ++p) {
                         const int j = 2 * cp + 256 * p;
                         // columns past the padded width read column 0; their sums are never stored
                         const float2 w = *reinterpret_cast<const float2*>(wk + kk * ld + (j < ld ? j : 0));
+                        const uint64_t wx = f32x2_dup(w.x), wy = f32x2_dup(w.y);
+                        // two rows per instruction, each an IEEE FMA as fmaf computes it
 #pragma unroll
-                        for (int r = 0; r < 8; ++r) {
-                            acc[p][0][r] = fmaf(hr[r], w.x, acc[p][0][r]);
-                            acc[p][1][r] = fmaf(hr[r], w.y, acc[p][1][r]);
+                        for (int i = 0; i < 4; ++i) {
+                            f32x2_fma(acc[p][0][i], hp[i], wx);
+                            f32x2_fma(acc[p][1][i], hp[i], wy);
                         }
                     }
                 };
@@ -594,11 +611,14 @@ __global__ void __launch_bounds__(256, 1) mlp_fp32_list_kernel(MlpDesc m, RowSrc
                     const int j = 2 * cp + 256 * p + e;
                     if (j < fo) {
                         const float bb = __ldg(m.b[l] + j);
+                        float a[8];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) f32x2_unpack(acc[p][e][i], a[2 * i], a[2 * i + 1]);
                         float4* o4 = reinterpret_cast<float4*>(ob + j * RB + 8 * rg);
-                        o4[0] = make_float4(fmaxf(acc[p][e][0] + bb, 0.f), fmaxf(acc[p][e][1] + bb, 0.f),
-                                            fmaxf(acc[p][e][2] + bb, 0.f), fmaxf(acc[p][e][3] + bb, 0.f));
-                        o4[1] = make_float4(fmaxf(acc[p][e][4] + bb, 0.f), fmaxf(acc[p][e][5] + bb, 0.f),
-                                            fmaxf(acc[p][e][6] + bb, 0.f), fmaxf(acc[p][e][7] + bb, 0.f));
+                        o4[0] = make_float4(fmaxf(a[0] + bb, 0.f), fmaxf(a[1] + bb, 0.f), fmaxf(a[2] + bb, 0.f),
+                                            fmaxf(a[3] + bb, 0.f));
+                        o4[1] = make_float4(fmaxf(a[4] + bb, 0.f), fmaxf(a[5] + bb, 0.f), fmaxf(a[6] + bb, 0.f),
+                                            fmaxf(a[7] + bb, 0.f));
                     }
                 }
             }
