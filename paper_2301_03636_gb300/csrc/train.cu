@@ -3,7 +3,7 @@
 // 0.5 * mean (y - t)^2 on ln runtime, gradient by the hand-written backward
 // of the ReLU MLP, Adam (Kingma & Ba) on the FP32 master weights.
 //
-// GEMMs are 64x64-tiled SIMT FP32 with generic operand strides:
+// GEMMs are 128x128-tiled SIMT FP32 with generic operand strides:
 //   forward   Out = In * W^T (+ b, ReLU on hidden layers)
 //   dIn       dH  = dZ * W, masked by the ReLU of the layer input
 //   dW        dW  = dZ^T * In, split over rows in fixed chunks, then summed in
@@ -17,8 +17,8 @@
 namespace adv {
 
 namespace {
-constexpr int GT = 64;   // tile
-constexpr int GK = 16;   // K chunk
+constexpr int GT = 128;  // tile (rows and columns)
+constexpr int GK = 8;    // K chunk
 constexpr int SPLIT_ROWS = 1024;
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -38,48 +38,92 @@ struct GemmArgs {
     int64_t ldm;
 };
 
-// EPI: 0 plain, 1 bias + ReLU, 2 bias, 3 ReLU-derivative mask
+// EPI: 0 plain, 1 bias + ReLU, 2 bias, 3 ReLU-derivative mask.
+// 128 x 128 tile, 256 threads, 8 x 8 outputs per thread (rows 4 ty .. + 3 and
+// 64 + 4 ty .. + 3, columns likewise with tx), K in chunks of 8 through a
+// double-buffered shared-memory tile: the next chunk's global loads are in
+// flight while the current one is used.  Each output is summed over k in
+// increasing order with FMA (the order of the definition).  An operand whose k
+// index is contiguous in memory is loaded with 8 consecutive threads along k,
+// otherwise with consecutive threads along its row or column index, so that a
+// warp's loads are coalesced either way.
 template <int EPI>
-__global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
-    __shared__ float As[GK][GT + 4];
-    __shared__ float Bs[GK][GT + 4];
+__global__ void __launch_bounds__(256, 2) gemm_kernel(GemmArgs g) {
+    __shared__ __align__(16) float As[2][GK][GT + 4];
+    __shared__ __align__(16) float Bs[2][GK][GT + 4];
     const int tid = threadIdx.x;
-    const int tx = tid % 16, ty = tid / 16;
+    const int tx = tid & 15, ty = tid >> 4;
     const int64_t m0 = (int64_t)blockIdx.y * GT, n0 = (int64_t)blockIdx.x * GT;
     const int64_t kb = (int64_t)blockIdx.z * g.k_per_split;
     const int64_t ke = kb + g.k_per_split < g.K ? kb + g.k_per_split : g.K;
-    float acc[4][4] = {};
-    for (int64_t k0 = kb; k0 < ke; k0 += GK) {
-        for (int i = tid; i < GK * GT; i += 256) {
-            const int kk = i / GT, mm = i % GT;
-            const int64_t k = k0 + kk, m = m0 + mm;
-            As[kk][mm] = (k < ke && m < g.M) ? g.A[m * g.sam + k * g.sak] : 0.f;
-            const int64_t n = n0 + mm;
-            Bs[kk][mm] = (k < ke && n < g.N) ? g.B[k * g.sbk + n * g.sbn] : 0.f;
+    const bool a_kc = g.sak == 1, b_kc = g.sbk == 1;
+    // element r (0..3) of this thread's share of a 128 x 8 operand chunk
+    auto idx = [&](bool kc, int r, int& mn, int& kk) {
+        if (kc) { mn = (tid >> 3) + 32 * r; kk = tid & 7; }
+        else { mn = tid & 127; kk = (tid >> 7) + 2 * r; }
+    };
+    float ra[4], rb[4];
+    auto load = [&](int64_t k0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int mn, kk;
+            idx(a_kc, r, mn, kk);
+            const int64_t m = m0 + mn, ka = k0 + kk;
+            ra[r] = (m < g.M && ka < ke) ? g.A[m * g.sam + ka * g.sak] : 0.f;
+            idx(b_kc, r, mn, kk);
+            const int64_t n = n0 + mn, kbb = k0 + kk;
+            rb[r] = (n < g.N && kbb < ke) ? g.B[kbb * g.sbk + n * g.sbn] : 0.f;
         }
-        __syncthreads();
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int mn, kk;
+            idx(a_kc, r, mn, kk);
+            As[buf][kk][mn] = ra[r];
+            idx(b_kc, r, mn, kk);
+            Bs[buf][kk][mn] = rb[r];
+        }
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    int buf = 0;
+    if (kb < ke) {
+        load(kb);
+        store(0);
+    }
+    __syncthreads();
+    for (int64_t k0 = kb; k0 < ke; k0 += GK) {
+        const bool more = k0 + GK < ke;
+        if (more) load(k0 + GK);
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-            float a[4], b[4];
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * ty]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + 4 * ty]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * tx]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + 4 * tx]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
+        if (more) store(buf ^ 1);   // that buffer's readers passed the barrier below last chunk
         __syncthreads();
+        buf ^= 1;
     }
     float* C = g.C + (int64_t)blockIdx.z * g.c_split_stride;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t m = m0 + ty * 4 + i;
+    for (int i = 0; i < 8; ++i) {
+        const int64_t m = m0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + i - 4);
         if (m >= g.M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t n = n0 + tx * 4 + j;
+        for (int j = 0; j < 8; ++j) {
+            const int64_t n = n0 + (j < 4 ? 4 * tx + j : 64 + 4 * tx + j - 4);
             if (n >= g.N) continue;
             float v = acc[i][j];
             if constexpr (EPI == 1) v = fmaxf(v + g.bias[n], 0.f);
@@ -90,10 +134,39 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
     }
 }
 
+// A GEMM with one output column (N = 1: the output layer's forward) or one
+// output row (M = 1: the output layer's weight gradient) as a matrix-vector
+// product: one thread per output element of the split, summing over k in
+// increasing order with FMA, as gemm_kernel does (same values), without the
+// 127 idle columns or rows of a 128 x 128 tile.
+template <int EPI, bool ROW>
+__global__ void __launch_bounds__(256) gemv_kernel(GemmArgs g) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // m (N = 1) or n (M = 1)
+    if (t >= (ROW ? g.N : g.M)) return;
+    const int64_t kb = (int64_t)blockIdx.z * g.k_per_split;
+    const int64_t ke = kb + g.k_per_split < g.K ? kb + g.k_per_split : g.K;
+    const float* A = ROW ? g.A : g.A + t * g.sam;
+    const float* B = ROW ? g.B + t * g.sbn : g.B;
+    float v = 0.f;
+    for (int64_t k = kb; k < ke; ++k) v = fmaf(A[k * g.sak], B[k * g.sbk], v);
+    const int64_t m = ROW ? 0 : t, n = ROW ? t : 0;
+    if constexpr (EPI == 1) v = fmaxf(v + g.bias[n], 0.f);
+    if constexpr (EPI == 2) v = v + g.bias[n];
+    if constexpr (EPI == 3) v = g.mask[m * g.ldm + n] > 0.f ? v : 0.f;
+    g.C[(int64_t)blockIdx.z * g.c_split_stride + m * g.ldc + n] = v;
+}
+
 template <int EPI>
 cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
-    dim3 grid((unsigned)((g.N + GT - 1) / GT), (unsigned)((g.M + GT - 1) / GT), (unsigned)splits);
-    gemm_kernel<EPI><<<grid, 256, 0, s>>>(g);
+    if (g.N == 1 || g.M == 1) {
+        const int64_t len = g.N == 1 ? g.M : g.N;
+        dim3 grid((unsigned)((len + 255) / 256), 1, (unsigned)splits);
+        if (g.N == 1) gemv_kernel<EPI, false><<<grid, 256, 0, s>>>(g);
+        else gemv_kernel<EPI, true><<<grid, 256, 0, s>>>(g);
+    } else {
+        dim3 grid((unsigned)((g.N + GT - 1) / GT), (unsigned)((g.M + GT - 1) / GT), (unsigned)splits);
+        gemm_kernel<EPI><<<grid, 256, 0, s>>>(g);
+    }
     adv_count_launch(1);
     return cudaGetLastError();
 }
