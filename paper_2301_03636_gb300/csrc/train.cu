@@ -36,6 +36,8 @@ struct GemmArgs {
     const float* bias;        // EPI 1, 2
     const float* mask;        // EPI 3: C = mask > 0 ? acc : 0, mask(m, n) = mask[m * ldm + n]
     int64_t ldm;
+    float* rowsum;            // optional: per split, sum over k of A(m, k) at rowsum[z * rowsum_stride + m]
+    int64_t rowsum_stride;
 };
 
 // EPI: 0 plain, 1 bias + ReLU, 2 bias, 3 ReLU-derivative mask.
@@ -46,7 +48,9 @@ struct GemmArgs {
 // increasing order with FMA (the order of the definition).  An operand whose k
 // index is contiguous in memory is loaded with 8 consecutive threads along k,
 // otherwise with consecutive threads along its row or column index, so that a
-// warp's loads are coalesced either way.
+// warp's loads are coalesced either way.  With `rowsum`, the blocks of the
+// first column tile also sum each row of A over the split's k range, in
+// increasing k (the bias gradient when A is dZ transposed).
 template <int EPI>
 __global__ void __launch_bounds__(256, 2) gemm_kernel(GemmArgs g) {
     __shared__ __align__(16) float As[2][GK][GT + 4];
@@ -85,11 +89,13 @@ __global__ void __launch_bounds__(256, 2) gemm_kernel(GemmArgs g) {
             Bs[buf][kk][mn] = rb[r];
         }
     };
-    float acc[8][8];
+    uint64_t acc[8][4];   // row i, columns (2 jj, 2 jj + 1) as an FP32 pair
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0ull;
+    const bool do_rs = g.rowsum && blockIdx.x == 0 && tid < GT;   // row tid of the tile
+    float accb = 0.f;
     int buf = 0;
     if (kb < ke) {
         load(kb);
@@ -103,29 +109,40 @@ __global__ void __launch_bounds__(256, 2) gemm_kernel(GemmArgs g) {
         for (int kk = 0; kk < GK; ++kk) {
             const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * ty]);
             const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + 4 * ty]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * tx]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + 4 * tx]);
+            const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(&Bs[buf][kk][4 * tx]);
+            const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(&Bs[buf][kk][64 + 4 * tx]);
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            const uint64_t b[4] = {b0.x, b0.y, b1.x, b1.y};
+            // two columns per instruction, each an IEEE FMA as fmaf computes it
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i) {
+                const uint64_t a2 = f32x2_dup(a[i]);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int jj = 0; jj < 4; ++jj) f32x2_fma(acc[i][jj], a2, b[jj]);
+            }
+        }
+        if (do_rs) {
+#pragma unroll
+            for (int kk = 0; kk < GK; ++kk) accb += As[buf][kk][tid];
         }
         if (more) store(buf ^ 1);   // that buffer's readers passed the barrier below last chunk
         __syncthreads();
         buf ^= 1;
     }
+    if (do_rs && m0 + tid < g.M) g.rowsum[(int64_t)blockIdx.z * g.rowsum_stride + m0 + tid] = accb;
     float* C = g.C + (int64_t)blockIdx.z * g.c_split_stride;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int64_t m = m0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + i - 4);
         if (m >= g.M) continue;
+        float r[8];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) f32x2_unpack(acc[i][jj], r[2 * jj], r[2 * jj + 1]);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int64_t n = n0 + (j < 4 ? 4 * tx + j : 64 + 4 * tx + j - 4);
             if (n >= g.N) continue;
-            float v = acc[i][j];
+            float v = r[j];
             if constexpr (EPI == 1) v = fmaxf(v + g.bias[n], 0.f);
             if constexpr (EPI == 2) v = v + g.bias[n];
             if constexpr (EPI == 3) v = g.mask[m * g.ldm + n] > 0.f ? v : 0.f;
@@ -138,18 +155,42 @@ __global__ void __launch_bounds__(256, 2) gemm_kernel(GemmArgs g) {
 // output row (M = 1: the output layer's weight gradient) as a matrix-vector
 // product: one thread per output element of the split, summing over k in
 // increasing order with FMA, as gemm_kernel does (same values), without the
-// 127 idle columns or rows of a 128 x 128 tile.
+// 127 idle columns or rows of a 128 x 128 tile.  With `rowsum` (M = 1 only),
+// thread N sums A over the split instead (the output bias's gradient).
 template <int EPI, bool ROW>
 __global__ void __launch_bounds__(256) gemv_kernel(GemmArgs g) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // m (N = 1) or n (M = 1)
-    if (t >= (ROW ? g.N : g.M)) return;
     const int64_t kb = (int64_t)blockIdx.z * g.k_per_split;
     const int64_t ke = kb + g.k_per_split < g.K ? kb + g.k_per_split : g.K;
+    if (ROW && g.rowsum && t == g.N) {
+        float v = 0.f;
+        for (int64_t k = kb; k < ke; ++k) v += g.A[k * g.sak];
+        g.rowsum[(int64_t)blockIdx.z * g.rowsum_stride] = v;
+        return;
+    }
+    if (t >= (ROW ? g.N : g.M)) return;
     const float* A = ROW ? g.A : g.A + t * g.sam;
     const float* B = ROW ? g.B + t * g.sbn : g.B;
     float v = 0.f;
-    for (int64_t k = kb; k < ke; ++k) v = fmaf(A[k * g.sak], B[k * g.sbk], v);
+    int64_t k = kb;
+    if (!ROW && g.sak == 1 && g.sbk == 1 && ((reinterpret_cast<uintptr_t>(A + kb) | reinterpret_cast<uintptr_t>(B + kb)) & 15) == 0) {
+        // the row of A and the column of B as 16-byte loads, the FMAs still in k order
+        for (; k + 4 <= ke; k += 4) {
+            const float4 a = *reinterpret_cast<const float4*>(A + k);
+            const float4 b = __ldg(reinterpret_cast<const float4*>(B + k));
+            v = fmaf(a.x, b.x, v);
+            v = fmaf(a.y, b.y, v);
+            v = fmaf(a.z, b.z, v);
+            v = fmaf(a.w, b.w, v);
+        }
+    }
+    for (; k < ke; ++k) v = fmaf(A[k * g.sak], B[k * g.sbk], v);
     const int64_t m = ROW ? 0 : t, n = ROW ? t : 0;
+    if (!ROW && g.rowsum) {   // one input column: the row's sum over the split is its only A element's
+        float r = 0.f;
+        for (int64_t kk = kb; kk < ke; ++kk) r += A[kk * g.sak];
+        g.rowsum[(int64_t)blockIdx.z * g.rowsum_stride + m] = r;
+    }
     if constexpr (EPI == 1) v = fmaxf(v + g.bias[n], 0.f);
     if constexpr (EPI == 2) v = v + g.bias[n];
     if constexpr (EPI == 3) v = g.mask[m * g.ldm + n] > 0.f ? v : 0.f;
@@ -159,7 +200,7 @@ __global__ void __launch_bounds__(256) gemv_kernel(GemmArgs g) {
 template <int EPI>
 cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
     if (g.N == 1 || g.M == 1) {
-        const int64_t len = g.N == 1 ? g.M : g.N;
+        const int64_t len = g.N == 1 ? g.M : g.N + (g.rowsum ? 1 : 0);
         dim3 grid((unsigned)((len + 255) / 256), 1, (unsigned)splits);
         if (g.N == 1) gemv_kernel<EPI, false><<<grid, 256, 0, s>>>(g);
         else gemv_kernel<EPI, true><<<grid, 256, 0, s>>>(g);
@@ -242,17 +283,6 @@ __global__ void rmsprop_kernel(float* __restrict__ p, const float* __restrict__ 
         v[i] = vi;
         p[i] -= lr * gi / (sqrtf(vi) + eps);
     }
-}
-
-// Column sums of dZ [n][w] per split of SPLIT_ROWS rows.
-__global__ void colsum_kernel(const float* __restrict__ dz, int64_t n, int w, float* __restrict__ part,
-                              int64_t split_stride) {
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= w) return;
-    const int64_t b = (int64_t)blockIdx.y * SPLIT_ROWS, e = b + SPLIT_ROWS < n ? b + SPLIT_ROWS : n;
-    float s = 0.f;
-    for (int64_t r = b; r < e; ++r) s += dz[r * w + o];
-    part[(int64_t)blockIdx.y * split_stride + o] = s;
 }
 
 // grad[j] = sum over splits (in order) of part[s][j]
@@ -369,25 +399,33 @@ cudaError_t launch_backward_saved(const ModelLayout& L, const TrainLayout& T, ui
     float* dz = reinterpret_cast<float*>(TW + T.dA);
     float* dnext = reinterpret_cast<float*>(TW + T.dB);
     float* part = reinterpret_cast<float*>(TW + T.part);
-    const int splits = (int)((n + SPLIT_ROWS - 1) / SPLIT_ROWS);
+    float* bpart = reinterpret_cast<float*>(TW + T.bias_part);
+    int64_t lmax = 0;   // the dW partial buffer holds T.splits x lmax floats
+    for (int l = 0; l < L.n_layers; ++l)
+        lmax = (int64_t)L.widths[l] * L.widths[l + 1] > lmax ? (int64_t)L.widths[l] * L.widths[l + 1] : lmax;
     for (int l = L.n_layers - 1; l >= 0; --l) {
         const int fi = L.widths[l], fo = L.widths[l + 1];
         float* gW = grad + L.layer_w_off[l];
         float* gb = grad + L.layer_b_off[l];
-        // dW = dZ^T * In, split over rows in fixed chunks, summed in a fixed order
+        // dW = dZ^T * In and db = column sums of dZ in one launch, split over rows
+        // in fixed chunks, each summed in a fixed order.  The single-output layer's
+        // matrix-vector form takes 128-row chunks (eight times the threads) where
+        // its partials fit.
+        int64_t rows_per = SPLIT_ROWS;
+        if (fo == 1 && ((n + 127) / 128) * (int64_t)fi <= (int64_t)T.splits * lmax) rows_per = 128;
+        const int sp = (int)((n + rows_per - 1) / rows_per);
         GemmArgs g{};
         g.A = dz; g.sam = 1; g.sak = fo;
         g.B = act(l); g.sbk = fi; g.sbn = 1;
         g.C = part; g.ldc = fi;
-        g.M = fo; g.N = fi; g.K = n; g.k_per_split = SPLIT_ROWS;
+        g.M = fo; g.N = fi; g.K = n; g.k_per_split = rows_per;
         g.c_split_stride = (int64_t)fo * fi;
-        e = gemm<0>(g, splits, s);
+        g.rowsum = bpart; g.rowsum_stride = fo;
+        e = gemm<0>(g, sp, s);
         if (e != cudaSuccess) return e;
-        split_sum_kernel<<<grid1((int64_t)fo * fi), 256, 0, s>>>(part, splits, (int64_t)fo * fi, (int64_t)fo * fi, gW);
-        dim3 cg((unsigned)((fo + 127) / 128), (unsigned)splits);
-        colsum_kernel<<<cg, 128, 0, s>>>(dz, n, fo, part, fo);   // the dW partials were consumed (stream order)
-        split_sum_kernel<<<grid1(fo), 256, 0, s>>>(part, splits, fo, fo, gb);
-        adv_count_launch(3);
+        split_sum_kernel<<<grid1((int64_t)fo * fi), 256, 0, s>>>(part, sp, (int64_t)fo * fi, (int64_t)fo * fi, gW);
+        split_sum_kernel<<<grid1(fo), 256, 0, s>>>(bpart, sp, fo, fo, gb);
+        adv_count_launch(2);
         if (l == 0) break;
         // dIn = dZ * W, masked by the ReLU of the input (the previous layer's output)
         GemmArgs h{};
