@@ -61,33 +61,69 @@ __global__ void __launch_bounds__(256, 2) gemm_kernel(GemmArgs g) {
     const int64_t kb = (int64_t)blockIdx.z * g.k_per_split;
     const int64_t ke = kb + g.k_per_split < g.K ? kb + g.k_per_split : g.K;
     const bool a_kc = g.sak == 1, b_kc = g.sbk == 1;
-    // element r (0..3) of this thread's share of a 128 x 8 operand chunk
+    // 16-byte loads where the operand allows them: 1 = four consecutive k of one
+    // row (k contiguous), 2 = four consecutive rows or columns of one k; each
+    // such piece lies wholly inside or wholly outside the operand
+    auto al16 = [](const float* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const int a_vec = (a_kc && g.sam % 4 == 0 && g.K % 4 == 0 && al16(g.A)) ? 1
+                      : (g.sam == 1 && g.sak % 4 == 0 && g.M % 4 == 0 && al16(g.A)) ? 2 : 0;
+    const int b_vec = (b_kc && g.sbn % 4 == 0 && g.K % 4 == 0 && al16(g.B)) ? 1
+                      : (g.sbn == 1 && g.sbk % 4 == 0 && g.N % 4 == 0 && al16(g.B)) ? 2 : 0;
+    // element r (0..3) of this thread's share of a 128 x 8 operand chunk (scalar loads)
     auto idx = [&](bool kc, int r, int& mn, int& kk) {
         if (kc) { mn = (tid >> 3) + 32 * r; kk = tid & 7; }
         else { mn = tid & 127; kk = (tid >> 7) + 2 * r; }
     };
+    // this thread's 16-byte piece: mode 1 row tid / 2, k (tid % 2) * 4 .. + 3;
+    // mode 2 k tid / 32, rows or columns (tid % 32) * 4 .. + 3
+    auto vpos = [&](int mode, int& mn, int& kk) {
+        if (mode == 1) { mn = tid >> 1; kk = (tid & 1) * 4; }
+        else { mn = (tid & 31) * 4; kk = tid >> 5; }
+    };
     float ra[4], rb[4];
-    auto load = [&](int64_t k0) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
+    auto load_one = [&](const float* P, int64_t smn, int64_t sk, int64_t lim, int64_t o0, bool kc, int mode,
+                        int64_t k0, float (&r4)[4]) {
+        if (mode) {
             int mn, kk;
-            idx(a_kc, r, mn, kk);
-            const int64_t m = m0 + mn, ka = k0 + kk;
-            ra[r] = (m < g.M && ka < ke) ? g.A[m * g.sam + ka * g.sak] : 0.f;
-            idx(b_kc, r, mn, kk);
-            const int64_t n = n0 + mn, kbb = k0 + kk;
-            rb[r] = (n < g.N && kbb < ke) ? g.B[kbb * g.sbk + n * g.sbn] : 0.f;
+            vpos(mode, mn, kk);
+            const int64_t x = o0 + mn, k = k0 + kk;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (x < lim && k < ke) v = *reinterpret_cast<const float4*>(P + x * smn + k * sk);
+            r4[0] = v.x; r4[1] = v.y; r4[2] = v.z; r4[3] = v.w;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                int mn, kk;
+                idx(kc, r, mn, kk);
+                const int64_t x = o0 + mn, k = k0 + kk;
+                r4[r] = (x < lim && k < ke) ? P[x * smn + k * sk] : 0.f;
+            }
+        }
+    };
+    auto load = [&](int64_t k0) {
+        load_one(g.A, g.sam, g.sak, g.M, m0, a_kc, a_vec, k0, ra);
+        load_one(g.B, g.sbn, g.sbk, g.N, n0, b_kc, b_vec, k0, rb);
+    };
+    auto store_one = [&](float (*S)[GT + 4], bool kc, int mode, const float (&r4)[4]) {
+        int mn, kk;
+        if (mode == 1) {
+            vpos(1, mn, kk);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) S[kk + j][mn] = r4[j];
+        } else if (mode == 2) {
+            vpos(2, mn, kk);
+            *reinterpret_cast<float4*>(&S[kk][mn]) = make_float4(r4[0], r4[1], r4[2], r4[3]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                idx(kc, r, mn, kk);
+                S[kk][mn] = r4[r];
+            }
         }
     };
     auto store = [&](int buf) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            int mn, kk;
-            idx(a_kc, r, mn, kk);
-            As[buf][kk][mn] = ra[r];
-            idx(b_kc, r, mn, kk);
-            Bs[buf][kk][mn] = rb[r];
-        }
+        store_one(As[buf], a_kc, a_vec, ra);
+        store_one(Bs[buf], b_kc, b_vec, rb);
     };
     uint64_t acc[8][4];   // row i, columns (2 jj, 2 jj + 1) as an FP32 pair
 #pragma unroll

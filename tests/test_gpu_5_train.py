@@ -244,3 +244,33 @@ def test_tensor_core_gradient_ragged_shapes(gpu_lib, precision, widths, n):
     assert abs(float(loss.item()) - loss_ref) <= 1e-2 * abs(loss_ref)
     assert rel.max() < 2e-2 * np.sqrt(3001 / n) and cos > 0.999
     assert m.device_status() == 0
+
+
+@pytest.mark.parametrize("widths,n", [((33, 66, 132, 40, 1), 3001), ((64, 200, 1, 8, 1), 3001),
+                                      ((64, 128, 32, 64, 1), 100)])
+def test_fp32_gradient_ragged_shapes(gpu_lib, widths, n):
+    """The FP32 step's GEMMs on ragged shapes against the FP64 oracle gradient.
+    (33, 66, 132, 40): rows of A that are not 16-byte aligned and partial
+    128 x 128 tiles in both directions.  (64, 200, 1, 8): a one-neuron hidden
+    layer, so the forward, the ReLU backward and both weight gradients around
+    it take the matrix-vector kernel (one column: the bias sums of the next
+    layer's weight gradient come from its row sums; one row: 128-row splits
+    and the extra bias thread).  At 100 rows: one partial tile and a single
+    short split.  FP32 sums every output in the definition's order, so the
+    bound is the FP32 one of the 64-256-256-256 test."""
+    d = W.make_descriptors(n, 91)
+    f, st = oracle.extract_features(d, widths[0])
+    t = W.make_labels(d, 91)
+    mu, sg = oracle.fit_standardizer(f, st)
+    p = W.make_weights(widths, 92, "glorot", 0.05)
+    loss_ref, g_ref = oracle.loss_grad(f, t, widths, p, mu, sg)
+    m = advisor.Model(widths, max_rows=n, max_kernels=1)
+    m.set_params(p, mu, sg)
+    loss, g = m.loss_grad(torch.from_numpy(f).cuda(), torch.from_numpy(t).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    rel = _split_rel(g, g_ref, widths)
+    cos = float(g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref)))
+    print("fp32 ragged: per-tensor rel-L2", np.array2string(rel, precision=2), "cos", cos)
+    assert abs(float(loss.item()) - loss_ref) <= 1e-5 * abs(loss_ref)
+    assert rel.max() < 1e-4 and cos > 0.999999
+    assert m.device_status() == 0
