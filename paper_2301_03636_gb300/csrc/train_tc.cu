@@ -324,31 +324,52 @@ __global__ void __launch_bounds__(256) dz_last_colsum16_kernel(const float* __re
     float sl = 0.f, sd = 0.f;                   // this row lane's loss and dy sums (column group 0)
     float wq[8];
     load8f(wo + 8 * cg, wq);
-    for (int r = r0 + rl; r < r0 + VEC_ROWS && r < n; r += lanes) {
-        const int v = r * w8 + cg;
-        float hv[8], o[8];
-        unpack8<T>(reinterpret_cast<const uint4*>(h)[v], hv);
-        float d;
-        if (labels) {
-            const float e = y[r] - labels[r];
-            d = e / (float)n;
-            if (cg == 0) {
-                sl += 0.5f * e * e;
-                sd += d;
+    const int r_end = r0 + VEC_ROWS < n ? r0 + VEC_ROWS : n;
+    constexpr int U = 8;   // rows whose loads are issued together (the sums still take them in order)
+    for (int rb = r0 + rl; rb < r_end; rb += U * lanes) {
+        uint4 hq[U];
+        float ya[U], yb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int r = rb + u * lanes;
+            if (r < r_end) {
+                hq[u] = reinterpret_cast<const uint4*>(h)[r * w8 + cg];
+                if (labels) {
+                    ya[u] = y[r];
+                    yb[u] = labels[r];
+                } else {
+                    ya[u] = dy[r];
+                }
             }
-        } else {
-            d = dy[r];
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) o[i] = hv[i] > 0.f ? d * wq[i] : 0.f;
-        const uint4 pk = pack8<T>(o);
-        reinterpret_cast<uint4*>(dz)[v] = pk;
-        float q[8];
-        unpack8<T>(pk, q);
+        for (int u = 0; u < U; ++u) {
+            const int r = rb + u * lanes;
+            if (r >= r_end) break;
+            float hv[8], o[8];
+            unpack8<T>(hq[u], hv);
+            float d;
+            if (labels) {
+                const float e = ya[u] - yb[u];
+                d = e / (float)n;
+                if (cg == 0) {
+                    sl += 0.5f * e * e;
+                    sd += d;
+                }
+            } else {
+                d = ya[u];
+            }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            s0[i] += q[i];
-            s1[i] = fmaf(d, hv[i], s1[i]);
+            for (int i = 0; i < 8; ++i) o[i] = hv[i] > 0.f ? d * wq[i] : 0.f;
+            const uint4 pk = pack8<T>(o);
+            reinterpret_cast<uint4*>(dz)[r * w8 + cg] = pk;
+            float q[8];
+            unpack8<T>(pk, q);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                s0[i] += q[i];
+                s1[i] = fmaf(d, hv[i], s1[i]);
+            }
         }
     }
 #pragma unroll
