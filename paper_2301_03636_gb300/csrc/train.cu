@@ -321,12 +321,21 @@ __global__ void rmsprop_kernel(float* __restrict__ p, const float* __restrict__ 
     }
 }
 
-// grad[j] = sum over splits (in order) of part[s][j]
+// grad[j] = sum over splits (in order) of part[s][j]; eight partials' loads
+// are issued together, then added one after another
 __global__ void split_sum_kernel(const float* __restrict__ part, int splits, int64_t stride, int64_t len,
                                  float* __restrict__ grad) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
         float s = 0.f;
-        for (int i = 0; i < splits; ++i) s += part[(int64_t)i * stride + j];
+        int i = 0;
+        for (; i + 8 <= splits; i += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = part[(int64_t)(i + u) * stride + j];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u];
+        }
+        for (; i < splits; ++i) s += part[(int64_t)i * stride + j];
         grad[j] = s;
     }
 }
