@@ -6,8 +6,11 @@
 // GEMMs are 128x128-tiled SIMT FP32 with generic operand strides:
 //   forward   Out = In * W^T (+ b, ReLU on hidden layers)
 //   dIn       dH  = dZ * W, masked by the ReLU of the layer input
-//   dW        dW  = dZ^T * In, split over rows in fixed chunks, then summed in
-//             a fixed order (deterministic: the same inputs give the same bits)
+//   dW, db    dW  = dZ^T * In and db = the column sums of dZ in the same
+//             launch, split over rows in fixed chunks, then summed in a fixed
+//             order (deterministic: the same inputs give the same bits)
+// A layer with one output (or one input) column runs as a matrix-vector
+// kernel instead of a 128-wide tile.
 #include <cmath>
 
 #include "features.cuh"
