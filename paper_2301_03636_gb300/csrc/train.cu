@@ -378,7 +378,7 @@ size_t train_layout(const ModelLayout& L, int64_t R, TrainLayout* t) {
         const int64_t len = (int64_t)L.widths[l] * L.widths[l + 1];
         lmax = len > lmax ? len : lmax;
     }
-    t->part = take((size_t)t->splits * lmax * 4);
+    t->part = take((size_t)2 * t->splits * lmax * 4);   // room for up to twice the 1,024-row splits
     t->loss_part = take(1024 * 4);
     t->loss = take(64);
     // 16-bit tensor-core training: 16-bit activations, weights and dZ
@@ -448,9 +448,13 @@ cudaError_t launch_backward_saved(const ModelLayout& L, const TrainLayout& T, ui
     float* dnext = reinterpret_cast<float*>(TW + T.dB);
     float* part = reinterpret_cast<float*>(TW + T.part);
     float* bpart = reinterpret_cast<float*>(TW + T.bias_part);
-    int64_t lmax = 0;   // the dW partial buffer holds T.splits x lmax floats
+    int64_t lmax = 0;   // the dW partial buffer holds 2 x T.splits x lmax floats
     for (int l = 0; l < L.n_layers; ++l)
         lmax = (int64_t)L.widths[l] * L.widths[l + 1] > lmax ? (int64_t)L.widths[l] * L.widths[l + 1] : lmax;
+    const int64_t part_cap = 2 * (int64_t)T.splits * lmax;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 0;
     for (int l = L.n_layers - 1; l >= 0; --l) {
         const int fi = L.widths[l], fo = L.widths[l + 1];
         float* gW = grad + L.layer_w_off[l];
@@ -458,9 +462,21 @@ cudaError_t launch_backward_saved(const ModelLayout& L, const TrainLayout& T, ui
         // dW = dZ^T * In and db = column sums of dZ in one launch, split over rows
         // in fixed chunks, each summed in a fixed order.  The single-output layer's
         // matrix-vector form takes 128-row chunks (eight times the threads) where
-        // its partials fit.
+        // its partials fit.  The tiled form takes as many chunks (whole 8-row
+        // steps) as give two blocks on every SM once: 1,024-row chunks of a
+        // 256 x 256 layer give 256 blocks, two on 104 SMs and one on the other 48,
+        // so the launch lasts two block-times for 1.7 of work.
         int64_t rows_per = SPLIT_ROWS;
-        if (fo == 1 && ((n + 127) / 128) * (int64_t)fi <= (int64_t)T.splits * lmax) rows_per = 128;
+        if (fo == 1) {
+            if (((n + 127) / 128) * (int64_t)fi <= part_cap) rows_per = 128;
+        } else if (fi > 1 && sms > 0) {
+            const int64_t tiles = (int64_t)((fo + GT - 1) / GT) * ((fi + GT - 1) / GT);
+            const int64_t want = 2 * sms / tiles > 1 ? 2 * sms / tiles : 1;
+            int64_t rp = ((n + want - 1) / want + 7) / 8 * 8;
+            rp = rp < 64 ? 64 : rp;
+            const int64_t spl = (n + rp - 1) / rp;
+            if (spl * fo * fi <= part_cap && spl * fo <= T.bias_part_floats) rows_per = rp;
+        }
         const int sp = (int)((n + rows_per - 1) / rows_per);
         GemmArgs g{};
         g.A = dz; g.sam = 1; g.sak = fo;
